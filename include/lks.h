@@ -1,0 +1,152 @@
+/*
+ * lks.h -- C ABI of the GB300 library for the lattice kinetic scheme (LKS) with a rigidly moving
+ * design grid and its discrete adjoint (arXiv 2506.23895).
+ *
+ * The calls follow the paper's statement of the problem:
+ *   lks_set_design(gamma)      the pseudo-density gamma : D -> [0,1] on the design grid (Sec. 2.1,
+ *                              Eq. 1), mapped to the Brinkman coefficient kappa_ref (Sec. 2.3);
+ *   lks_set_motion(schedule)   the prescribed rigid motion theta(t), omega(t), x_G(t), u_G(t) of
+ *                              the design grid (Sec. 2.3, Eqs. rigid_body_position/velocity);
+ *   lks_forward(n) -> J        Algorithm 1 (Sec. 2.3) for n steps with the time-averaged
+ *                              objective J1 or J2 (Sec. 2.5);
+ *   lks_adjoint() -> dJ/dgamma the reverse-time adjoint sweep (Algorithm 2, Sec. 2.4) taken as the
+ *                              exact discrete adjoint of the forward steps, with the design
+ *                              sensitivity gathered back onto the design grid (Sec. 2.4).
+ *
+ * Conventions for every call:
+ *   - Every function returns an lks_status; nothing throws across the ABI.  After an error,
+ *     lks_last_error() returns a one-line message.
+ *   - Input arrays are copied; the caller keeps ownership.  The library never frees caller
+ *     memory.  Device memory is either the caller's workspace (lks_create) or allocated by the
+ *     library and released by lks_destroy.
+ *   - "host" pointers are ordinary CPU memory; "device" pointers are CUDA global memory on the
+ *     context's device.  All work is issued on cfg.stream (NULL = legacy default stream); calls
+ *     that return host values synchronise that stream.
+ *   - Arrays are row-major with x fastest: analysis fields [nz][ny][nx], design fields
+ *     [lz][ly][lx] (nz = lz = 1 in 2D).
+ *   - A context is not thread-safe; use one context per host thread.
+ */
+#ifndef LKS_H
+#define LKS_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lks_ctx lks_ctx;
+
+typedef enum {
+    LKS_OK = 0,
+    LKS_ERR_ARG = 1,      /* invalid argument or configuration (message says which) */
+    LKS_ERR_ORDER = 2,    /* call out of order, e.g. adjoint before forward */
+    LKS_ERR_NOMEM = 3,    /* workspace too small or device allocation failed */
+    LKS_ERR_CUDA = 4,     /* a CUDA runtime call failed */
+    LKS_ERR_DIVERGED = 5, /* non-finite or |u| > 0.5 state after a forward run */
+    LKS_ERR_TIMEOUT = 6   /* reserved for bounded device waits */
+} lks_status;
+
+/* Face boundary types; faces are ordered x-, x+, y-, y+, z-, z+ (Eqs. bc_rho, bc_u).
+ * PERIODIC must be set on both faces of an axis.  WALL and INLET prescribe u (bc_val[f][0..2])
+ * and copy rho from the interior; OUTLET prescribes rho (bc_val[f][3]) and the tangential u and
+ * copies the normal u.  A boundary node copies from the interior node one step inward along
+ * every boundary normal it lies on; on edges and corners WALL > INLET > OUTLET, ties to the
+ * lower face index. */
+enum { LKS_BC_PERIODIC = 0, LKS_BC_WALL = 1, LKS_BC_INLET = 2, LKS_BC_OUTLET = 3 };
+
+/* Objectives of Sec. 2.5: J1 = -mean pressure (p = rho/3) over the target region and J2 =
+ * -mean n.u over it, both averaged over the steps win_begin..win_end. */
+enum { LKS_OBJ_PRESSURE = 0, LKS_OBJ_VELOCITY = 1 };
+
+/* Arithmetic of the state and adjoint stencils.  FP32 keeps rho - rho0 and u in float with
+ * FP64 objective and sensitivity accumulation; FP64 is the plain double-precision path. */
+enum { LKS_FP32 = 0, LKS_FP64 = 1 };
+
+typedef struct {
+    int dim;                 /* 2 (D2Q9) or 3 (D3Q15) */
+    int nx, ny, nz;          /* analysis grid; nz = 1 in 2D; every active axis >= 3 nodes */
+    int lx, ly, lz;          /* design grid (unit spacing); lx = 0: no moving body */
+    int precision;           /* LKS_FP32 or LKS_FP64 */
+    int max_steps;           /* largest n_steps passed to lks_forward (sizes the checkpoints) */
+    double A;                /* viscosity parameter of f^eq, nu = 1/6 - 2A/9 (Sec. 2.2) */
+    double kappa_max, q;     /* Brinkman interpolation kappa_ref(gamma) (Sec. 2.3) */
+    double rho0;             /* reference density; the FP32 path stores rho - rho0 */
+    int bc[6];               /* LKS_BC_* per face */
+    double bc_val[6][4];     /* per face: ux, uy, uz, rho */
+    double u_init[3];        /* initial uniform velocity (rho = rho0), then boundary values */
+    double body_force[3];    /* constant body force added to u (u = u* + F); 0 normally */
+    double xi_G[3];          /* rotation centre in design-grid coordinates */
+    int obj_kind;            /* LKS_OBJ_* */
+    int obj_box[6];          /* target region: inclusive x0,x1,y0,y1,z0,z1 */
+    double obj_dir[3];       /* n for J2 */
+    double obj_cyl_r;        /* > 0: region also limited to (x-cx)^2 + (y-cy)^2 <= r^2 */
+    double obj_cyl_c[2];
+    int win_begin, win_end;  /* objective window (inclusive step indices, 1-based) */
+    size_t ckpt_bytes;       /* device bytes for adjoint snapshots; 0 = full history if it
+                                fits in 8 GB, else the minimum of a two-level scheme */
+    void* stream;            /* cudaStream_t for all work; NULL = legacy default stream */
+} lks_config;
+
+/* Prescribed rigid motion, rows n = 0..n_rows-1 for time t_n = n (Delta t = 1).
+ * Each row: theta, omega, xG[3], uG[3] (8 doubles, host memory, copied).  In 3D the rotation
+ * is about the z axis (the paper's 3D rotor, Sec. 3.3); x_ref = R(theta)(xi - xi_G) + x_G and
+ * u_ref = R'(theta)(xi - xi_G) omega + u_G (Eqs. rigid_body_position / rigid_body_velocity). */
+typedef struct {
+    int n_rows;
+    const double* rows;
+} lks_motion;
+
+/* Bytes of device workspace a context for cfg needs (0 on an invalid cfg). */
+size_t lks_workspace_bytes(const lks_config* cfg);
+
+/* Create a context.  workspace: device pointer of ws_bytes >= lks_workspace_bytes(cfg),
+ * 256-byte aligned, owned by the caller and kept alive until lks_destroy; or NULL to let the
+ * library allocate it.  Errors: LKS_ERR_ARG (bad cfg; *out = NULL), LKS_ERR_NOMEM. */
+lks_status lks_create(const lks_config* cfg, void* workspace, size_t ws_bytes, lks_ctx** out);
+
+/* Set gamma on the design grid (lx*ly*lz doubles; host if on_device = 0, else device).
+ * Values must lie in [0,1] (LKS_ERR_ARG otherwise).  Invalidates any forward run. */
+lks_status lks_set_design(lks_ctx* ctx, const double* gamma, int on_device);
+
+/* Set the motion schedule; needs n_rows >= max_steps + 1.  The transfer footprint (every
+ * analysis node within two cells of a moved design node) must stay inside the grid and off
+ * boundary nodes for every step, else LKS_ERR_ARG.  Invalidates any forward run. */
+lks_status lks_set_motion(lks_ctx* ctx, const lks_motion* motion);
+
+/* Replace the initial state (rho, ux, uy, uz planes of nodes doubles each, host).  NULL
+ * restores the default (rho0, u_init, then boundary values). */
+lks_status lks_set_initial_state(lks_ctx* ctx, const double* state);
+
+/* Algorithm 1 for n_steps (1 <= n_steps <= max_steps) from the initial state; writes J
+ * (host double) and keeps what the adjoint needs.  LKS_ERR_ORDER without design/motion. */
+lks_status lks_forward(lks_ctx* ctx, int n_steps, double* J_out);
+
+/* Exact discrete adjoint of the last forward run; writes dJ/dgamma (lx*ly*lz doubles, host or
+ * device).  LKS_ERR_ORDER if no valid forward run precedes it. */
+lks_status lks_adjoint(lks_ctx* ctx, double* dJdgamma, int on_device);
+
+/* Copy the current forward state to the host as (rho, ux, uy, uz) planes in double. */
+lks_status lks_get_state(const lks_ctx* ctx, double* state_out);
+
+/* Evaluate the transfer alone at step n of the motion schedule: kappa (nodes doubles) and
+ * u_S (3 planes) on the whole analysis grid, host memory. */
+lks_status lks_transfer(lks_ctx* ctx, int step, double* kappa_out, double* us_out);
+
+/* Counters of the last forward+adjoint: [0] forward steps, [1] recomputed steps,
+ * [2] snapshot slots, [3] tape length (steps per segment), [4] kernel launches. */
+lks_status lks_get_stats(const lks_ctx* ctx, long long* stats5);
+
+/* The checkpoint schedule the adjoint would follow, as (kind, a, b) triples, for inspection:
+ * kind 0 restore a, 1 advance a->b (segment indices), 2 store a, 3 free a, 4 tape a,
+ * 5 adjoint a.  Returns the number of triples written (<= cap) or -1 on bad arguments.
+ * Host only; needs no device. */
+int lks_checkpoint_schedule(int n_segments, int free_slots, int* triples, int cap);
+
+const char* lks_last_error(const lks_ctx* ctx);
+void lks_destroy(lks_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LKS_H */

@@ -1,0 +1,185 @@
+// Device-side helpers: lattice velocity sets, node classification, boundary rules and the
+// velocity-gradient stencil.  Used by every kernel file of the library.
+#pragma once
+
+#include "lks_internal.h"
+
+namespace lks {
+
+// ------------------------------------------------------------------ lattices (Sec. 2.2)
+// D2Q9: rest, 4 axes, 4 diagonals.  D3Q15: rest, 6 axes, 8 cube corners.  Standard weights
+// (4/9, 1/9, 1/36) and (2/9, 1/9, 1/72).
+template <int D>
+struct Lat;
+
+template <>
+struct Lat<2> {
+    static constexpr int Q = 9;
+    __host__ __device__ static constexpr int c(int i, int a) {
+        // order: 0 | +x +y -x -y | (+,+) (-,+) (-,-) (+,-)
+        return a == 0 ? ((i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0))
+             : a == 1 ? ((i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0))
+                      : 0;
+    }
+    __host__ __device__ static constexpr double w(int i) {
+        return i == 0 ? 4.0 / 9.0 : (i < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
+    }
+};
+
+template <>
+struct Lat<3> {
+    static constexpr int Q = 15;
+    // order: 0 | +x -x +y -y +z -z | corners (sx,sy,sz) for k = 7..14 enumerated below
+    __host__ __device__ static constexpr int corner(int k, int a) {
+        // k = 0..7 -> signs of the 8 corners: bit a set -> -1
+        return ((k >> a) & 1) ? -1 : 1;
+    }
+    __host__ __device__ static constexpr int c(int i, int a) {
+        return i == 0 ? 0
+             : i < 7 ? ((i - 1) / 2 == a ? ((i - 1) % 2 == 0 ? 1 : -1) : 0)
+                     : corner(i - 7, a);
+    }
+    __host__ __device__ static constexpr double w(int i) {
+        return i == 0 ? 2.0 / 9.0 : (i < 7 ? 1.0 / 9.0 : 1.0 / 72.0);
+    }
+};
+
+// ------------------------------------------------------------------ indexing
+
+__device__ __forceinline__ long long node_index(const Geom& g, int x, int y, int z) {
+    return ((long long)z * g.n[1] + y) * g.n[0] + x;
+}
+
+__device__ __forceinline__ int wrapi(int i, int n) {
+    i = (i < 0) ? i + n : i;
+    return (i >= n) ? i - n : i;
+}
+
+__device__ __forceinline__ bool is_boundary(const Geom& g, int x, int y, int z) {
+    const int c[3] = {x, y, z};
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+        if (a < g.dim && !g.periodic[a] && (c[a] == 0 || c[a] == g.n[a] - 1)) return true;
+    return false;
+}
+
+__device__ __forceinline__ bool in_box(const Geom& g, int x, int y, int z, long long& bi) {
+    int bx = x - g.blo[0], by = y - g.blo[1], bz = z - g.blo[2];
+    if (g.boxN == 0 || bx < 0 || by < 0 || bz < 0 || bx >= g.bn[0] || by >= g.bn[1] ||
+        bz >= g.bn[2])
+        return false;
+    bi = ((long long)bz * g.bn[1] + by) * g.bn[0] + bx;
+    return true;
+}
+
+__device__ __forceinline__ bool in_target(const Geom& g, int x, int y, int z) {
+    if (x < g.obox[0] || x > g.obox[1] || y < g.obox[2] || y > g.obox[3]) return false;
+    if (g.dim == 3 && (z < g.obox[4] || z > g.obox[5])) return false;
+    if (g.ocyl_r > 0.0) {
+        double dx = x - g.ocyl_c[0], dy = y - g.ocyl_c[1];
+        if (dx * dx + dy * dy > g.ocyl_r * g.ocyl_r) return false;
+    }
+    return true;
+}
+
+// ------------------------------------------------------------------ boundary rules
+// Boundary node b copies the unprescribed quantities from the interior node one step inward
+// along each boundary normal it lies on.  The face that decides b's type is the one with the
+// highest precedence (WALL > INLET > OUTLET), ties to the lower face index.
+
+__device__ __forceinline__ int bc_prec(int t) {
+    return t == BC_WALL ? 3 : (t == BC_INLET ? 2 : (t == BC_OUTLET ? 1 : 0));
+}
+
+// Winning face of a boundary node given which faces it lies on (side[a]: -1 none, 0 low, 1 high).
+__device__ __forceinline__ int winning_face(const Geom& g, const int side[3]) {
+    int best = -1;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (side[a] < 0) continue;
+        int f = 2 * a + side[a];
+        if (best < 0 || bc_prec(g.bc[f]) > bc_prec(g.bc[best])) best = f;
+    }
+    return best;
+}
+
+// Value of boundary node (winning face f) given its source node's value v.
+template <class T>
+__device__ __forceinline__ V4<T> bc_value(const Geom& g, int f, const V4<T>& v) {
+    V4<T> b;
+    int t = g.bc[f];
+    if (t == BC_WALL || t == BC_INLET) {
+        b.r = v.r;
+        b.x = (T)g.bcv[f][0];
+        b.y = (T)g.bcv[f][1];
+        b.z = (g.dim == 3) ? (T)g.bcv[f][2] : (T)0;
+    } else {
+        int na = f / 2;
+        b.r = (T)(g.bcv[f][3] - g.rho0);
+        b.x = (na == 0) ? v.x : (T)g.bcv[f][0];
+        b.y = (na == 1) ? v.y : (T)g.bcv[f][1];
+        b.z = (g.dim == 3) ? ((na == 2) ? v.z : (T)g.bcv[f][2]) : (T)0;
+    }
+    return b;
+}
+
+// Options per axis for boundary nodes sourced from interior node coordinate ci along axis a:
+// returns how many (1..3) and fills coordinates (first is ci itself) and sides.
+__device__ __forceinline__ int bc_axis_options(const Geom& g, int a, int ci, int opt[3],
+                                               int side[3]) {
+    opt[0] = ci;
+    side[0] = -1;
+    int k = 1;
+    if (a < g.dim && !g.periodic[a]) {
+        if (ci == 1) {
+            opt[k] = 0;
+            side[k] = 0;
+            ++k;
+        }
+        if (ci == g.n[a] - 2) {
+            opt[k] = g.n[a] - 1;
+            side[k] = 1;
+            ++k;
+        }
+    }
+    return k;
+}
+
+// Write every boundary node whose copy source is interior node (x,y,z) holding value v.
+template <class T>
+__device__ void write_bc_from(const Geom& g, int x, int y, int z, const V4<T>& v, V4<T>* s) {
+    int ox[3], oy[3], oz[3], sx[3], sy[3], sz[3];
+    int nx = bc_axis_options(g, 0, x, ox, sx);
+    int ny = bc_axis_options(g, 1, y, oy, sy);
+    int nz = bc_axis_options(g, 2, z, oz, sz);
+    if (nx == 1 && ny == 1 && nz == 1) return;
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                if (i == 0 && j == 0 && k == 0) continue;
+                int side[3] = {sx[i], sy[j], sz[k]};
+                int f = winning_face(g, side);
+                s[node_index(g, ox[i], oy[j], oz[k])] = bc_value(g, f, v);
+            }
+}
+
+// ------------------------------------------------------------------ gradient stencil
+// First derivative along an axis: central difference, periodic wrap, and the second-order
+// one-sided difference on a non-periodic boundary node (the reading taken for the velocity
+// gradient of f^eq).  coef(i, off): weight of row i's stencil at offset off (0 if none).
+__device__ __forceinline__ double deriv_coef(int i, int n, int periodic, int off) {
+    if (periodic) return off == 1 ? 0.5 : (off == -1 ? -0.5 : 0.0);
+    if (i == 0) return off == 0 ? -1.5 : (off == 1 ? 2.0 : (off == 2 ? -0.5 : 0.0));
+    if (i == n - 1) return off == 0 ? 1.5 : (off == -1 ? -2.0 : (off == -2 ? 0.5 : 0.0));
+    return off == 1 ? 0.5 : (off == -1 ? -0.5 : 0.0);
+}
+
+// Peskin four-point cosine kernel w(r) = (1 + cos(pi r / 2)) / 4 for |r| < 2 (Sec. 2.3).
+__device__ __forceinline__ double peskin(double r) {
+    return fabs(r) < 2.0 ? 0.25 * (1.0 + cospi(0.5 * r)) : 0.0;
+}
+__device__ __forceinline__ float peskin(float r) {
+    return fabsf(r) < 2.0f ? 0.25f * (1.0f + cospif(0.5f * r)) : 0.0f;
+}
+
+}  // namespace lks

@@ -1,0 +1,118 @@
+// Internal declarations shared by the host engine and the kernel translation units.
+// Not part of the public ABI (include/lks.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lks {
+
+// One node of state (rho - rho0, ux, uy, uz) or adjoint (lam_rho, lam_u).  16 B (float) or
+// 32 B (double), so one vector load/store moves a node.
+template <class T>
+struct alignas(4 * sizeof(T)) V4 {
+    T r, x, y, z;
+};
+
+enum { BC_PERIODIC = 0, BC_WALL = 1, BC_INLET = 2, BC_OUTLET = 3 };
+
+// Everything a kernel needs to know about the analysis grid, boundaries, objective and the
+// transfer footprint box.  Passed by value.
+struct Geom {
+    int dim;
+    int n[3];
+    int periodic[3];
+    long long nodes;
+    int bc[6];
+    double bcv[6][4];   // ux, uy, uz, rho per face
+    double rho0, A;
+    double body[3];
+    // footprint box (union over all steps of the transfer support), may be empty
+    int blo[3], bn[3];
+    long long boxN;
+    // objective region
+    int okind;
+    int obox[6];
+    double odir[3];
+    double ocyl_r, ocyl_c[2];
+    double ocount;
+};
+
+// Design grid and per-step rigid motion.
+struct Design {
+    int L[3];
+    double xiG[3];
+    long long nd;       // design nodes
+    long long ncol;     // design columns lx*ly
+};
+
+struct Motion {
+    double c, s, om;    // cos(theta), sin(theta), omega
+    double xG[3], uG[3];
+};
+
+// Per-step scratch produced by the design-position kernel and consumed by the transfer,
+// the fill and the sensitivity gather.
+struct TransferScratch {
+    int* col_base;       // [ncol][2] floor of x_ref, y_ref per design column
+    void* col_frac;      // [ncol][2] T: fractional part in [0,1)
+    int* zt_idx;         // [bn_z][4] design z index per analysis z of the box (-1: none)
+    void* zt_w;          // [bn_z][4] T: kernel weight
+    int* tap_cnt;        // [box columns]
+    int* tap_idx;        // [box columns][kMaxTaps] design column index
+    void* tap_w;         // [box columns][kMaxTaps] T
+    void* col_m;         // [box columns][3] T: m0, m1x, m1y
+    int* dz_base;        // [lz] floor of the moved z of each design plane
+    void* dz_frac;       // [lz] T: its fractional part
+    int* err;            // device error word (bit 0: tap overflow)
+};
+
+constexpr int kMaxTaps = 32;
+
+// ---- kernel launchers (templated on T = float / double, explicitly instantiated) ----
+template <class T>
+void launch_init_state(const Geom& g, V4<T>* s, cudaStream_t st);
+template <class T>
+void launch_fill_uniform(const Geom& g, V4<T>* s, const double u[3], cudaStream_t st);
+template <class T>
+void launch_apply_bc(const Geom& g, V4<T>* s, cudaStream_t st);
+template <class T>
+void launch_feq(const Geom& g, const V4<T>* s, T* F, cudaStream_t st);
+template <class T>
+void launch_gather(const Geom& g, const T* F, const V4<T>* kus, V4<T>* out, cudaStream_t st);
+template <class T>
+void launch_objective(const Geom& g, const V4<T>* s, double* jstep, cudaStream_t st);
+template <class T>
+void launch_adj_bcT(const Geom& g, V4<T>* lam, double h, cudaStream_t st);
+template <class T>
+void launch_adj_mu(const Geom& g, const V4<T>* lam, const V4<T>* kus, const V4<T>* sn,
+                   V4<T>* mu, T* e, double h, cudaStream_t st);
+template <class T>
+void launch_adj_moments(const Geom& g, const V4<T>* mu, const V4<T>* sp, V4<T>* lam_out,
+                        T* phi, cudaStream_t st);
+template <class T>
+void launch_adj_divT(const Geom& g, const T* phi, V4<T>* lam_out, cudaStream_t st);
+template <class T>
+void launch_check_state(const Geom& g, const V4<T>* s, int* flag, cudaStream_t st);
+
+template <class T>
+void launch_design_prep(const Design& d, const double* gamma, double kappa_max, double q,
+                        T* kref, T* kprime, int* bad, cudaStream_t st);
+template <class T>
+void launch_design_pos(const Design& d, const Geom& g, const Motion& m, TransferScratch ts,
+                       cudaStream_t st);
+template <class T>
+void launch_transfer(const Design& d, const Geom& g, const Motion& m, TransferScratch ts,
+                     const T* kref, V4<T>* kus, cudaStream_t st);
+template <class T>
+void launch_sens(const Design& d, const Geom& g, TransferScratch ts, const T* e,
+                 const T* kprime, double* gacc, cudaStream_t st);
+template <class T>
+void launch_box_to_grid(const Geom& g, const V4<T>* kus, double* kappa, double* us,
+                        cudaStream_t st);
+template <class T>
+void launch_state_to_f64(const Geom& g, const V4<T>* s, double* out, cudaStream_t st);
+template <class T>
+void launch_state_from_f64(const Geom& g, const double* in, V4<T>* s, cudaStream_t st);
+
+}  // namespace lks

@@ -1,0 +1,503 @@
+// Plain per-node kernels of the LKS step and its exact discrete adjoint.
+//
+// Forward step (Alg. 1): k_feq evaluates f_i^eq at every node from the old state (Sec. 2.2,
+// equilibrium with the viscosity term) into a Q-plane scratch, k_gather sums f_i^eq(x - c_i)
+// into rho*, u* (Eqs. rho, u), applies the Brinkman update u = (u* + kappa u_S)/(1 + kappa)
+// (Eq. u_ex_2) and writes the boundary nodes sourced from each interior node (Eqs. bc_rho,
+// bc_u).  Adjoint step (Alg. 2 structure, exact transpose of the above): k_adj_bcT pushes
+// boundary adjoints onto their copy sources, k_adj_mu divides by (1 + kappa) and forms the
+// kappa sensitivity density e, k_adj_moments gathers F~_i(y) = mu_rho(y+c_i) + c_i.mu_u(y+c_i)
+// into the moments of Eqs. arho, au, as and the adjoint equilibrium, k_adj_divT adds the
+// transposed velocity-gradient term.  These kernels are templated on the scalar type; the
+// double instantiation is the plain FP64 path.
+#include "lks_device.cuh"
+
+namespace lks {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+inline unsigned grid_for(long long n) { return (unsigned)((n + kThreads - 1) / kThreads); }
+
+__device__ __forceinline__ void node_coords(const Geom& g, long long m, int& x, int& y, int& z) {
+    x = (int)(m % g.n[0]);
+    long long t = m / g.n[0];
+    y = (int)(t % g.n[1]);
+    z = (int)(t / g.n[1]);
+}
+
+template <class T>
+__global__ void k_init_state(Geom g, V4<T>* s) {
+    long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (m >= g.nodes) return;
+    V4<T> v;
+    v.r = (T)0;
+    v.x = (T)0;
+    v.y = (T)0;
+    v.z = (T)0;
+    s[m] = v;
+}
+
+template <class T>
+__global__ void k_fill_uniform(Geom g, V4<T>* s, T ux, T uy, T uz) {
+    long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (m >= g.nodes) return;
+    V4<T> v;
+    v.r = (T)0;
+    v.x = ux;
+    v.y = uy;
+    v.z = uz;
+    s[m] = v;
+}
+
+// Every boundary node takes its value from its copy source (used for initial states).
+template <class T>
+__global__ void k_apply_bc(Geom g, V4<T>* s) {
+    long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (m >= g.nodes) return;
+    int x, y, z;
+    node_coords(g, m, x, y, z);
+    if (is_boundary(g, x, y, z)) return;
+    write_bc_from(g, x, y, z, s[m], s);
+}
+
+template <class T, int D>
+__global__ void k_feq(Geom g, const V4<T>* __restrict__ s, T* __restrict__ F) {
+    using L = Lat<D>;
+    long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (m >= g.nodes) return;
+    int c[3];
+    node_coords(g, m, c[0], c[1], c[2]);
+    const V4<T> v = s[m];
+    const T u[3] = {v.x, v.y, D == 3 ? v.z : (T)0};
+    T G[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) G[a][b] = (T)0;
+#pragma unroll
+    for (int b = 0; b < D; ++b) {
+        const int i = c[b], n = g.n[b], per = g.periodic[b];
+#pragma unroll
+        for (int off = -2; off <= 2; ++off) {
+            const T cf = (T)deriv_coef(i, n, per, off);
+            if (cf == (T)0) continue;
+            int q[3] = {c[0], c[1], c[2]};
+            q[b] = wrapi(i + off, n);
+            const V4<T> w = s[node_index(g, q[0], q[1], q[2])];
+            G[0][b] += cf * w.x;
+            G[1][b] += cf * w.y;
+            if (D == 3) G[2][b] += cf * w.z;
+        }
+    }
+    T uu = (T)0;
+#pragma unroll
+    for (int a = 0; a < D; ++a) uu += u[a] * u[a];
+    const T A = (T)g.A;
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) {
+        T cu = (T)0, cSc = (T)0;
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            cu += (T)L::c(i, a) * u[a];
+#pragma unroll
+            for (int b = 0; b < D; ++b)
+                if (L::c(i, a) * L::c(i, b) != 0)
+                    cSc += (T)(L::c(i, a) * L::c(i, b)) * (G[a][b] + G[b][a]);
+        }
+        F[(long long)i * g.nodes + m] =
+            (T)L::w(i) * (v.r + (T)3 * cu + (T)4.5 * cu * cu - (T)1.5 * uu + A * cSc);
+    }
+}
+
+template <class T, int D>
+__global__ void k_gather(Geom g, const T* __restrict__ F, const V4<T>* __restrict__ kus,
+                         V4<T>* __restrict__ out) {
+    using L = Lat<D>;
+    long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (m >= g.nodes) return;
+    int x, y, z;
+    node_coords(g, m, x, y, z);
+    if (is_boundary(g, x, y, z)) return;
+    T rs = (T)0, us[3] = {(T)0, (T)0, (T)0};
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) {
+        const int xs = wrapi(x - L::c(i, 0), g.n[0]);
+        const int ys = wrapi(y - L::c(i, 1), g.n[1]);
+        const int zs = (D == 3) ? wrapi(z - L::c(i, 2), g.n[2]) : 0;
+        const T f = F[(long long)i * g.nodes + node_index(g, xs, ys, zs)];
+        rs += f;
+#pragma unroll
+        for (int a = 0; a < D; ++a)
+            if (L::c(i, a) != 0) us[a] += (T)L::c(i, a) * f;
+    }
+    V4<T> o;
+    o.r = rs;
+    long long bi;
+    if (in_box(g, x, y, z, bi)) {
+        const V4<T> ks = kus[bi];
+        const T k = ks.r, inv = (T)1 / ((T)1 + k);
+        o.x = (us[0] + (T)g.body[0] + k * ks.x) * inv;
+        o.y = (us[1] + (T)g.body[1] + k * ks.y) * inv;
+        o.z = (D == 3) ? (us[2] + (T)g.body[2] + k * ks.z) * inv : (T)0;
+    } else {
+        o.x = us[0] + (T)g.body[0];
+        o.y = us[1] + (T)g.body[1];
+        o.z = (D == 3) ? us[2] + (T)g.body[2] : (T)0;
+    }
+    out[m] = o;
+    write_bc_from(g, x, y, z, o, out);
+}
+
+// Objective at one level (Sec. 2.5): j = -mean(rho)/3 or -mean(n.u) over the target region,
+// one block, fixed-order FP64 reduction.
+template <class T>
+__global__ void k_objective(Geom g, const V4<T>* __restrict__ s, double* jstep) {
+    __shared__ double red[kThreads];
+    const int x0 = g.obox[0], x1 = g.obox[1], y0 = g.obox[2], y1 = g.obox[3];
+    const int z0 = (g.dim == 3) ? g.obox[4] : 0, z1 = (g.dim == 3) ? g.obox[5] : 0;
+    const int bx = x1 - x0 + 1, by = y1 - y0 + 1, bz = z1 - z0 + 1;
+    const long long tot = (long long)bx * by * bz;
+    double acc = 0.0;
+    for (long long k = threadIdx.x; k < tot; k += blockDim.x) {
+        int x = x0 + (int)(k % bx);
+        long long t = k / bx;
+        int y = y0 + (int)(t % by);
+        int z = z0 + (int)(t / by);
+        if (!in_target(g, x, y, z)) continue;
+        const V4<T> v = s[node_index(g, x, y, z)];
+        if (g.okind == 0)
+            acc += (double)v.r;
+        else
+            acc += g.odir[0] * (double)v.x + g.odir[1] * (double)v.y + g.odir[2] * (double)v.z;
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = kThreads / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        double sum = red[0];
+        jstep[0] = (g.okind == 0) ? -(g.rho0 + sum / g.ocount) / 3.0 : -sum / g.ocount;
+    }
+}
+
+// Objective's direct adjoint source at one node (h = window weight or 0 outside the window).
+template <class T>
+__device__ __forceinline__ void obj_source(const Geom& g, int x, int y, int z, double h,
+                                           V4<T>& l) {
+    if (h == 0.0 || !in_target(g, x, y, z)) return;
+    if (g.okind == 0) {
+        l.r += (T)(-h / (3.0 * g.ocount));
+    } else {
+        l.x += (T)(-h * g.odir[0] / g.ocount);
+        l.y += (T)(-h * g.odir[1] / g.ocount);
+        l.z += (T)(-h * g.odir[2] / g.ocount);
+    }
+}
+
+// Transpose of the boundary copies: each interior node adjacent to the boundary collects the
+// copied components of the boundary nodes it sources (WALL/INLET copy rho, OUTLET copies the
+// normal velocity).  Boundary nodes are read only; later kernels treat them as zero.
+template <class T>
+__global__ void k_adj_bcT(Geom g, V4<T>* lam, double h) {
+    long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (m >= g.nodes) return;
+    int x, y, z;
+    node_coords(g, m, x, y, z);
+    if (is_boundary(g, x, y, z)) return;
+    int ox[3], oy[3], oz[3], sx[3], sy[3], sz[3];
+    int nx = bc_axis_options(g, 0, x, ox, sx);
+    int ny = bc_axis_options(g, 1, y, oy, sy);
+    int nz = bc_axis_options(g, 2, z, oz, sz);
+    if (nx == 1 && ny == 1 && nz == 1) return;
+    V4<T> acc = lam[m];
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                if (i == 0 && j == 0 && k == 0) continue;
+                int side[3] = {sx[i], sy[j], sz[k]};
+                int f = winning_face(g, side);
+                V4<T> lb = lam[node_index(g, ox[i], oy[j], oz[k])];
+                obj_source(g, ox[i], oy[j], oz[k], h, lb);
+                int t = g.bc[f];
+                if (t == BC_WALL || t == BC_INLET) {
+                    acc.r += lb.r;
+                } else {
+                    int na = f / 2;
+                    if (na == 0) acc.x += lb.x;
+                    if (na == 1) acc.y += lb.y;
+                    if (na == 2) acc.z += lb.z;
+                }
+            }
+    lam[m] = acc;
+}
+
+// mu = (lam_rho, lam_u / (1 + kappa)) on interior nodes, 0 on boundary nodes; in the
+// footprint box also e = mu_u . (u_S - u^n) = dJ/dkappa(x, t_n).
+template <class T>
+__global__ void k_adj_mu(Geom g, const V4<T>* __restrict__ lam, const V4<T>* __restrict__ kus,
+                         const V4<T>* __restrict__ sn, V4<T>* __restrict__ mu,
+                         T* __restrict__ e, double h) {
+    long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (m >= g.nodes) return;
+    int x, y, z;
+    node_coords(g, m, x, y, z);
+    V4<T> o;
+    if (is_boundary(g, x, y, z)) {
+        o.r = o.x = o.y = o.z = (T)0;
+        mu[m] = o;
+        return;
+    }
+    V4<T> l = lam[m];
+    obj_source(g, x, y, z, h, l);
+    o.r = l.r;
+    long long bi;
+    if (in_box(g, x, y, z, bi)) {
+        const V4<T> ks = kus[bi];
+        const T inv = (T)1 / ((T)1 + ks.r);
+        o.x = l.x * inv;
+        o.y = l.y * inv;
+        o.z = l.z * inv;
+        const V4<T> v = sn[m];
+        e[bi] = o.x * (ks.x - v.x) + o.y * (ks.y - v.y) + o.z * (ks.z - v.z);
+    } else {
+        o.x = l.x;
+        o.y = l.y;
+        o.z = l.z;
+    }
+    mu[m] = o;
+}
+
+__device__ __forceinline__ int sym6(int a, int b) {
+    return a == b ? a : (a + b == 1 ? 3 : (a + b == 2 ? 4 : 5));
+}
+
+// Moments of F~_i(y) = mu_rho(y+c_i) + c_i.mu_u(y+c_i) and the adjoint of f^eq's dependence on
+// rho and u at level n-1; phi = 2 A s~ is kept for the transposed gradient.
+template <class T, int D>
+__global__ void k_adj_moments(Geom g, const V4<T>* __restrict__ mu,
+                              const V4<T>* __restrict__ sp, V4<T>* __restrict__ lo,
+                              T* __restrict__ phi) {
+    using L = Lat<D>;
+    long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (m >= g.nodes) return;
+    int c[3];
+    node_coords(g, m, c[0], c[1], c[2]);
+    T R = (T)0, U[3] = {(T)0, (T)0, (T)0}, S[6] = {(T)0, (T)0, (T)0, (T)0, (T)0, (T)0};
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) {
+        int q[3];
+        bool inside = true;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            q[a] = c[a] + (a < D ? L::c(i, a) : 0);
+            if (a < D) {
+                if (g.periodic[a]) q[a] = wrapi(q[a], g.n[a]);
+                else if (q[a] < 0 || q[a] >= g.n[a]) inside = false;
+            }
+        }
+        if (!inside) continue;
+        const V4<T> mv = mu[node_index(g, q[0], q[1], q[2])];
+        T Ft = mv.r;
+        if (L::c(i, 0) != 0) Ft += (T)L::c(i, 0) * mv.x;
+        if (L::c(i, 1) != 0) Ft += (T)L::c(i, 1) * mv.y;
+        if (D == 3 && L::c(i, 2) != 0) Ft += (T)L::c(i, 2) * mv.z;
+        const T wF = (T)L::w(i) * Ft;
+        R += wF;
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            if (L::c(i, a) == 0) continue;
+            U[a] += (T)L::c(i, a) * wF;
+#pragma unroll
+            for (int b = a; b < D; ++b)
+                if (L::c(i, b) != 0) S[sym6(a, b)] += (T)(L::c(i, a) * L::c(i, b)) * wF;
+        }
+    }
+    const V4<T> v = sp[m];
+    const T u[3] = {v.x, v.y, D == 3 ? v.z : (T)0};
+    V4<T> o;
+    o.r = R;
+    T lu[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        lu[a] = (T)0;
+        if (a < D) {
+            lu[a] = (T)3 * U[a] - (T)3 * R * u[a];
+#pragma unroll
+            for (int b = 0; b < D; ++b) lu[a] += (T)9 * S[sym6(a, b)] * u[b];
+        }
+    }
+    o.x = lu[0];
+    o.y = lu[1];
+    o.z = lu[2];
+    lo[m] = o;
+    const T twoA = (T)(2.0 * g.A);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) phi[(long long)k * g.nodes + m] = twoA * S[k];
+}
+
+// lam_u,alpha(z) += sum_beta (D_beta^T phi_alpha,beta)(z): the transpose of the velocity-gradient
+// stencil, gathered per node from the rows whose stencil reaches z.
+template <class T, int D>
+__global__ void k_adj_divT(Geom g, const T* __restrict__ phi, V4<T>* __restrict__ lo) {
+    long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (m >= g.nodes) return;
+    int c[3];
+    node_coords(g, m, c[0], c[1], c[2]);
+    T acc[3] = {(T)0, (T)0, (T)0};
+#pragma unroll
+    for (int b = 0; b < D; ++b) {
+        const int n = g.n[b], per = g.periodic[b];
+#pragma unroll
+        for (int k = -2; k <= 2; ++k) {
+            int yi = c[b] - k;
+            if (per) yi = wrapi(yi, n);
+            else if (yi < 0 || yi >= n) continue;
+            const T cf = (T)deriv_coef(yi, n, per, k);
+            if (cf == (T)0) continue;
+            int q[3] = {c[0], c[1], c[2]};
+            q[b] = yi;
+            const long long mq = node_index(g, q[0], q[1], q[2]);
+#pragma unroll
+            for (int a = 0; a < D; ++a) acc[a] += cf * phi[(long long)sym6(a, b) * g.nodes + mq];
+        }
+    }
+    V4<T> o = lo[m];
+    o.x += acc[0];
+    o.y += acc[1];
+    if (D == 3) o.z += acc[2];
+    lo[m] = o;
+}
+
+template <class T>
+__global__ void k_check_state(Geom g, const V4<T>* __restrict__ s, int* flag) {
+    long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (m >= g.nodes) return;
+    const V4<T> v = s[m];
+    const double a = fabs((double)v.x) + fabs((double)v.y) + fabs((double)v.z);
+    if (!(a < 0.5) || !isfinite((double)v.r)) atomicOr(flag, 1);
+}
+
+template <class T>
+__global__ void k_state_to_f64(Geom g, const V4<T>* __restrict__ s, double* __restrict__ out) {
+    long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (m >= g.nodes) return;
+    const V4<T> v = s[m];
+    out[m] = g.rho0 + (double)v.r;
+    out[g.nodes + m] = (double)v.x;
+    out[2 * g.nodes + m] = (double)v.y;
+    out[3 * g.nodes + m] = (double)v.z;
+}
+
+template <class T>
+__global__ void k_state_from_f64(Geom g, const double* __restrict__ in, V4<T>* __restrict__ s) {
+    long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (m >= g.nodes) return;
+    V4<T> v;
+    v.r = (T)(in[m] - g.rho0);
+    v.x = (T)in[g.nodes + m];
+    v.y = (T)in[2 * g.nodes + m];
+    v.z = (g.dim == 3) ? (T)in[3 * g.nodes + m] : (T)0;
+    s[m] = v;
+}
+
+}  // namespace
+
+template <class T>
+void launch_init_state(const Geom& g, V4<T>* s, cudaStream_t st) {
+    k_fill_uniform<T><<<grid_for(g.nodes), kThreads, 0, st>>>(g, s, (T)0, (T)0, (T)0);
+}
+
+template <class T>
+void launch_fill_uniform(const Geom& g, V4<T>* s, const double u[3], cudaStream_t st) {
+    k_fill_uniform<T><<<grid_for(g.nodes), kThreads, 0, st>>>(g, s, (T)u[0], (T)u[1],
+                                                              g.dim == 3 ? (T)u[2] : (T)0);
+}
+
+template <class T>
+void launch_apply_bc(const Geom& g, V4<T>* s, cudaStream_t st) {
+    k_apply_bc<T><<<grid_for(g.nodes), kThreads, 0, st>>>(g, s);
+}
+
+template <class T>
+void launch_feq(const Geom& g, const V4<T>* s, T* F, cudaStream_t st) {
+    if (g.dim == 2) k_feq<T, 2><<<grid_for(g.nodes), kThreads, 0, st>>>(g, s, F);
+    else k_feq<T, 3><<<grid_for(g.nodes), kThreads, 0, st>>>(g, s, F);
+}
+
+template <class T>
+void launch_gather(const Geom& g, const T* F, const V4<T>* kus, V4<T>* out, cudaStream_t st) {
+    if (g.dim == 2) k_gather<T, 2><<<grid_for(g.nodes), kThreads, 0, st>>>(g, F, kus, out);
+    else k_gather<T, 3><<<grid_for(g.nodes), kThreads, 0, st>>>(g, F, kus, out);
+}
+
+template <class T>
+void launch_objective(const Geom& g, const V4<T>* s, double* jstep, cudaStream_t st) {
+    k_objective<T><<<1, kThreads, 0, st>>>(g, s, jstep);
+}
+
+template <class T>
+void launch_adj_bcT(const Geom& g, V4<T>* lam, double h, cudaStream_t st) {
+    k_adj_bcT<T><<<grid_for(g.nodes), kThreads, 0, st>>>(g, lam, h);
+}
+
+template <class T>
+void launch_adj_mu(const Geom& g, const V4<T>* lam, const V4<T>* kus, const V4<T>* sn,
+                   V4<T>* mu, T* e, double h, cudaStream_t st) {
+    k_adj_mu<T><<<grid_for(g.nodes), kThreads, 0, st>>>(g, lam, kus, sn, mu, e, h);
+}
+
+template <class T>
+void launch_adj_moments(const Geom& g, const V4<T>* mu, const V4<T>* sp, V4<T>* lam_out,
+                        T* phi, cudaStream_t st) {
+    if (g.dim == 2)
+        k_adj_moments<T, 2><<<grid_for(g.nodes), kThreads, 0, st>>>(g, mu, sp, lam_out, phi);
+    else
+        k_adj_moments<T, 3><<<grid_for(g.nodes), kThreads, 0, st>>>(g, mu, sp, lam_out, phi);
+}
+
+template <class T>
+void launch_adj_divT(const Geom& g, const T* phi, V4<T>* lam_out, cudaStream_t st) {
+    if (g.dim == 2) k_adj_divT<T, 2><<<grid_for(g.nodes), kThreads, 0, st>>>(g, phi, lam_out);
+    else k_adj_divT<T, 3><<<grid_for(g.nodes), kThreads, 0, st>>>(g, phi, lam_out);
+}
+
+template <class T>
+void launch_check_state(const Geom& g, const V4<T>* s, int* flag, cudaStream_t st) {
+    k_check_state<T><<<grid_for(g.nodes), kThreads, 0, st>>>(g, s, flag);
+}
+
+template <class T>
+void launch_state_to_f64(const Geom& g, const V4<T>* s, double* out, cudaStream_t st) {
+    k_state_to_f64<T><<<grid_for(g.nodes), kThreads, 0, st>>>(g, s, out);
+}
+
+template <class T>
+void launch_state_from_f64(const Geom& g, const double* in, V4<T>* s, cudaStream_t st) {
+    k_state_from_f64<T><<<grid_for(g.nodes), kThreads, 0, st>>>(g, in, s);
+}
+
+#define LKS_INST(T)                                                                          \
+    template void launch_init_state<T>(const Geom&, V4<T>*, cudaStream_t);                   \
+    template void launch_fill_uniform<T>(const Geom&, V4<T>*, const double*, cudaStream_t);  \
+    template void launch_apply_bc<T>(const Geom&, V4<T>*, cudaStream_t);                     \
+    template void launch_feq<T>(const Geom&, const V4<T>*, T*, cudaStream_t);                \
+    template void launch_gather<T>(const Geom&, const T*, const V4<T>*, V4<T>*, cudaStream_t); \
+    template void launch_objective<T>(const Geom&, const V4<T>*, double*, cudaStream_t);     \
+    template void launch_adj_bcT<T>(const Geom&, V4<T>*, double, cudaStream_t);              \
+    template void launch_adj_mu<T>(const Geom&, const V4<T>*, const V4<T>*, const V4<T>*,    \
+                                   V4<T>*, T*, double, cudaStream_t);                        \
+    template void launch_adj_moments<T>(const Geom&, const V4<T>*, const V4<T>*, V4<T>*, T*, \
+                                        cudaStream_t);                                       \
+    template void launch_adj_divT<T>(const Geom&, const T*, V4<T>*, cudaStream_t);           \
+    template void launch_check_state<T>(const Geom&, const V4<T>*, int*, cudaStream_t);      \
+    template void launch_state_to_f64<T>(const Geom&, const V4<T>*, double*, cudaStream_t);  \
+    template void launch_state_from_f64<T>(const Geom&, const double*, V4<T>*, cudaStream_t);
+
+LKS_INST(float)
+LKS_INST(double)
+
+}  // namespace lks

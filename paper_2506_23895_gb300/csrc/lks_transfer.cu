@@ -1,0 +1,308 @@
+// Design-grid kernels: the Brinkman interpolation kappa_ref(gamma) (Sec. 2.3), the per-step
+// transfer of kappa and u_S from the rigidly moved design grid onto the analysis grid
+// (Eqs. brinkman_ref, velocity_ref with Peskin's cosine kernel) and its transpose, the design
+// sensitivity gather (Sec. 2.4).
+//
+// The rotation is in the x-y plane (about z in 3D, as in Sec. 3.3), so the kernel weight
+// W = w(dx) w(dy) w(dz) separates into an x-y part that is the same for every design plane and
+// a z part that is the same for every design column.  Per step:
+//   k_design_pos  x_ref, y_ref of every design column (FP64) as integer base + fraction, and
+//                 the z taps of every analysis plane of the footprint box;
+//   k_tap_lists   for each analysis column of the box, the design columns whose support covers
+//                 it (found through the inverse rigid map) with their x-y weights, in design
+//                 index order, plus the moments m0 = sum W, m1 = sum W (xi - xi_G);
+//   k_fill        kappa = sum_z sum_taps W kappa_ref and u_S = omega R'(theta) m1 + u_G m0 on the
+//                 box: a deterministic gather, no atomics;
+//   k_sens        for each design node, sum_x W(x - x_ref) e(x) over its 4^d support (the
+//                 transpose of the kappa transfer), accumulated into dJ/dgamma in FP64.
+#include "lks_device.cuh"
+
+namespace lks {
+
+namespace {
+
+constexpr int kThreads = 256;
+inline unsigned grid_for(long long n) { return (unsigned)((n + kThreads - 1) / kThreads); }
+
+__global__ void k_design_prep_check(long long nd, const double* gamma, int* bad) {
+    long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (k >= nd) return;
+    const double gm = gamma[k];
+    if (!(gm >= 0.0 && gm <= 1.0)) atomicOr(bad, 1);
+}
+
+template <class T>
+__global__ void k_design_prep(long long nd, const double* __restrict__ gamma, double kmax,
+                              double q, T* __restrict__ kref, T* __restrict__ kprime) {
+    long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (k >= nd) return;
+    const double gm = gamma[k];
+    const double d = (1.0 - gm) + q;
+    kref[k] = (T)(kmax * q * gm / d);                 // kappa_ref (Sec. 2.3)
+    kprime[k] = (T)(kmax * q * (1.0 + q) / (d * d));   // d kappa_ref / d gamma
+}
+
+template <class T>
+__global__ void k_design_pos(Design d, Geom g, Motion m, TransferScratch ts) {
+    long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    T* frac = (T*)ts.col_frac;
+    if (k < d.ncol) {
+        const int i = (int)(k % d.L[0]), j = (int)(k / d.L[0]);
+        const double dx = i - d.xiG[0], dy = j - d.xiG[1];
+        const double xr = m.c * dx - m.s * dy + m.xG[0];   // Eq. rigid_body_position
+        const double yr = m.s * dx + m.c * dy + m.xG[1];
+        const double bx = floor(xr), by = floor(yr);
+        ts.col_base[2 * k] = (int)bx;
+        ts.col_base[2 * k + 1] = (int)by;
+        frac[2 * k] = (T)(xr - bx);
+        frac[2 * k + 1] = (T)(yr - by);
+        return;
+    }
+    k -= d.ncol;
+    const int lz = d.L[2];
+    if (k < lz) {  // moved z of design plane k (3D: pure shift; 2D: the single plane at 0)
+        T* dzf = (T*)ts.dz_frac;
+        if (g.dim == 3) {
+            const double zr = (double)k - d.xiG[2] + m.xG[2];
+            const double bz = floor(zr);
+            ts.dz_base[k] = (int)bz;
+            dzf[k] = (T)(zr - bz);
+        } else {
+            ts.dz_base[k] = 0;
+            dzf[k] = (T)0;
+        }
+        return;
+    }
+    k -= lz;
+    if (k < g.bn[2]) {  // z taps of analysis plane blo_z + k
+        int* zi = ts.zt_idx + 4 * k;
+        T* zw = (T*)ts.zt_w + 4 * k;
+        for (int t = 0; t < 4; ++t) {
+            zi[t] = -1;
+            zw[t] = (T)0;
+        }
+        if (g.dim == 2) {
+            zi[0] = 0;
+            zw[0] = (T)1;
+            return;
+        }
+        const int z = g.blo[2] + (int)k;
+        const double shift = m.xG[2] - d.xiG[2];       // z_ref(zeta) = zeta + shift
+        const int z0 = (int)floor((double)z - shift) - 1;
+        int cnt = 0;
+        for (int t = 0; t < 4; ++t) {
+            const int zeta = z0 + t;
+            if (zeta < 0 || zeta >= lz) continue;
+            const double zr = (double)zeta + shift;
+            const double bz = floor(zr);
+            const T r = (T)(z - (int)bz) - (T)(zr - bz);
+            if (!(fabs((double)r) < 2.0)) continue;
+            const T w = peskin(r);
+            if (w == (T)0) continue;
+            zi[cnt] = zeta;
+            zw[cnt] = w;
+            ++cnt;
+        }
+    }
+}
+
+template <class T>
+__global__ void k_tap_lists(Design d, Geom g, Motion m, TransferScratch ts) {
+    const long long ncols = (long long)g.bn[0] * g.bn[1];
+    long long col = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (col >= ncols) return;
+    const int x = g.blo[0] + (int)(col % g.bn[0]);
+    const int y = g.blo[1] + (int)(col / g.bn[0]);
+    // inverse rigid map: design coordinates of this analysis column
+    const double px = x - m.xG[0], py = y - m.xG[1];
+    const double ic = m.c * px + m.s * py + d.xiG[0];
+    const double jc = -m.s * px + m.c * py + d.xiG[1];
+    const double R = 2.0 * (fabs(m.c) + fabs(m.s)) + 1e-6;
+    const int i0 = max(0, (int)ceil(ic - R)), i1 = min(d.L[0] - 1, (int)floor(ic + R));
+    const int j0 = max(0, (int)ceil(jc - R)), j1 = min(d.L[1] - 1, (int)floor(jc + R));
+    const T* frac = (const T*)ts.col_frac;
+    int* tidx = ts.tap_idx + col * kMaxTaps;
+    T* tw = (T*)ts.tap_w + col * kMaxTaps;
+    int cnt = 0;
+    T m0 = (T)0, m1x = (T)0, m1y = (T)0;
+    for (int j = j0; j <= j1; ++j)
+        for (int i = i0; i <= i1; ++i) {
+            const long long k = (long long)j * d.L[0] + i;
+            const T rx = (T)(x - ts.col_base[2 * k]) - frac[2 * k];
+            const T ry = (T)(y - ts.col_base[2 * k + 1]) - frac[2 * k + 1];
+            if (!(fabs((double)rx) < 2.0 && fabs((double)ry) < 2.0)) continue;
+            const T W = peskin(rx) * peskin(ry);
+            if (W == (T)0) continue;
+            if (cnt == kMaxTaps) {
+                atomicOr(ts.err, 1);
+                break;
+            }
+            tidx[cnt] = (int)k;
+            tw[cnt] = W;
+            ++cnt;
+            m0 += W;
+            m1x += W * (T)(i - d.xiG[0]);
+            m1y += W * (T)(j - d.xiG[1]);
+        }
+    ts.tap_cnt[col] = cnt;
+    T* cm = (T*)ts.col_m + 3 * col;
+    cm[0] = m0;
+    cm[1] = m1x;
+    cm[2] = m1y;
+}
+
+template <class T>
+__global__ void k_fill(Design d, Geom g, Motion m, TransferScratch ts,
+                       const T* __restrict__ kref, V4<T>* __restrict__ kus) {
+    long long bi = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (bi >= g.boxN) return;
+    const long long ncols = (long long)g.bn[0] * g.bn[1];
+    const long long col = bi % ncols;
+    const int bz = (int)(bi / ncols);
+    const int cnt = ts.tap_cnt[col];
+    const int* tidx = ts.tap_idx + col * kMaxTaps;
+    const T* tw = (const T*)ts.tap_w + col * kMaxTaps;
+    const int* zi = ts.zt_idx + 4 * bz;
+    const T* zw = (const T*)ts.zt_w + 4 * bz;
+    T kap = (T)0, mz = (T)0;
+    for (int t = 0; t < 4; ++t) {
+        const int zeta = zi[t];
+        if (zeta < 0) continue;
+        const T wz = zw[t];
+        mz += wz;
+        const T* kp = kref + (long long)zeta * d.ncol;
+        for (int e = 0; e < cnt; ++e) kap += (tw[e] * wz) * kp[tidx[e]];
+    }
+    const T* cm = (const T*)ts.col_m + 3 * col;
+    const T om = (T)m.om, c = (T)m.c, s = (T)m.s;
+    // u_ref is affine in xi (Eq. rigid_body_velocity): sum W u_ref = omega R'(theta) m1 + u_G m0
+    V4<T> o;
+    o.r = kap;
+    o.x = mz * ((-s * cm[1] - c * cm[2]) * om + (T)m.uG[0] * cm[0]);
+    o.y = mz * ((c * cm[1] - s * cm[2]) * om + (T)m.uG[1] * cm[0]);
+    o.z = (g.dim == 3) ? mz * ((T)m.uG[2] * cm[0]) : (T)0;
+    kus[bi] = o;
+}
+
+template <class T>
+__global__ void k_sens(Design d, Geom g, TransferScratch ts, const T* __restrict__ e,
+                       const T* __restrict__ kprime, double* __restrict__ gacc) {
+    long long dn = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (dn >= d.nd) return;
+    const long long k = dn % d.ncol;
+    const int zeta = (int)(dn / d.ncol);
+    const T* frac = (const T*)ts.col_frac;
+    const int bx = ts.col_base[2 * k], by = ts.col_base[2 * k + 1];
+    const T fx = frac[2 * k], fy = frac[2 * k + 1];
+    const int bzz = ts.dz_base[zeta];
+    const T fz = ((const T*)ts.dz_frac)[zeta];
+    T wx[4], wy[4], wz[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        wx[t] = peskin((T)(t - 1) - fx);
+        wy[t] = peskin((T)(t - 1) - fy);
+        wz[t] = (g.dim == 3) ? peskin((T)(t - 1) - fz) : (t == 1 ? (T)1 : (T)0);
+    }
+    T acc = (T)0;
+#pragma unroll
+    for (int tz = 0; tz < 4; ++tz) {
+        if (wz[tz] == (T)0) continue;
+        const int z = (g.dim == 3) ? bzz - 1 + tz : 0;
+#pragma unroll
+        for (int ty = 0; ty < 4; ++ty) {
+            const int y = by - 1 + ty;
+#pragma unroll
+            for (int tx = 0; tx < 4; ++tx) {
+                const T W = (wx[tx] * wy[ty]) * wz[tz];
+                if (W == (T)0) continue;
+                const int x = bx - 1 + tx;
+                const int ex = x - g.blo[0], ey = y - g.blo[1], ez = z - g.blo[2];
+                // the box is the union of all supports; a tap can only fall outside it at
+                // |r| -> 2, where W vanishes, through host/device rounding of x_ref
+                if (ex < 0 || ey < 0 || ez < 0 || ex >= g.bn[0] || ey >= g.bn[1] || ez >= g.bn[2])
+                    continue;
+                acc += W * e[((long long)ez * g.bn[1] + ey) * g.bn[0] + ex];
+            }
+        }
+    }
+    gacc[dn] += (double)kprime[dn] * (double)acc;
+}
+
+template <class T>
+__global__ void k_box_to_grid(Geom g, const V4<T>* __restrict__ kus, double* kappa, double* us) {
+    long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (m >= g.nodes) return;
+    const int x = (int)(m % g.n[0]);
+    const long long t = m / g.n[0];
+    const int y = (int)(t % g.n[1]), z = (int)(t / g.n[1]);
+    long long bi;
+    double k = 0, a = 0, b = 0, c = 0;
+    if (in_box(g, x, y, z, bi)) {
+        const V4<T> v = kus[bi];
+        k = v.r;
+        a = v.x;
+        b = v.y;
+        c = v.z;
+    }
+    kappa[m] = k;
+    us[m] = a;
+    us[g.nodes + m] = b;
+    us[2 * g.nodes + m] = c;
+}
+
+}  // namespace
+
+template <class T>
+void launch_design_prep(const Design& d, const double* gamma, double kappa_max, double q,
+                        T* kref, T* kprime, int* bad, cudaStream_t st) {
+    if (d.nd == 0) return;
+    k_design_prep_check<<<grid_for(d.nd), kThreads, 0, st>>>(d.nd, gamma, bad);
+    k_design_prep<T><<<grid_for(d.nd), kThreads, 0, st>>>(d.nd, gamma, kappa_max, q, kref, kprime);
+}
+
+template <class T>
+void launch_design_pos(const Design& d, const Geom& g, const Motion& m, TransferScratch ts,
+                       cudaStream_t st) {
+    if (d.nd == 0 || g.boxN == 0) return;
+    const long long n = d.ncol + d.L[2] + g.bn[2];
+    k_design_pos<T><<<grid_for(n), kThreads, 0, st>>>(d, g, m, ts);
+}
+
+template <class T>
+void launch_transfer(const Design& d, const Geom& g, const Motion& m, TransferScratch ts,
+                     const T* kref, V4<T>* kus, cudaStream_t st) {
+    if (d.nd == 0 || g.boxN == 0) return;
+    const long long ncols = (long long)g.bn[0] * g.bn[1];
+    k_tap_lists<T><<<grid_for(ncols), kThreads, 0, st>>>(d, g, m, ts);
+    k_fill<T><<<grid_for(g.boxN), kThreads, 0, st>>>(d, g, m, ts, kref, kus);
+}
+
+template <class T>
+void launch_sens(const Design& d, const Geom& g, TransferScratch ts, const T* e,
+                 const T* kprime, double* gacc, cudaStream_t st) {
+    if (d.nd == 0 || g.boxN == 0) return;
+    k_sens<T><<<grid_for(d.nd), kThreads, 0, st>>>(d, g, ts, e, kprime, gacc);
+}
+
+template <class T>
+void launch_box_to_grid(const Geom& g, const V4<T>* kus, double* kappa, double* us,
+                        cudaStream_t st) {
+    k_box_to_grid<T><<<grid_for(g.nodes), kThreads, 0, st>>>(g, kus, kappa, us);
+}
+
+#define LKS_INST_T(T)                                                                        \
+    template void launch_design_prep<T>(const Design&, const double*, double, double, T*, T*, \
+                                        int*, cudaStream_t);                                 \
+    template void launch_design_pos<T>(const Design&, const Geom&, const Motion&,             \
+                                       TransferScratch, cudaStream_t);                       \
+    template void launch_transfer<T>(const Design&, const Geom&, const Motion&,               \
+                                     TransferScratch, const T*, V4<T>*, cudaStream_t);       \
+    template void launch_sens<T>(const Design&, const Geom&, TransferScratch, const T*,       \
+                                 const T*, double*, cudaStream_t);                           \
+    template void launch_box_to_grid<T>(const Geom&, const V4<T>*, double*, double*,          \
+                                        cudaStream_t);
+
+LKS_INST_T(float)
+LKS_INST_T(double)
+
+}  // namespace lks

@@ -1,0 +1,243 @@
+"""Python binding of the C ABI in include/lks.h (argument marshalling only).
+
+Every step of the computation runs in liblks_gb300.so; this module only converts arguments.
+PyTorch provides the device workspace (and, optionally, the stream).  If the library is
+missing the import of this module's functions raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Tuple
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblks_gb300.so")
+
+FP32, FP64 = 0, 1
+STATUS = {0: "LKS_OK", 1: "LKS_ERR_ARG", 2: "LKS_ERR_ORDER", 3: "LKS_ERR_NOMEM",
+          4: "LKS_ERR_CUDA", 5: "LKS_ERR_DIVERGED", 6: "LKS_ERR_TIMEOUT"}
+
+# every symbol include/lks.h declares
+EXPORTS = ("lks_workspace_bytes", "lks_create", "lks_set_design", "lks_set_motion",
+           "lks_set_initial_state", "lks_forward", "lks_adjoint", "lks_get_state",
+           "lks_transfer", "lks_get_stats", "lks_checkpoint_schedule", "lks_last_error",
+           "lks_destroy")
+
+
+class LksError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class LksConfig(ctypes.Structure):
+    _fields_ = [
+        ("dim", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+        ("lx", ctypes.c_int), ("ly", ctypes.c_int), ("lz", ctypes.c_int),
+        ("precision", ctypes.c_int), ("max_steps", ctypes.c_int),
+        ("A", ctypes.c_double), ("kappa_max", ctypes.c_double), ("q", ctypes.c_double),
+        ("rho0", ctypes.c_double),
+        ("bc", ctypes.c_int * 6),
+        ("bc_val", (ctypes.c_double * 4) * 6),
+        ("u_init", ctypes.c_double * 3), ("body_force", ctypes.c_double * 3),
+        ("xi_G", ctypes.c_double * 3),
+        ("obj_kind", ctypes.c_int),
+        ("obj_box", ctypes.c_int * 6),
+        ("obj_dir", ctypes.c_double * 3),
+        ("obj_cyl_r", ctypes.c_double), ("obj_cyl_c", ctypes.c_double * 2),
+        ("win_begin", ctypes.c_int), ("win_end", ctypes.c_int),
+        ("ckpt_bytes", ctypes.c_size_t),
+        ("stream", ctypes.c_void_p),
+    ]
+
+
+class LksMotion(ctypes.Structure):
+    _fields_ = [("n_rows", ctypes.c_int), ("rows", ctypes.POINTER(ctypes.c_double))]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load liblks_gb300.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with paper_2506_23895_gb300/build.py")
+    lib = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    D = ctypes.POINTER(ctypes.c_double)
+    lib.lks_workspace_bytes.argtypes = [ctypes.POINTER(LksConfig)]
+    lib.lks_workspace_bytes.restype = ctypes.c_size_t
+    lib.lks_create.argtypes = [ctypes.POINTER(LksConfig), P, ctypes.c_size_t, ctypes.POINTER(P)]
+    lib.lks_set_design.argtypes = [P, P, ctypes.c_int]
+    lib.lks_set_motion.argtypes = [P, ctypes.POINTER(LksMotion)]
+    lib.lks_set_initial_state.argtypes = [P, D]
+    lib.lks_forward.argtypes = [P, ctypes.c_int, D]
+    lib.lks_adjoint.argtypes = [P, P, ctypes.c_int]
+    lib.lks_get_state.argtypes = [P, D]
+    lib.lks_transfer.argtypes = [P, ctypes.c_int, D, D]
+    lib.lks_get_stats.argtypes = [P, ctypes.POINTER(ctypes.c_longlong)]
+    lib.lks_checkpoint_schedule.argtypes = [ctypes.c_int, ctypes.c_int,
+                                            ctypes.POINTER(ctypes.c_int), ctypes.c_int]
+    lib.lks_checkpoint_schedule.restype = ctypes.c_int
+    lib.lks_last_error.argtypes = [P]
+    lib.lks_last_error.restype = ctypes.c_char_p
+    lib.lks_destroy.argtypes = [P]
+    lib.lks_destroy.restype = None
+    for name in ("lks_create", "lks_set_design", "lks_set_motion", "lks_set_initial_state",
+                 "lks_forward", "lks_adjoint", "lks_get_state", "lks_transfer", "lks_get_stats"):
+        getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def make_config(problem, precision: int = FP32, max_steps: Optional[int] = None,
+                ckpt_bytes: int = 0, stream: Optional[int] = None) -> LksConfig:
+    """lks_config from a workloads.Problem."""
+    p = problem
+    c = LksConfig()
+    c.dim = p.dim
+    c.nx, c.ny, c.nz = p.n
+    c.lx, c.ly, c.lz = p.L
+    c.precision = precision
+    c.max_steps = p.n_steps if max_steps is None else max_steps
+    c.A, c.kappa_max, c.q, c.rho0 = p.A, p.kappa_max, p.q, p.rho0
+    for f in range(6):
+        c.bc[f] = p.bc[f]
+        for k in range(4):
+            c.bc_val[f][k] = p.bc_val[f][k]
+    for a in range(3):
+        c.u_init[a] = p.u_init[a]
+        c.body_force[a] = p.body_force[a]
+        c.xi_G[a] = p.xi_G[a]
+        c.obj_dir[a] = p.obj_dir[a]
+    c.obj_kind = p.obj_kind
+    for k in range(6):
+        c.obj_box[k] = p.obj_box[k]
+    c.obj_cyl_r = p.obj_cyl_r
+    c.obj_cyl_c[0], c.obj_cyl_c[1] = p.obj_cyl_c
+    c.win_begin, c.win_end = p.win
+    c.ckpt_bytes = ckpt_bytes
+    c.stream = stream
+    return c
+
+
+def checkpoint_schedule(n_segments: int, free_slots: int):
+    """The (kind, a, b) actions of the adjoint's checkpoint schedule (host only)."""
+    lib = load()
+    n = lib.lks_checkpoint_schedule(n_segments, free_slots, None, 0)
+    if n < 0:
+        raise ValueError("bad schedule arguments")
+    buf = (ctypes.c_int * (3 * n))()
+    lib.lks_checkpoint_schedule(n_segments, free_slots, buf, n)
+    return [tuple(buf[3 * i:3 * i + 3]) for i in range(n)]
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+class Solver:
+    """One problem instance on the GPU: set_design, set_motion, forward -> J, adjoint -> dJ/dgamma.
+
+    The device workspace is a torch uint8 tensor owned by this object.
+    """
+
+    def __init__(self, problem, precision: int = FP32, max_steps: Optional[int] = None,
+                 ckpt_bytes: int = 0, stream=None):
+        import torch
+
+        self.lib = load()
+        self.problem = problem
+        self.precision = precision
+        s = None if stream is None else int(stream.cuda_stream if hasattr(stream, "cuda_stream")
+                                              else stream)
+        self.cfg = make_config(problem, precision, max_steps, ckpt_bytes, s)
+        nbytes = self.lib.lks_workspace_bytes(ctypes.byref(self.cfg))
+        if nbytes == 0:
+            raise LksError(1, "invalid configuration")
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        self.ctx = ctypes.c_void_p()
+        st = self.lib.lks_create(ctypes.byref(self.cfg), ctypes.c_void_p(self.workspace.data_ptr()),
+                                 nbytes, ctypes.byref(self.ctx))
+        if st != 0:
+            raise LksError(st, "lks_create failed")
+        self.nd = problem.design_nodes
+        self.design_shape = (1 if problem.dim == 2 else problem.L[2], problem.L[1], problem.L[0])
+        self.state_shape = (4, problem.n[2], problem.n[1], problem.n[0])
+
+    def _check(self, st):
+        if st != 0:
+            raise LksError(st, self.lib.lks_last_error(self.ctx).decode())
+
+    def set_design(self, gamma) -> None:
+        if hasattr(gamma, "is_cuda") and gamma.is_cuda:
+            g = gamma.detach().contiguous().double()
+            self._keep = g
+            self._check(self.lib.lks_set_design(self.ctx, ctypes.c_void_p(g.data_ptr()), 1))
+        else:
+            g = np.ascontiguousarray(np.asarray(gamma, dtype=np.float64))
+            self._check(self.lib.lks_set_design(self.ctx, g.ctypes.data_as(ctypes.c_void_p), 0))
+
+    def set_motion(self, rows) -> None:
+        r = np.ascontiguousarray(np.asarray(rows, dtype=np.float64).reshape(-1, 8))
+        m = LksMotion(r.shape[0], _dptr(r))
+        self._rows = r
+        self._check(self.lib.lks_set_motion(self.ctx, ctypes.byref(m)))
+
+    def set_initial_state(self, state=None) -> None:
+        if state is None:
+            self._check(self.lib.lks_set_initial_state(self.ctx, None))
+        else:
+            s = np.ascontiguousarray(np.asarray(state, dtype=np.float64))
+            assert s.shape == self.state_shape
+            self._check(self.lib.lks_set_initial_state(self.ctx, _dptr(s)))
+
+    def forward(self, n_steps: Optional[int] = None) -> float:
+        n = self.problem.n_steps if n_steps is None else n_steps
+        J = ctypes.c_double(0.0)
+        self._check(self.lib.lks_forward(self.ctx, n, ctypes.byref(J)))
+        return J.value
+
+    def adjoint(self, out=None):
+        """dJ/dgamma into `out` (torch CUDA float64 tensor) or a new numpy array."""
+        if out is not None and hasattr(out, "is_cuda") and out.is_cuda:
+            assert out.dtype.is_floating_point and out.element_size() == 8 and out.is_contiguous()
+            self._check(self.lib.lks_adjoint(self.ctx, ctypes.c_void_p(out.data_ptr()), 1))
+            return out
+        g = np.zeros(self.design_shape, dtype=np.float64)
+        self._check(self.lib.lks_adjoint(self.ctx, g.ctypes.data_as(ctypes.c_void_p), 0))
+        return g
+
+    def get_state(self) -> np.ndarray:
+        s = np.zeros(self.state_shape, dtype=np.float64)
+        self._check(self.lib.lks_get_state(self.ctx, _dptr(s)))
+        return s
+
+    def transfer(self, step: int) -> Tuple[np.ndarray, np.ndarray]:
+        k = np.zeros(self.state_shape[1:], dtype=np.float64)
+        us = np.zeros((3,) + self.state_shape[1:], dtype=np.float64)
+        self._check(self.lib.lks_transfer(self.ctx, step, _dptr(k), _dptr(us)))
+        return k, us
+
+    def stats(self):
+        a = (ctypes.c_longlong * 5)()
+        self._check(self.lib.lks_get_stats(self.ctx, a))
+        return {"forward_steps": a[0], "recomputed_steps": a[1], "snapshot_slots": a[2],
+                "tape_steps": a[3], "launches": a[4]}
+
+    def close(self) -> None:
+        if getattr(self, "ctx", None):
+            self.lib.lks_destroy(self.ctx)
+            self.ctx = None
+            self.workspace = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,112 @@
+"""Host-only checks of the C ABI: the library builds and loads, exports every symbol that
+include/lks.h declares, sizes workspaces, and its checkpoint schedule reverses every segment
+exactly once within the snapshot budget (no GPU needed)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2506_23895_gb300 import build as B
+from paper_2506_23895_gb300 import lks
+from paper_2506_23895_gb300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return lks.load()
+
+
+def declared_symbols():
+    txt = open(os.path.join(ROOT, "include", "lks.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(lks_[a-z_0-9]+)\s*\(", txt)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_symbols()
+    assert len(names) >= 13
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(lks.EXPORTS)
+
+
+def test_workspace_bytes_and_invalid_configs(lib):
+    w = W.small_duct3d()
+    c = lks.make_config(w.problem, lks.FP32)
+    n32 = lib.lks_workspace_bytes(ctypes.byref(c))
+    c64 = lks.make_config(w.problem, lks.FP64)
+    n64 = lib.lks_workspace_bytes(ctypes.byref(c64))
+    assert n32 > 0 and n64 > n32
+    bad = lks.make_config(w.problem, lks.FP32)
+    bad.bc[0] = 0  # periodic on one face only
+    assert lib.lks_workspace_bytes(ctypes.byref(bad)) == 0
+    bad = lks.make_config(w.problem, lks.FP32)
+    bad.nx = 2
+    assert lib.lks_workspace_bytes(ctypes.byref(bad)) == 0
+    bad = lks.make_config(w.problem, lks.FP32)
+    bad.A = 0.8  # non-positive viscosity
+    assert lib.lks_workspace_bytes(ctypes.byref(bad)) == 0
+    # a checkpoint budget caps the snapshot pool
+    big = lks.make_config(W.config(4).problem, lks.FP32)
+    full = lib.lks_workspace_bytes(ctypes.byref(big))
+    assert full < 100 * 2 ** 30  # two-level minimum, not 20001 snapshots
+    big.ckpt_bytes = 8 * 2 ** 30
+    assert lib.lks_workspace_bytes(ctypes.byref(big)) < full
+
+
+def simulate(actions, n_seg, free_slots):
+    """Replay a schedule; return the reversed order and the number of segment advances."""
+    stored = {0}
+    slots = 0
+    work = None
+    reversed_order = []
+    advances = 0
+    taped = None
+    for kind, a, b in actions:
+        if kind == 0:      # restore
+            assert a in stored
+            work = a
+        elif kind == 1:    # advance a -> b
+            assert work == a and b > a
+            advances += b - a
+            work = b
+        elif kind == 2:    # store
+            assert work == a and a not in stored
+            stored.add(a)
+            slots += 1
+            assert slots <= free_slots
+        elif kind == 3:    # free
+            stored.remove(a)
+            slots -= 1
+        elif kind == 4:    # tape segment a
+            assert work == a
+            advances += 1
+            taped = a
+            work = a + 1
+        elif kind == 5:    # adjoint over segment a
+            assert taped == a
+            reversed_order.append(a)
+            taped = None
+    return reversed_order, advances
+
+
+@pytest.mark.parametrize("n_seg,slots", [(1, 0), (5, 4), (10, 9), (141, 140), (30, 4), (50, 2),
+                                         (12, 0), (200, 6)])
+def test_checkpoint_schedule_reverses_everything_within_budget(lib, n_seg, slots):
+    acts = lks.checkpoint_schedule(n_seg, slots)
+    order, adv = simulate(acts, n_seg, slots)
+    assert order == list(range(n_seg - 1, -1, -1))
+    if slots >= n_seg - 1:
+        assert adv == 2 * n_seg - 1 or n_seg == 1  # one extra pass over all but the last
+    # binomial bound: with s slots and r sweeps, C(s+r, s) segments need at most r advances each
+    from math import comb
+    s = slots
+    if s > 0:
+        r = 1
+        while comb(s + r, s) < n_seg:
+            r += 1
+        assert adv <= (r + 1) * n_seg
