@@ -137,6 +137,16 @@ lks_status lks_transfer(lks_ctx* ctx, int step, double* kappa_out, double* us_ou
  * [2] snapshot slots, [3] tape length (steps per segment), [4] kernel launches. */
 lks_status lks_get_stats(const lks_ctx* ctx, long long* stats5);
 
+/* Time the stencil kernels with CUDA events recorded on the context's stream: the forward
+ * step (everything after the transfer) and the adjoint step (everything but the transfer and
+ * the sensitivity gather), every `stride` steps (0 switches timing off).  Adds two event
+ * records per sampled step. */
+lks_status lks_set_timing(lks_ctx* ctx, int stride);
+
+/* Read and reset the timing: [0] forward-step ms summed, [1] forward samples, [2] adjoint-step
+ * ms summed, [3] adjoint samples.  Synchronises the stream. */
+lks_status lks_read_timing(lks_ctx* ctx, double* out4);
+
 /* The checkpoint schedule the adjoint would follow, as (kind, a, b) triples, for inspection:
  * kind 0 restore a, 1 advance a->b (segment indices), 2 store a, 3 free a, 4 tape a,
  * 5 adjoint a.  Returns the number of triples written (<= cap) or -1 on bad arguments.

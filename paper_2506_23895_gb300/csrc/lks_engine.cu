@@ -113,6 +113,11 @@ struct lks_ctx {
     int work_level = -1;        // step level held by the working buffer (-1 unknown)
     double J = 0.0;
     long long stats[5] = {0, 0, 0, 0, 0};
+    const void* last = nullptr;  // buffer holding the newest forward level
+    // optional event timing of the stencil kernels, sampled every timing_stride steps
+    int timing_stride = 0;
+    std::vector<cudaEvent_t> tev[2];
+    size_t tused[2] = {0, 0};
     std::string err;
 };
 
@@ -316,6 +321,28 @@ V4<T>* st4(void* p) {
     return (V4<T>*)p;
 }
 
+bool timing_begin(lks_ctx* c, int n, int which) {
+    if (c->timing_stride <= 0 || (n % c->timing_stride) != 0) return false;
+    std::vector<cudaEvent_t>& v = c->tev[which];
+    if (c->tused[which] + 2 > v.size()) {
+        cudaEvent_t a, b;
+        if (cudaEventCreate(&a) != cudaSuccess) return false;
+        if (cudaEventCreate(&b) != cudaSuccess) {
+            cudaEventDestroy(a);
+            return false;
+        }
+        v.push_back(a);
+        v.push_back(b);
+    }
+    cudaEventRecord(v[c->tused[which]], c->st);
+    return true;
+}
+
+void timing_end(lks_ctx* c, int which) {
+    cudaEventRecord(c->tev[which][c->tused[which] + 1], c->st);
+    c->tused[which] += 2;
+}
+
 Motion motion_row(const lks_ctx* c, int n) {
     const double* r = c->motion.data() + 8 * (size_t)n;
     Motion m;
@@ -345,10 +372,12 @@ template <class T>
 lks_status forward_step(lks_ctx* c, int n, const void* src, void* dst) {
     lks_status s = transfer_at<T>(c, n);
     if (s != LKS_OK) return s;
+    const bool tm = timing_begin(c, n, 0);
     launch_feq<T>(c->g, (const V4<T>*)src, (T*)c->F, c->st);
     LAUNCHED();
     launch_gather<T>(c->g, (const T*)c->F, (const V4<T>*)c->kus, (V4<T>*)dst, c->st);
     LAUNCHED();
+    if (tm) timing_end(c, 0);
     return LKS_OK;
 }
 
@@ -364,25 +393,31 @@ lks_status copy_state(lks_ctx* c, void* dst, const void* src) {
 
 template <class T>
 lks_status run_steps(lks_ctx* c, int from_level, int to_level, bool with_obj, int tape_seg) {
-    // advance the working buffer from from_level to to_level; optionally record tape levels
+    // Advance from from_level to to_level.  Without a tape the two working buffers alternate;
+    // with a tape (segment tape_seg, whose start level sits in tape slot 0) every level is
+    // written straight into its own tape slot and the working buffer keeps from_level.
     for (int n = from_level + 1; n <= to_level; ++n) {
-        void* src = c->s[c->work];
-        void* dst = c->s[1 - c->work];
+        const void* src;
+        void* dst;
+        if (tape_seg >= 0) {
+            src = slot_ptr(c, tape_slot(c, n - 1 - tape_seg * c->K));
+            dst = slot_ptr(c, tape_slot(c, n - tape_seg * c->K));
+        } else {
+            src = c->s[c->work];
+            dst = c->s[1 - c->work];
+        }
         lks_status s = forward_step<T>(c, n, src, dst);
         if (s != LKS_OK) return s;
-        c->work = 1 - c->work;
+        if (tape_seg < 0) c->work = 1 - c->work;
+        c->last = dst;
         if (with_obj && n >= c->cfg.win_begin && n <= c->cfg.win_end) {
-            launch_objective<T>(c->g, (const V4<T>*)c->s[c->work], c->jstep + n, c->st);
+            launch_objective<T>(c->g, (const V4<T>*)dst, c->jstep + n, c->st);
             LAUNCHED();
-        }
-        if (tape_seg >= 0) {
-            s = copy_state(c, slot_ptr(c, tape_slot(c, n - tape_seg * c->K)), c->s[c->work]);
-            if (s != LKS_OK) return s;
         }
         if (with_obj) ++c->stats[0];
         else ++c->stats[1];
     }
-    c->work_level = to_level;
+    c->work_level = (tape_seg >= 0) ? from_level : to_level;
     return LKS_OK;
 }
 
@@ -436,19 +471,21 @@ lks_status adjoint_step(lks_ctx* c, int n, const void* sn, const void* sp) {
     if (s != LKS_OK) return s;
     V4<T>* lc = st4<T>(c->lam[0]);
     V4<T>* ln = st4<T>(c->lam[1]);
+    const bool tm = timing_begin(c, n, 1);
     launch_adj_bcT<T>(c->g, lc, hn, c->st);
     LAUNCHED();
     launch_adj_mu<T>(c->g, lc, (const V4<T>*)c->kus, (const V4<T>*)sn, st4<T>(c->mu),
                      (T*)c->e, hn, c->st);
     LAUNCHED();
-    if (c->d.nd > 0 && c->g.boxN > 0) {
-        launch_sens<T>(c->d, c->g, c->ts, (const T*)c->e, (const T*)c->kprime, c->gacc, c->st);
-        LAUNCHED();
-    }
     launch_adj_moments<T>(c->g, st4<T>(c->mu), (const V4<T>*)sp, ln, (T*)c->phi, c->st);
     LAUNCHED();
     launch_adj_divT<T>(c->g, (const T*)c->phi, ln, c->st);
     LAUNCHED();
+    if (tm) timing_end(c, 1);
+    if (c->d.nd > 0 && c->g.boxN > 0) {
+        launch_sens<T>(c->d, c->g, c->ts, (const T*)c->e, (const T*)c->kprime, c->gacc, c->st);
+        LAUNCHED();
+    }
     std::swap(c->lam[0], c->lam[1]);
     return LKS_OK;
 }
@@ -480,7 +517,9 @@ lks_status do_forward(lks_ctx* c, int N) {
     c->stats[4] = 0;
     c->work = 0;
     c->work_level = -1;
+    c->last = nullptr;
     CU(cudaMemsetAsync(c->jstep, 0, (size_t)(c->cfg.max_steps + 2) * 8, c->st));
+    CU(cudaMemsetAsync(c->flags, 0, 64, c->st));
     size_t i = 0;
     for (; i < c->acts.size(); ++i) {
         const Act& a = c->acts[i];
@@ -493,8 +532,7 @@ lks_status do_forward(lks_ctx* c, int N) {
     const int w0 = c->cfg.win_begin, w1 = std::min(c->cfg.win_end, N);
     std::vector<double> js(c->cfg.max_steps + 2, 0.0);
     CU(cudaMemcpyAsync(js.data(), c->jstep, js.size() * 8, cudaMemcpyDeviceToHost, c->st));
-    CU(cudaMemsetAsync(c->flags, 0, 64, c->st));
-    launch_check_state<T>(c->g, (const V4<T>*)c->s[c->work], c->flags + 2, c->st);
+    launch_check_state<T>(c->g, (const V4<T>*)c->last, c->flags + 2, c->st);
     LAUNCHED();
     int fl[4];
     CU(cudaMemcpyAsync(fl, c->flags, sizeof(fl), cudaMemcpyDeviceToHost, c->st));
@@ -800,10 +838,11 @@ lks_status lks_get_state(const lks_ctx* cc, double* out) {
     double* tmp = nullptr;
     const size_t bytes = (size_t)c->g.nodes * 4 * 8;
     CU(cudaMalloc(&tmp, bytes));
+    const void* src = c->last ? c->last : c->s0;
     if (c->prec == LKS_FP64)
-        launch_state_to_f64<double>(c->g, (const V4<double>*)c->s[c->work], tmp, c->st);
+        launch_state_to_f64<double>(c->g, (const V4<double>*)src, tmp, c->st);
     else
-        launch_state_to_f64<float>(c->g, (const V4<float>*)c->s[c->work], tmp, c->st);
+        launch_state_to_f64<float>(c->g, (const V4<float>*)src, tmp, c->st);
     cudaError_t e1 = cudaMemcpyAsync(out, tmp, bytes, cudaMemcpyDeviceToHost, c->st);
     cudaError_t e2 = cudaStreamSynchronize(c->st);
     cudaFree(tmp);
@@ -859,10 +898,36 @@ int lks_checkpoint_schedule(int n_segments, int free_slots, int* triples, int ca
     return (int)acts.size();
 }
 
+lks_status lks_set_timing(lks_ctx* c, int stride) {
+    if (!c || stride < 0) return LKS_ERR_ARG;
+    c->timing_stride = stride;
+    c->tused[0] = c->tused[1] = 0;
+    return LKS_OK;
+}
+
+lks_status lks_read_timing(lks_ctx* c, double* out4) {
+    if (!c || !out4) return LKS_ERR_ARG;
+    CU(cudaStreamSynchronize(c->st));
+    for (int w = 0; w < 2; ++w) {
+        double tot = 0.0;
+        for (size_t i = 0; i + 1 < c->tused[w]; i += 2) {
+            float ms = 0.f;
+            CU(cudaEventElapsedTime(&ms, c->tev[w][i], c->tev[w][i + 1]));
+            tot += ms;
+        }
+        out4[2 * w] = tot;
+        out4[2 * w + 1] = (double)(c->tused[w] / 2);
+        c->tused[w] = 0;
+    }
+    return LKS_OK;
+}
+
 const char* lks_last_error(const lks_ctx* c) { return c ? c->err.c_str() : "null context"; }
 
 void lks_destroy(lks_ctx* c) {
     if (!c) return;
+    for (int w = 0; w < 2; ++w)
+        for (cudaEvent_t e : c->tev[w]) cudaEventDestroy(e);
     if (c->own_ws && c->ws) cudaFree(c->ws);
     delete c;
 }

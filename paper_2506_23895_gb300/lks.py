@@ -22,8 +22,8 @@ STATUS = {0: "LKS_OK", 1: "LKS_ERR_ARG", 2: "LKS_ERR_ORDER", 3: "LKS_ERR_NOMEM",
 # every symbol include/lks.h declares
 EXPORTS = ("lks_workspace_bytes", "lks_create", "lks_set_design", "lks_set_motion",
            "lks_set_initial_state", "lks_forward", "lks_adjoint", "lks_get_state",
-           "lks_transfer", "lks_get_stats", "lks_checkpoint_schedule", "lks_last_error",
-           "lks_destroy")
+           "lks_transfer", "lks_get_stats", "lks_set_timing", "lks_read_timing",
+           "lks_checkpoint_schedule", "lks_last_error", "lks_destroy")
 
 
 class LksError(RuntimeError):
@@ -81,6 +81,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.lks_get_state.argtypes = [P, D]
     lib.lks_transfer.argtypes = [P, ctypes.c_int, D, D]
     lib.lks_get_stats.argtypes = [P, ctypes.POINTER(ctypes.c_longlong)]
+    lib.lks_set_timing.argtypes = [P, ctypes.c_int]
+    lib.lks_read_timing.argtypes = [P, D]
     lib.lks_checkpoint_schedule.argtypes = [ctypes.c_int, ctypes.c_int,
                                             ctypes.POINTER(ctypes.c_int), ctypes.c_int]
     lib.lks_checkpoint_schedule.restype = ctypes.c_int
@@ -89,7 +91,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.lks_destroy.argtypes = [P]
     lib.lks_destroy.restype = None
     for name in ("lks_create", "lks_set_design", "lks_set_motion", "lks_set_initial_state",
-                 "lks_forward", "lks_adjoint", "lks_get_state", "lks_transfer", "lks_get_stats"):
+                 "lks_forward", "lks_adjoint", "lks_get_state", "lks_transfer", "lks_get_stats",
+                 "lks_set_timing", "lks_read_timing"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -166,6 +169,7 @@ class Solver:
                                  nbytes, ctypes.byref(self.ctx))
         if st != 0:
             raise LksError(st, "lks_create failed")
+        self._f64 = torch.float64
         self.nd = problem.design_nodes
         self.design_shape = (1 if problem.dim == 2 else problem.L[2], problem.L[1], problem.L[0])
         self.state_shape = (4, problem.n[2], problem.n[1], problem.n[0])
@@ -175,10 +179,13 @@ class Solver:
             raise LksError(st, self.lib.lks_last_error(self.ctx).decode())
 
     def set_design(self, gamma) -> None:
-        if hasattr(gamma, "is_cuda") and gamma.is_cuda:
-            g = gamma.detach().contiguous().double()
+        if hasattr(gamma, "data_ptr"):  # torch tensor, device or (pinned) host
+            g = gamma.detach()
+            if g.dtype != self._f64 or not g.is_contiguous():
+                g = g.contiguous().double()
             self._keep = g
-            self._check(self.lib.lks_set_design(self.ctx, ctypes.c_void_p(g.data_ptr()), 1))
+            self._check(self.lib.lks_set_design(self.ctx, ctypes.c_void_p(g.data_ptr()),
+                                                1 if g.is_cuda else 0))
         else:
             g = np.ascontiguousarray(np.asarray(gamma, dtype=np.float64))
             self._check(self.lib.lks_set_design(self.ctx, g.ctypes.data_as(ctypes.c_void_p), 0))
@@ -204,10 +211,12 @@ class Solver:
         return J.value
 
     def adjoint(self, out=None):
-        """dJ/dgamma into `out` (torch CUDA float64 tensor) or a new numpy array."""
-        if out is not None and hasattr(out, "is_cuda") and out.is_cuda:
-            assert out.dtype.is_floating_point and out.element_size() == 8 and out.is_contiguous()
-            self._check(self.lib.lks_adjoint(self.ctx, ctypes.c_void_p(out.data_ptr()), 1))
+        """dJ/dgamma into `out` (a contiguous float64 torch tensor, CUDA or host) or a new
+        numpy array."""
+        if out is not None and hasattr(out, "data_ptr"):
+            assert out.element_size() == 8 and out.is_contiguous()
+            self._check(self.lib.lks_adjoint(self.ctx, ctypes.c_void_p(out.data_ptr()),
+                                             1 if out.is_cuda else 0))
             return out
         g = np.zeros(self.design_shape, dtype=np.float64)
         self._check(self.lib.lks_adjoint(self.ctx, g.ctypes.data_as(ctypes.c_void_p), 0))
@@ -223,6 +232,14 @@ class Solver:
         us = np.zeros((3,) + self.state_shape[1:], dtype=np.float64)
         self._check(self.lib.lks_transfer(self.ctx, step, _dptr(k), _dptr(us)))
         return k, us
+
+    def set_timing(self, stride: int) -> None:
+        self._check(self.lib.lks_set_timing(self.ctx, stride))
+
+    def read_timing(self):
+        a = (ctypes.c_double * 4)()
+        self._check(self.lib.lks_read_timing(self.ctx, a))
+        return {"fwd_ms": a[0], "fwd_n": int(a[1]), "adj_ms": a[2], "adj_n": int(a[3])}
 
     def stats(self):
         a = (ctypes.c_longlong * 5)()

@@ -274,7 +274,7 @@ def small_channel2d(nx: int = 24, ny: int = 20, LD: int = 8, n_steps: int = 40,
         obj_kind=obj_kind, obj_box=box, obj_dir=(1.0, 0.0, 0.0),
         win=(max(1, n_steps // 2), n_steps), n_steps=n_steps, name="small2d")
     m = motion_table(n_steps, (cx, cy, 0.0), omega=omega, trans_amp=trans_amp,
-                     trans_period=max(8.0, n_steps / 1.5), trans_axis=1, theta0=0.3)
+                     trans_period=max(60.0, n_steps / 1.5), trans_axis=1, theta0=0.3)
     g = make_gamma((LD, LD, 1), 1.0, seed)
     return Workload(p, g, m)
 
@@ -298,7 +298,7 @@ def small_duct3d(nx: int = 16, ny: int = 15, nz: int = 16, LD: int = 5, n_steps:
         obj_cyl_r=2.5 if obj_kind == OBJ_VELOCITY else 0.0, obj_cyl_c=(cx, cy),
         win=(max(1, n_steps // 2), n_steps), n_steps=n_steps, name="small3d")
     m = motion_table(n_steps, (cx, cy, cz + 0.25), omega=omega, trans_amp=trans_amp,
-                     trans_period=max(8.0, n_steps / 1.5), trans_axis=1, theta0=0.2)
+                     trans_period=max(40.0, n_steps / 1.5), trans_axis=1, theta0=0.2)
     g = make_gamma((LD, LD, LD), 1.0, seed)
     return Workload(p, g, m)
 

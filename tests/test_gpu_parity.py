@@ -53,9 +53,9 @@ CASES = {
     "small3d_J2": lambda: W.small_duct3d(),
     "small3d_J1": lambda: W.small_duct3d(obj_kind=W.OBJ_PRESSURE, n_steps=18, seed=22),
     "ragged2d": lambda: W.small_channel2d(nx=70, ny=45, LD=16, n_steps=60, omega=0.01,
-                                          trans_amp=3.0, seed=31),
+                                          trans_amp=1.5, seed=31),
     "ragged3d": lambda: W.small_duct3d(nx=37, ny=29, nz=33, LD=9, n_steps=20, omega=0.01,
-                                       trans_amp=2.0, seed=32),
+                                       trans_amp=1.0, seed=32),
 }
 
 
@@ -102,7 +102,7 @@ def test_periodic_box_with_moving_body(L):
     p.obj_box = (0, 39, 0, 4, 0, 0)
     p.win = (10, 30)
     p.u_init = (0.02, 0.01, 0.0)
-    mot = W.motion_table(steps, (19.2, 16.7, 0.0), omega=0.04, trans_amp=2.0, trans_period=20.0,
+    mot = W.motion_table(steps, (19.2, 16.7, 0.0), omega=0.04, trans_amp=1.5, trans_period=60.0,
                          trans_axis=0, theta0=0.3)
     w = W.Workload(p, W.make_gamma(Ld, 1.0, 8), mot)
     Jg, go = oracle.gradient(p, w.gamma, mot)
