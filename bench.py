@@ -1,0 +1,378 @@
+#!/usr/bin/env python
+"""Forward+adjoint throughput of the LKS / moving-design-grid / discrete-adjoint path on one GB300.
+
+Workload (default): the 3D D3Q15 256^3 duct with a 96^3 design grid rotating about the flow
+axis and translating sinusoidally, 20000 time steps, FP32 state with FP64 objective and
+sensitivity accumulation, binomial checkpointing with forward recomputation.  One bench "step"
+is one full pass of the path: set_design -> forward (Alg. 1, J) -> adjoint (dJ/dgamma).
+MLUPS counts analysis node updates once per time step (nodes * time steps / s / 1e6).
+
+Also reported: the forward-only rate, the plain FP64 GPU path on the same grid over a shorter
+horizon with the FP32-vs-FP64 errors on J and dJ/dgamma, the forward-step kernel against the
+measured HBM copy bandwidth, the end-to-end rate through the public API with host buffers, the
+single-thread FP64 CPU oracle on a bounded sample, and SM clocks during the timed region.
+
+`--impl reference` times the CPU oracle (the method's plain FP64 restatement) as the
+reference arm on bounded samples of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "forward+adjoint MLUPS and % HBM roofline, FP32 vs FP64, at <=1e-4 sensitivity err"
+UNIT = "MLUPS"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--horizon", type=int, default=None,
+                    help="time steps per pass (default: the workload's full horizon)")
+    ap.add_argument("--fp64-horizon", type=int, default=60)
+    ap.add_argument("--timing-stride", type=int, default=8)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_sources_sha1():
+    h = hashlib.sha1()
+    csrc = os.path.join(ROOT, "paper_2506_23895_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(f.read())
+    return h.hexdigest()
+
+
+def ncu_traffic(kernel_key):
+    """DRAM bytes per launch from the committed ncu summary, if taken on the current sources."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    if d.get("kernel_sources_sha1") != kernel_sources_sha1():
+        return None
+    v = d.get(kernel_key)
+    return None if v is None else float(v)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.idx)],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(workload_idx, n_steps=2):
+    """The FP64 oracle, single thread, on a bounded sample of the workload."""
+    import oracle
+    from paper_2506_23895_gb300 import workloads as W
+
+    oracle.build()
+    w = W.config(workload_idx, n_steps=n_steps)
+    t0 = time.perf_counter()
+    oracle.gradient(w.problem, w.gamma, w.motion)
+    dt = time.perf_counter() - t0
+    nodes = w.problem.nodes
+    return {"value": nodes * n_steps / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{w.problem.name}: full {w.problem.n[0]}x{w.problem.n[1]}x{w.problem.n[2]}"
+                      f" grid and design, {n_steps} time steps forward + exact adjoint,"
+                      f" single-thread FP64 C++ (-O2), {dt:.1f} s"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2506_23895_gb300 import workloads as W
+
+    oracle.build()
+    w = W.config(4, n_steps=1)
+    nodes = w.problem.nodes
+    for _ in range(args.warmup):
+        oracle.gradient(w.problem, w.gamma, w.motion)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.gradient(w.problem, w.gamma, w.motion)
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    v = nodes * len(times) / tot / 1e6
+    sample = (f"{w.problem.name}: full grid and design, 1 time step forward + exact adjoint"
+              f" per bench step, single-thread FP64 C++ oracle")
+    out = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1000 * tot / len(times),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "impl": "reference",
+           "config": {"workload": "cfg4_3d_256: D3Q15 256^3 duct, 96^3 design rotating about z "
+                                  "+ transverse sinusoid, 20000-step horizon (1-step samples)"},
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2506_23895_gb300 import lks
+    from paper_2506_23895_gb300 import workloads as W
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if ws == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    w = W.config(4, n_steps=args.horizon)
+    p = w.problem
+    H = p.n_steps
+    nodes = p.nodes
+    stream = torch.cuda.current_stream()
+    solver = lks.Solver(p, lks.FP32, stream=stream)
+    solver.set_motion(w.motion)
+    gamma_dev = torch.from_numpy(w.gamma).to(dev)
+    g_dev = torch.empty(w.gamma.shape, dtype=torch.float64, device=dev)
+
+    def one_pass():
+        solver.set_design(gamma_dev)
+        J = solver.forward()
+        solver.adjoint(out=g_dev)
+        return J
+
+    for _ in range(args.warmup):
+        one_pass()
+    torch.cuda.synchronize()
+    barrier()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    solver.set_timing(max(1, min(args.timing_stride, H // 2)))
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * args.steps + 2)]
+    launches = 0
+    torch.cuda.synchronize()
+    barrier()
+    ev[0].record()
+    for k in range(args.steps):
+        solver.set_design(gamma_dev)
+        J = solver.forward()
+        ev[1 + 2 * k].record()
+        solver.adjoint(out=g_dev)
+        ev[2 + 2 * k].record()
+        launches += solver.stats()["launches"] + 2  # + the two design-prep kernels
+    ev[-1].record()
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    tm = solver.read_timing()
+    t_ms = ev[0].elapsed_time(ev[-1])
+    fwd_ms = 0.0
+    prev = ev[0]
+    for k in range(args.steps):
+        fwd_ms += prev.elapsed_time(ev[1 + 2 * k])
+        prev = ev[2 + 2 * k]
+    t_ms = max_over_ranks(t_ms)
+    node_steps = nodes * H
+    value = node_steps * args.steps * ws / (t_ms / 1000.0) / 1e6
+    fwd_mlups = node_steps * args.steps / (fwd_ms / 1000.0) / 1e6
+
+    peak, peak_kind = peaks()
+    bytes_fwd = 32.0 * nodes     # read + write (rho - rho0, u) in FP32: 2 x 16 B per node
+    bytes_adj = 44.0 * nodes     # lam^n in, u^{n-1} in (12 B), lam^{n-1} out
+    fwd_step_ms = tm["fwd_ms"] / max(tm["fwd_n"], 1)
+    adj_step_ms = tm["adj_ms"] / max(tm["adj_n"], 1)
+    ach = bytes_fwd / (fwd_step_ms / 1000.0) / 1e9
+    ach_adj = bytes_adj / (adj_step_ms / 1000.0) / 1e9
+    traffic = ncu_traffic("fwd_step_dram_bytes_per_launch")
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": f"cfg4_3d_256: D3Q15 {p.n[0]}x{p.n[1]}x{p.n[2]} duct, "
+                                  f"{p.L[0]}^3 design rotating about z + transverse sinusoid "
+                                  f"(amp 20, period 2000), {H} time steps, FP32 forward+adjoint",
+                      "time_steps": H, "nodes": nodes, "parallelism": f"replicas x{ws}",
+                      "l2": "state 268 MB per level > 129 MB L2; no flush needed",
+                      "checkpointing": solver.stats()},
+           "forward_mlups": fwd_mlups,
+           "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                        "frac": ach / peak, "traffic": traffic,
+                        "kernel": "forward step (stencil kernels after the transfer)",
+                        "peak_kind": f"{peak_kind} hbm_gbs (copy)",
+                        "algorithmic_bytes_per_launch": bytes_fwd,
+                        "avg_launch_ms": fwd_step_ms, "samples": tm["fwd_n"]},
+           "roofline_adjoint": {"bound": "hbm", "achieved": ach_adj, "peak": peak,
+                                "unit": "GB/s", "frac": ach_adj / peak,
+                                "algorithmic_bytes_per_launch": bytes_adj,
+                                "avg_launch_ms": adj_step_ms, "samples": tm["adj_n"]},
+           "gpu_launches": launches, "clocks": clk, "J": J}
+    solver.set_timing(0)
+
+    # end to end through the public API with pinned host buffers
+    if not args.no_e2e:
+        gamma_pin = torch.from_numpy(w.gamma).pin_memory()
+        g_pin = torch.empty(w.gamma.shape, dtype=torch.float64).pin_memory()
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            solver.set_design(gamma_pin)
+            solver.forward()
+            solver.adjoint(out=g_pin)
+        torch.cuda.synchronize()
+        dt = max_over_ranks(time.perf_counter() - t0)
+        barrier()
+        out["e2e"] = {"value": node_steps * args.steps * ws / dt / 1e6, "unit": UNIT,
+                      "h2d_bytes_per_step": int(w.gamma.nbytes),
+                      "d2h_bytes_per_step": int(w.gamma.nbytes) + 8}
+    solver.close()
+    del solver
+    torch.cuda.empty_cache()
+
+    # plain FP64 GPU path on the same grid over a shorter horizon, with FP32 errors against it
+    if rank == 0 and not args.no_fp64:
+        wh = W.config(4, n_steps=args.fp64_horizon)
+        res = {}
+        for prec in (lks.FP64, lks.FP32):
+            s = lks.Solver(wh.problem, prec, stream=stream)
+            s.set_motion(wh.motion)
+            s.set_design(torch.from_numpy(wh.gamma).to(dev))
+            gout = torch.empty(wh.gamma.shape, dtype=torch.float64, device=dev)
+            s.forward()
+            s.adjoint(out=gout)  # warm-up pass
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            Jh = s.forward()
+            s.adjoint(out=gout)
+            e1.record()
+            torch.cuda.synchronize()
+            res[prec] = (Jh, gout.cpu().numpy(), e0.elapsed_time(e1))
+            s.close()
+            del s
+            torch.cuda.empty_cache()
+        J64, g64, ms64 = res[lks.FP64]
+        J32, g32, ms32 = res[lks.FP32]
+        out["fp64_plain"] = {
+            "value": nodes * args.fp64_horizon / (ms64 / 1000.0) / 1e6, "unit": UNIT,
+            "time_steps": args.fp64_horizon,
+            "fp32_same_horizon": nodes * args.fp64_horizon / (ms32 / 1000.0) / 1e6}
+        out["accuracy_fp32_vs_fp64"] = {
+            "time_steps": args.fp64_horizon,
+            "J_rel": abs(J32 - J64) / abs(J64),
+            "dJdgamma_rel_l2": float(np.linalg.norm(g32 - g64) / np.linalg.norm(g64)),
+            "tolerance": {"J_rel": 1e-5, "dJdgamma_rel_l2": 1e-4}}
+    if rank == 0:
+        if ws == 1 and not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline(4, n_steps=2)
+        print(json.dumps(out), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -86,7 +86,11 @@ typedef struct {
     size_t ckpt_bytes;       /* device bytes for adjoint snapshots; 0 = full history if it
                                 fits in 8 GB, else the minimum of a two-level scheme */
     void* stream;            /* cudaStream_t for all work; NULL = legacy default stream */
+    int flags;               /* LKS_FLAG_* bits; 0 normally */
 } lks_config;
+
+/* Run every step on the plain per-node kernels even where the fused FP32 3D step applies. */
+#define LKS_FLAG_PLAIN_KERNELS 1
 
 /* Prescribed rigid motion, rows n = 0..n_rows-1 for time t_n = n (Delta t = 1).
  * Each row: theta, omega, xG[3], uG[3] (8 doubles, host memory, copied).  In 3D the rotation
@@ -132,6 +136,9 @@ lks_status lks_get_state(const lks_ctx* ctx, double* state_out);
 /* Evaluate the transfer alone at step n of the motion schedule: kappa (nodes doubles) and
  * u_S (3 planes) on the whole analysis grid, host memory. */
 lks_status lks_transfer(lks_ctx* ctx, int step, double* kappa_out, double* us_out);
+
+/* 1 if forward steps of this context run the fused FP32 D3Q15 kernel, else 0. */
+int lks_uses_fused(const lks_ctx* ctx);
 
 /* Counters of the last forward+adjoint: [0] forward steps, [1] recomputed steps,
  * [2] snapshot slots, [3] tape length (steps per segment), [4] kernel launches. */

@@ -114,6 +114,7 @@ struct lks_ctx {
     double J = 0.0;
     long long stats[5] = {0, 0, 0, 0, 0};
     const void* last = nullptr;  // buffer holding the newest forward level
+    bool fused3d = false;        // FP32 3D non-periodic: one fused kernel per forward step
     // optional event timing of the stencil kernels, sampled every timing_stride steps
     int timing_stride = 0;
     std::vector<cudaEvent_t> tev[2];
@@ -373,10 +374,17 @@ lks_status forward_step(lks_ctx* c, int n, const void* src, void* dst) {
     lks_status s = transfer_at<T>(c, n);
     if (s != LKS_OK) return s;
     const bool tm = timing_begin(c, n, 0);
-    launch_feq<T>(c->g, (const V4<T>*)src, (T*)c->F, c->st);
-    LAUNCHED();
-    launch_gather<T>(c->g, (const T*)c->F, (const V4<T>*)c->kus, (V4<T>*)dst, c->st);
-    LAUNCHED();
+    if (sizeof(T) == 4 && c->fused3d) {
+        cudaError_t e = launch_fused_step3d(c->g, (const V4<float>*)src, (const V4<float>*)c->kus,
+                                            (V4<float>*)dst, c->flags + 3, c->st);
+        if (e != cudaSuccess) return fail(c, LKS_ERR_CUDA, "fused step: %s", cudaGetErrorString(e));
+        ++c->stats[4];
+    } else {
+        launch_feq<T>(c->g, (const V4<T>*)src, (T*)c->F, c->st);
+        LAUNCHED();
+        launch_gather<T>(c->g, (const T*)c->F, (const V4<T>*)c->kus, (V4<T>*)dst, c->st);
+        LAUNCHED();
+    }
     if (tm) timing_end(c, 0);
     return LKS_OK;
 }
@@ -538,6 +546,8 @@ lks_status do_forward(lks_ctx* c, int N) {
     CU(cudaMemcpyAsync(fl, c->flags, sizeof(fl), cudaMemcpyDeviceToHost, c->st));
     CU(cudaStreamSynchronize(c->st));
     if (fl[1]) return fail(c, LKS_ERR_ARG, "transfer tap list overflow");
+    if (fl[3] & 8) return fail(c, LKS_ERR_TIMEOUT, "a tensor-copy wait timed out in the fused step");
+    if (fl[3]) return fail(c, LKS_ERR_CUDA, "fused step reported error %d", fl[3]);
     if (fl[2]) return fail(c, LKS_ERR_DIVERGED, "state diverged (non-finite or |u| >= 0.5)");
     const double h = 1.0 / (double)(c->cfg.win_end - c->cfg.win_begin + 1);
     double J = 0.0;
@@ -549,6 +559,7 @@ lks_status do_forward(lks_ctx* c, int N) {
 
 template <class T>
 lks_status do_adjoint(lks_ctx* c) {
+    CU(cudaMemsetAsync(c->flags, 0, 64, c->st));
     CU(cudaMemsetAsync(c->lam[0], 0, c->snap_bytes, c->st));
     if (c->d.nd > 0) CU(cudaMemsetAsync(c->gacc, 0, (size_t)c->d.nd * 8, c->st));
     for (size_t i = c->adj_begin - 1; i < c->acts.size(); ++i) {
@@ -564,6 +575,8 @@ lks_status do_adjoint(lks_ctx* c) {
     CU(cudaMemcpyAsync(fl, c->flags, sizeof(fl), cudaMemcpyDeviceToHost, c->st));
     CU(cudaStreamSynchronize(c->st));
     if (fl[1]) return fail(c, LKS_ERR_ARG, "transfer tap list overflow");
+    if (fl[3] & 8) return fail(c, LKS_ERR_TIMEOUT, "a tensor-copy wait timed out in the fused step");
+    if (fl[3]) return fail(c, LKS_ERR_CUDA, "fused step reported error %d", fl[3]);
     return LKS_OK;
 }
 
@@ -684,6 +697,8 @@ lks_status lks_create(const lks_config* cfg, void* workspace, size_t ws_bytes, l
     c->ts.dz_frac = w + L.off[L_DZF];
     c->flags = (int*)(w + L.off[L_FLAGS]);
     c->ts.err = c->flags + 1;
+    c->fused3d = (c->prec == LKS_FP32) && !(cfg->flags & LKS_FLAG_PLAIN_KERNELS) &&
+                 fused3d_eligible(g);
     c->pool = w + L.off[L_POOL];
     c->pool_slots = L.pool_slots;
     c->snap_bytes = L.snap;
@@ -878,6 +893,8 @@ lks_status lks_transfer(lks_ctx* c, int step, double* kappa_out, double* us_out)
         return fail(c, LKS_ERR_CUDA, "transfer copy failed");
     return LKS_OK;
 }
+
+int lks_uses_fused(const lks_ctx* c) { return c && c->fused3d ? 1 : 0; }
 
 lks_status lks_get_stats(const lks_ctx* c, long long* st5) {
     if (!c || !st5) return LKS_ERR_ARG;

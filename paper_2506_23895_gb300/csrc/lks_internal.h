@@ -95,6 +95,11 @@ void launch_adj_divT(const Geom& g, const T* phi, V4<T>* lam_out, cudaStream_t s
 template <class T>
 void launch_check_state(const Geom& g, const V4<T>* s, int* flag, cudaStream_t st);
 
+// Fused FP32 D3Q15 step (non-periodic grids, TMA-fed z-march).
+bool fused3d_eligible(const Geom& g);
+cudaError_t launch_fused_step3d(const Geom& g, const V4<float>* src, const V4<float>* kus,
+                                V4<float>* dst, int* err, cudaStream_t st);
+
 template <class T>
 void launch_design_prep(const Design& d, const double* gamma, double kappa_max, double q,
                         T* kref, T* kprime, int* bad, cudaStream_t st);

@@ -201,13 +201,43 @@ __device__ __forceinline__ void obj_source(const Geom& g, int x, int y, int z, d
 // Transpose of the boundary copies: each interior node adjacent to the boundary collects the
 // copied components of the boundary nodes it sources (WALL/INLET copy rho, OUTLET copies the
 // normal velocity).  Boundary nodes are read only; later kernels treat them as zero.
+// Shell enumeration: slab s (0..5) is the interior layer next to face s (axis s/2, low or
+// high side); a node next to several faces is handled by the first slab that contains it.
+__device__ __forceinline__ bool shell_node(const Geom& g, long long t, int& x, int& y, int& z) {
+    const long long per[3] = {(long long)g.n[1] * g.n[2], (long long)g.n[0] * g.n[2],
+                              (long long)g.n[0] * g.n[1]};
+    int slab = 0;
+    while (slab < 6 && t >= per[slab / 2]) {
+        t -= per[slab / 2];
+        ++slab;
+    }
+    if (slab >= 6) return false;
+    const int a = slab / 2;
+    if (a >= g.dim || g.periodic[a]) return false;
+    const int fixed = (slab & 1) ? g.n[a] - 2 : 1;
+    int c[3];
+    const int b0 = (a == 0) ? 1 : 0, b1 = (a == 2) ? 1 : 2;
+    c[a] = fixed;
+    c[b0] = (int)(t % g.n[b0]);
+    c[b1] = (int)(t / g.n[b0]);
+    // owned by an earlier slab?
+    for (int e = 0; e < slab; ++e) {
+        const int ae = e / 2;
+        if (ae >= g.dim || g.periodic[ae]) continue;
+        if (c[ae] == ((e & 1) ? g.n[ae] - 2 : 1)) return false;
+    }
+    x = c[0];
+    y = c[1];
+    z = c[2];
+    return !is_boundary(g, x, y, z);
+}
+
 template <class T>
 __global__ void k_adj_bcT(Geom g, V4<T>* lam, double h) {
-    long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (m >= g.nodes) return;
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     int x, y, z;
-    node_coords(g, m, x, y, z);
-    if (is_boundary(g, x, y, z)) return;
+    if (!shell_node(g, t, x, y, z)) return;
+    const long long m = node_index(g, x, y, z);
     int ox[3], oy[3], oz[3], sx[3], sy[3], sz[3];
     int nx = bc_axis_options(g, 0, x, ox, sx);
     int ny = bc_axis_options(g, 1, y, oy, sy);
@@ -441,7 +471,9 @@ void launch_objective(const Geom& g, const V4<T>* s, double* jstep, cudaStream_t
 
 template <class T>
 void launch_adj_bcT(const Geom& g, V4<T>* lam, double h, cudaStream_t st) {
-    k_adj_bcT<T><<<grid_for(g.nodes), kThreads, 0, st>>>(g, lam, h);
+    const long long shell = 2LL * ((long long)g.n[1] * g.n[2] + (long long)g.n[0] * g.n[2] +
+                                   (long long)g.n[0] * g.n[1]);
+    k_adj_bcT<T><<<grid_for(shell), kThreads, 0, st>>>(g, lam, h);
 }
 
 template <class T>

@@ -22,7 +22,7 @@ STATUS = {0: "LKS_OK", 1: "LKS_ERR_ARG", 2: "LKS_ERR_ORDER", 3: "LKS_ERR_NOMEM",
 # every symbol include/lks.h declares
 EXPORTS = ("lks_workspace_bytes", "lks_create", "lks_set_design", "lks_set_motion",
            "lks_set_initial_state", "lks_forward", "lks_adjoint", "lks_get_state",
-           "lks_transfer", "lks_get_stats", "lks_set_timing", "lks_read_timing",
+           "lks_transfer", "lks_uses_fused", "lks_get_stats", "lks_set_timing", "lks_read_timing",
            "lks_checkpoint_schedule", "lks_last_error", "lks_destroy")
 
 
@@ -50,7 +50,11 @@ class LksConfig(ctypes.Structure):
         ("win_begin", ctypes.c_int), ("win_end", ctypes.c_int),
         ("ckpt_bytes", ctypes.c_size_t),
         ("stream", ctypes.c_void_p),
+        ("flags", ctypes.c_int),
     ]
+
+
+FLAG_PLAIN_KERNELS = 1
 
 
 class LksMotion(ctypes.Structure):
@@ -81,6 +85,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.lks_get_state.argtypes = [P, D]
     lib.lks_transfer.argtypes = [P, ctypes.c_int, D, D]
     lib.lks_get_stats.argtypes = [P, ctypes.POINTER(ctypes.c_longlong)]
+    lib.lks_uses_fused.argtypes = [P]
+    lib.lks_uses_fused.restype = ctypes.c_int
     lib.lks_set_timing.argtypes = [P, ctypes.c_int]
     lib.lks_read_timing.argtypes = [P, D]
     lib.lks_checkpoint_schedule.argtypes = [ctypes.c_int, ctypes.c_int,
@@ -99,7 +105,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
 
 
 def make_config(problem, precision: int = FP32, max_steps: Optional[int] = None,
-                ckpt_bytes: int = 0, stream: Optional[int] = None) -> LksConfig:
+                ckpt_bytes: int = 0, stream: Optional[int] = None, flags: int = 0) -> LksConfig:
     """lks_config from a workloads.Problem."""
     p = problem
     c = LksConfig()
@@ -126,6 +132,7 @@ def make_config(problem, precision: int = FP32, max_steps: Optional[int] = None,
     c.win_begin, c.win_end = p.win
     c.ckpt_bytes = ckpt_bytes
     c.stream = stream
+    c.flags = flags
     return c
 
 
@@ -151,7 +158,7 @@ class Solver:
     """
 
     def __init__(self, problem, precision: int = FP32, max_steps: Optional[int] = None,
-                 ckpt_bytes: int = 0, stream=None):
+                 ckpt_bytes: int = 0, stream=None, flags: int = 0):
         import torch
 
         self.lib = load()
@@ -159,7 +166,7 @@ class Solver:
         self.precision = precision
         s = None if stream is None else int(stream.cuda_stream if hasattr(stream, "cuda_stream")
                                               else stream)
-        self.cfg = make_config(problem, precision, max_steps, ckpt_bytes, s)
+        self.cfg = make_config(problem, precision, max_steps, ckpt_bytes, s, flags)
         nbytes = self.lib.lks_workspace_bytes(ctypes.byref(self.cfg))
         if nbytes == 0:
             raise LksError(1, "invalid configuration")
@@ -232,6 +239,10 @@ class Solver:
         us = np.zeros((3,) + self.state_shape[1:], dtype=np.float64)
         self._check(self.lib.lks_transfer(self.ctx, step, _dptr(k), _dptr(us)))
         return k, us
+
+    @property
+    def fused(self) -> bool:
+        return bool(self.lib.lks_uses_fused(self.ctx))
 
     def set_timing(self, stride: int) -> None:
         self._check(self.lib.lks_set_timing(self.ctx, stride))

@@ -33,8 +33,10 @@ def rel_l2(a, b):
     return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
 
 
-def run_gpu(L, w, prec, n=None, ckpt=0, init=None):
-    s = L.Solver(w.problem, prec, ckpt_bytes=ckpt)
+def run_gpu(L, w, prec, n=None, ckpt=0, init=None, flags=0, expect_fused=None):
+    s = L.Solver(w.problem, prec, ckpt_bytes=ckpt, flags=flags)
+    if expect_fused is not None:
+        assert s.fused == expect_fused
     s.set_design(w.gamma)
     s.set_motion(w.motion)
     if init is not None:
@@ -179,3 +181,48 @@ def test_error_paths(L):
     s.forward()
     s.adjoint()
     s.close()
+
+
+MID3D = lambda: W.small_duct3d(nx=70, ny=45, nz=52, LD=14, n_steps=30, omega=0.004,
+                               trans_amp=2.0, seed=33)
+
+
+@pytest.mark.parametrize("name", ["small3d_J2", "small3d_J1", "ragged3d", "mid3d"])
+def test_fused_fp32_step_matches_plain_fp32_and_oracle(L, name):
+    w = MID3D() if name == "mid3d" else CASES[name]()
+    Jf, sf, gf, _ = run_gpu(L, w, L.FP32, expect_fused=True)
+    Jp, sp, gp, _ = run_gpu(L, w, L.FP32, flags=L.FLAG_PLAIN_KERNELS, expect_fused=False)
+    assert abs(Jf - Jp) <= 2e-6 * abs(Jp)
+    assert rel_max(sf, sp) < 1e-5
+    assert rel_l2(gf, gp) < 1e-5
+    Jo, go = oracle.gradient(w.problem, w.gamma, w.motion)
+    assert abs(Jf - Jo) <= 1e-5 * abs(Jo)
+    assert rel_l2(gf, go) < 1e-4
+
+
+def test_fp64_and_2d_use_plain_kernels(L):
+    w = CASES["small3d_J2"]()
+    s = L.Solver(w.problem, L.FP64)
+    assert not s.fused
+    s.close()
+    w2 = CASES["small2d_J1"]()
+    s = L.Solver(w2.problem, L.FP32)
+    assert not s.fused
+    s.close()
+
+
+def test_full_size_256_cube_two_steps_against_oracle(L):
+    """The benchmark's 256^3 grid and 96^3 design (workload 4) in the benchmark's launch
+    configuration, over a two-step horizon the oracle can follow: J, the final state and
+    dJ/dgamma of the fused FP32 path and the plain FP64 path against the oracle."""
+    w = W.config(4, n_steps=2)
+    Jo, fo = oracle.forward(w.problem, w.gamma, w.motion)
+    Jg, go = oracle.gradient(w.problem, w.gamma, w.motion)
+    J64, s64, g64, _ = run_gpu(L, w, L.FP64)
+    assert abs(J64 - Jg) <= 1e-11 * abs(Jg)
+    assert rel_max(s64, fo) < 1e-11
+    assert rel_max(g64, go) < 1e-11
+    J32, s32, g32, _ = run_gpu(L, w, L.FP32, expect_fused=True)
+    assert abs(J32 - Jg) <= 1e-5 * abs(Jg)
+    assert rel_max(s32, fo) < 1e-5
+    assert rel_l2(g32, go) < 1e-4
