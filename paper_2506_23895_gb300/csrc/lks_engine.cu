@@ -93,6 +93,9 @@ struct lks_ctx {
     double* gamma;
     void* kref;
     void* kprime;
+    void* kref_t;
+    void* k2;
+    float* face;
     double* gacc;
     double* jstep;
     TransferScratch ts;
@@ -238,7 +241,7 @@ struct Layout {
 enum {
     L_S0, L_S1, L_SINIT, L_L0, L_L1, L_F, L_MU, L_PHI, L_KUS, L_E, L_GAMMA, L_KREF, L_KPRIME,
     L_GACC, L_JSTEP, L_CBASE, L_CFRAC, L_ZTI, L_ZTW, L_TCNT, L_TIDX, L_TW, L_CM, L_DZB, L_DZF,
-    L_FLAGS, L_POOL, L_COUNT
+    L_FLAGS, L_KREFT, L_K2, L_FACE, L_POOL, L_COUNT
 };
 
 Layout make_layout(const lks_config* cfg) {
@@ -274,6 +277,12 @@ Layout make_layout(const lks_config* cfg) {
     sz[L_DZB] = (size_t)std::max(cfg->lz, 1) * 4;
     sz[L_DZF] = (size_t)std::max(cfg->lz, 1) * T;
     sz[L_FLAGS] = 64;
+    sz[L_KREFT] = (size_t)std::max(nd, 1LL) * T;
+    sz[L_K2] = nd ? (size_t)cols * std::max(cfg->lz, 1) * T : 0;
+    {
+        const long long n0 = cfg->nx, n1 = cfg->ny, n2 = dim == 3 ? cfg->nz : 1;
+        sz[L_FACE] = (size_t)6 * (n1 * n2 + n0 * n2 + n0 * n1) * 4;
+    }
     // snapshot pool
     const long long N = cfg->max_steps;
     long long P;
@@ -363,7 +372,8 @@ lks_status transfer_at(lks_ctx* c, int n) {
     const Motion m = motion_row(c, n);
     launch_design_pos<T>(c->d, c->g, m, c->ts, c->st);
     LAUNCHED();
-    launch_transfer<T>(c->d, c->g, m, c->ts, (const T*)c->kref, st4<T>(c->kus), c->st);
+    launch_transfer<T>(c->d, c->g, m, c->ts, (const T*)c->kref_t, (T*)c->k2, st4<T>(c->kus),
+                       c->st);
     LAUNCHED();
     return LKS_OK;
 }
@@ -482,6 +492,21 @@ lks_status adjoint_step(lks_ctx* c, int n, const void* sn, const void* sp) {
     const bool tm = timing_begin(c, n, 1);
     launch_adj_bcT<T>(c->g, lc, hn, c->st);
     LAUNCHED();
+    if (sizeof(T) == 4 && c->fused3d) {
+        cudaError_t e = launch_fused_adj3d(c->g, (const V4<float>*)lc, (V4<float>*)ln,
+                                           (const V4<float>*)c->kus, (const V4<float>*)sn,
+                                           (const V4<float>*)sp, (float*)c->e, c->face, hn,
+                                           c->flags + 3, c->st);
+        if (e != cudaSuccess) return fail(c, LKS_ERR_CUDA, "fused adjoint: %s", cudaGetErrorString(e));
+        c->stats[4] += 2;
+        if (tm) timing_end(c, 1);
+        if (c->d.nd > 0 && c->g.boxN > 0) {
+            launch_sens<T>(c->d, c->g, c->ts, (const T*)c->e, (const T*)c->kprime, c->gacc, c->st);
+            LAUNCHED();
+        }
+        std::swap(c->lam[0], c->lam[1]);
+        return LKS_OK;
+    }
     launch_adj_mu<T>(c->g, lc, (const V4<T>*)c->kus, (const V4<T>*)sn, st4<T>(c->mu),
                      (T*)c->e, hn, c->st);
     LAUNCHED();
@@ -683,6 +708,9 @@ lks_status lks_create(const lks_config* cfg, void* workspace, size_t ws_bytes, l
     c->gamma = (double*)(w + L.off[L_GAMMA]);
     c->kref = w + L.off[L_KREF];
     c->kprime = w + L.off[L_KPRIME];
+    c->kref_t = w + L.off[L_KREFT];
+    c->k2 = w + L.off[L_K2];
+    c->face = (float*)(w + L.off[L_FACE]);
     c->gacc = (double*)(w + L.off[L_GACC]);
     c->jstep = (double*)(w + L.off[L_JSTEP]);
     c->ts.col_base = (int*)(w + L.off[L_CBASE]);
@@ -731,10 +759,10 @@ lks_status lks_set_design(lks_ctx* c, const double* gamma, int on_device) {
     CU(cudaMemsetAsync(c->flags, 0, 4, c->st));
     if (c->prec == LKS_FP64)
         launch_design_prep<double>(c->d, c->gamma, c->cfg.kappa_max, c->cfg.q, (double*)c->kref,
-                                   (double*)c->kprime, c->flags, c->st);
+                                   (double*)c->kref_t, (double*)c->kprime, c->flags, c->st);
     else
         launch_design_prep<float>(c->d, c->gamma, c->cfg.kappa_max, c->cfg.q, (float*)c->kref,
-                                  (float*)c->kprime, c->flags, c->st);
+                                  (float*)c->kref_t, (float*)c->kprime, c->flags, c->st);
     LAUNCHED();
     if (on_device) {
         int bad = 0;

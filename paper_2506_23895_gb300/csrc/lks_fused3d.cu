@@ -4,7 +4,7 @@
 // of Eq. u_ex_2 and the boundary rules of Eqs. bc_rho, bc_u) in one pass over the state:
 //   * a block owns a 32 x 16 tile of output columns and marches along z over a chunk of planes;
 //   * raw state planes (rho - rho0, u as one float4 per node) with a halo of two cells arrive in
-//     a five-slot shared-memory ring through cp.async.bulk.tensor (TMA) completing on mbarriers;
+//     a seven-slot shared-memory ring through cp.async.bulk.tensor (TMA) completing on mbarriers;
 //     the waits are bounded and a stalled copy sets an error flag instead of hanging;
 //   * every node's f_i^eq is evaluated once, at its source, with the opposite-direction pairs
 //     sharing their symmetric part; the 12 directions that leave the column go through shared
@@ -18,6 +18,7 @@
 #include <algorithm>
 
 #include "lks_device.cuh"
+#include "lks_tma.cuh"
 
 namespace lks {
 
@@ -26,7 +27,7 @@ namespace {
 constexpr int TX = 32, TY = 16;             // output tile
 constexpr int HX = TX + 4, HY = TY + 4;     // raw tile with a two-cell halo
 constexpr int FX = TX + 2, FY = TY + 2;     // f^eq region with a one-cell halo
-constexpr int NSLOT = 5;                    // raw-plane ring depth
+constexpr int NSLOT = 7;                    // raw-plane ring depth (5 planes in flight)
 constexpr int NTHR = TX * TY;               // 512
 constexpr int NHALO = FX * FY - TX * TY;    // 100 extra f^eq nodes on the tile rim
 constexpr int NCROSS = 12;                  // directions leaving the column
@@ -40,45 +41,6 @@ constexpr size_t SMEM_BYTES = OFF_BAR + NSLOT * 8;
 
 // cross-direction slots in sF: 0 +x, 1 -x, 2 +y, 3 -y, 4..7 corners with cz=+1 (sx,sy) =
 // (+,+),(-,+),(+,-),(-,-), 8..11 corners with cz=-1 in the same (sx,sy) order.
-__device__ __forceinline__ int corner_slot(int sx, int sy, int sz) {
-    return (sz > 0 ? 4 : 8) + (sx > 0 ? 0 : 1) + (sy > 0 ? 0 : 2);
-}
-
-__device__ __forceinline__ uint32_t smem_addr(const void* p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
-}
-
-__device__ __forceinline__ void tma_load_plane(uint32_t dst, const CUtensorMap* map, int x, int y,
-                                               int z, uint32_t bar) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
-                 "r"(PLANE_BYTES)
-                 : "memory");
-    asm volatile(
-        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(0), "r"(x), "r"(y), "r"(z), "r"(bar)
-        : "memory");
-}
-
-// Bounded wait on an mbarrier phase: about a second of spinning, then give up.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-    const long long t0 = clock64();
-    while (true) {
-        uint32_t done;
-        asm volatile(
-            "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;"
-            " selp.u32 %0, 1, 0, p; }"
-            : "=r"(done)
-            : "r"(bar), "r"(parity)
-            : "memory");
-        if (done) return true;
-        if (clock64() - t0 > (1LL << 31)) return false;
-    }
-}
 
 struct FusedArgs {
     Geom g;
@@ -90,126 +52,118 @@ struct FusedArgs {
     float A, w0, w1, w2;
 };
 
-// Evaluate f^eq at one node of the f^eq region.  Stores the 12 cross-column values into sF and
-// returns the rest, +z and -z values.
-__device__ __forceinline__ void feq_node(const FusedArgs& a, const float4* __restrict__ rm,
-                                         const float4* __restrict__ r0,
-                                         const float4* __restrict__ rp, float* __restrict__ sF,
-                                         int fx, int fy, int gx, int gy, int gz, float& f_rest,
-                                         float& f_pz, float& f_mz) {
-    const Geom& g = a.g;
-    const int h = (fy + 1) * HX + (fx + 1);
-    const float4 c = r0[h];
-    // D_ab = 2 d u_a / d x_b : central differences, one-sided on boundary nodes
-    float Dx[3], Dy[3], Dz[3];
-    {
-        const float4 e = r0[h + 1], w = r0[h - 1];
-        if (gx == 0) {
-            const float4 e2 = r0[h + 2];
-            Dx[0] = -3.f * c.y + 4.f * e.y - e2.y;
-            Dx[1] = -3.f * c.z + 4.f * e.z - e2.z;
-            Dx[2] = -3.f * c.w + 4.f * e.w - e2.w;
-        } else if (gx == g.n[0] - 1) {
-            const float4 w2 = r0[h - 2];
-            Dx[0] = 3.f * c.y - 4.f * w.y + w2.y;
-            Dx[1] = 3.f * c.z - 4.f * w.z + w2.z;
-            Dx[2] = 3.f * c.w - 4.f * w.w + w2.w;
-        } else {
-            Dx[0] = e.y - w.y;
-            Dx[1] = e.z - w.z;
-            Dx[2] = e.w - w.w;
-        }
+// 2 x first derivative (D = 2 du/dx) of (ux, uy, uz) along one axis from the node c and its
+// neighbours at -1/+1 (and -2/+2 for the one-sided forms).  mode 0: central, 1: one-sided at
+// the low boundary node, 2: one-sided at the high boundary node.
+__device__ __forceinline__ void deriv2(int mode, const float4& c, const float4& m1,
+                                       const float4& p1, const float4& m2, const float4& p2,
+                                       float& dx, float& dy, float& dz) {
+    if (mode == 0) {
+        dx = p1.y - m1.y;
+        dy = p1.z - m1.z;
+        dz = p1.w - m1.w;
+    } else if (mode == 1) {   // -3 c + 4 u(+1) - u(+2)
+        dx = -3.f * c.y + 4.f * p1.y - p2.y;
+        dy = -3.f * c.z + 4.f * p1.z - p2.z;
+        dz = -3.f * c.w + 4.f * p1.w - p2.w;
+    } else {                  // 3 c - 4 u(-1) + u(-2)
+        dx = 3.f * c.y - 4.f * m1.y + m2.y;
+        dy = 3.f * c.z - 4.f * m1.z + m2.z;
+        dz = 3.f * c.w - 4.f * m1.w + m2.w;
     }
-    {
-        const float4 nn = r0[h + HX], ss = r0[h - HX];
-        if (gy == 0) {
-            const float4 n2 = r0[h + 2 * HX];
-            Dy[0] = -3.f * c.y + 4.f * nn.y - n2.y;
-            Dy[1] = -3.f * c.z + 4.f * nn.z - n2.z;
-            Dy[2] = -3.f * c.w + 4.f * nn.w - n2.w;
-        } else if (gy == g.n[1] - 1) {
-            const float4 s2 = r0[h - 2 * HX];
-            Dy[0] = 3.f * c.y - 4.f * ss.y + s2.y;
-            Dy[1] = 3.f * c.z - 4.f * ss.z + s2.z;
-            Dy[2] = 3.f * c.w - 4.f * ss.w + s2.w;
-        } else {
-            Dy[0] = nn.y - ss.y;
-            Dy[1] = nn.z - ss.z;
-            Dy[2] = nn.w - ss.w;
-        }
-    }
-    {
-        const float4 up = rp[h], dn = rm[h];
-        if (gz == 0 || gz == g.n[2] - 1) {
-            // the plane two away is outside the ring: read it from global memory
-            const bool lo = (gz == 0);
-            const int z2 = lo ? 2 : g.n[2] - 3;
-            float4 f2 = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (gx >= 0 && gx < g.n[0] && gy >= 0 && gy < g.n[1])
-                f2 = a.src[((long long)z2 * g.n[1] + gy) * g.n[0] + gx];
-            const float s = lo ? 1.f : -1.f;
-            const float4 n1 = lo ? up : dn;
-            Dz[0] = s * (-3.f * c.y + 4.f * n1.y - f2.y);
-            Dz[1] = s * (-3.f * c.z + 4.f * n1.z - f2.z);
-            Dz[2] = s * (-3.f * c.w + 4.f * n1.w - f2.w);
-        } else {
-            Dz[0] = up.y - dn.y;
-            Dz[1] = up.z - dn.z;
-            Dz[2] = up.w - dn.w;
-        }
+}
+
+// f^eq at one node of the f^eq region (Sec. 2.2): stores the 12 values that leave the column
+// into sF (at sFn = sF + node index, planes FS apart) and returns rest, +z and -z.
+// c0/cm/cp point at the node in planes p, p-1, p+1; zfar is the plane two away for the
+// one-sided z difference (only read when zm != 0).
+template <bool EDGE>
+__device__ __forceinline__ void feq_node(const FusedArgs& a, const float4* __restrict__ c0,
+                                         const float4* __restrict__ cm,
+                                         const float4* __restrict__ cp, float* __restrict__ sFn,
+                                         int xm, int ym, int zm, const float4& zfar,
+                                         float& f_rest, float& f_pz, float& f_mz) {
+    constexpr int FS = FX * FY;
+    const float4 c = c0[0];
+    // Dab = 2 d u_a / d x_b
+    float Dxx, Dyx, Dzx, Dxy, Dyy, Dzy, Dxz, Dyz, Dzz;
+    if (EDGE) {
+        deriv2(xm, c, c0[-1], c0[1], xm == 2 ? c0[-2] : c, xm == 1 ? c0[2] : c, Dxx, Dyx, Dzx);
+        deriv2(ym, c, c0[-HX], c0[HX], ym == 2 ? c0[-2 * HX] : c, ym == 1 ? c0[2 * HX] : c, Dxy,
+               Dyy, Dzy);
+        deriv2(zm, c, cm[0], cp[0], zfar, zfar, Dxz, Dyz, Dzz);
+    } else {
+        const float4 e = c0[1], w = c0[-1], n = c0[HX], s = c0[-HX], u = cp[0], d = cm[0];
+        Dxx = e.y - w.y;
+        Dyx = e.z - w.z;
+        Dzx = e.w - w.w;
+        Dxy = n.y - s.y;
+        Dyy = n.z - s.z;
+        Dzy = n.w - s.w;
+        Dxz = u.y - d.y;
+        Dyz = u.z - d.z;
+        Dzz = u.w - d.w;
     }
     const float A = a.A, hA = 0.5f * a.A;
+    // A S_ab with S = grad u + grad u^T (D is twice the derivative)
+    const float ASxx = A * Dxx, ASyy = A * Dyy, ASzz = A * Dzz;
+    const float ASxy = hA * (Dxy + Dyx);
+    const float ASxz = hA * (Dxz + Dzx);
+    const float ASyz = hA * (Dyz + Dzy);
     const float ux = c.y, uy = c.z, uz = c.w;
-    const float ASxx = A * Dx[0], ASyy = A * Dy[1], ASzz = A * Dz[2];
-    const float ASxy = hA * (Dy[0] + Dx[1]);
-    const float ASxz = hA * (Dz[0] + Dx[2]);
-    const float ASyz = hA * (Dz[1] + Dy[2]);
     const float P = c.x - 1.5f * (ux * ux + uy * uy + uz * uz);
-    const int fi = fy * FX + fx;
-    constexpr int FS = FX * FY;
-    // rest and axes: w (P + 4.5 u_a^2 + A S_aa) +- 3 w u_a
     f_rest = a.w0 * P;
+    // axes: w1 (P + 4.5 u_a^2 + A S_aa) +- 3 w1 u_a
     const float w1 = a.w1, w13 = 3.f * a.w1;
     {
-        const float bx = w1 * (P + 4.5f * ux * ux + ASxx);
-        sF[0 * FS + fi] = bx + w13 * ux;
-        sF[1 * FS + fi] = bx - w13 * ux;
-        const float by = w1 * (P + 4.5f * uy * uy + ASyy);
-        sF[2 * FS + fi] = by + w13 * uy;
-        sF[3 * FS + fi] = by - w13 * uy;
-        const float bz = w1 * (P + 4.5f * uz * uz + ASzz);
-        f_pz = bz + w13 * uz;
-        f_mz = bz - w13 * uz;
+        const float b = w1 * (P + 4.5f * ux * ux + ASxx);
+        sFn[0 * FS] = b + w13 * ux;
+        sFn[1 * FS] = b - w13 * ux;
     }
-    // corners (sx, sy, +1) and their opposites (-sx, -sy, -1)
-    const float w2 = a.w2, w23 = 3.f * a.w2, w245 = 4.5f * a.w2, w2A2 = 2.f * a.w2;
+    {
+        const float b = w1 * (P + 4.5f * uy * uy + ASyy);
+        sFn[2 * FS] = b + w13 * uy;
+        sFn[3 * FS] = b - w13 * uy;
+    }
+    {
+        const float b = w1 * (P + 4.5f * uz * uz + ASzz);
+        f_pz = b + w13 * uz;
+        f_mz = b - w13 * uz;
+    }
+    // corners (sx, sy, +1) and their opposites (-sx, -sy, -1):
+    // w2 [P + A tr S + 4.5 (c.u)^2 + 2 A (sx sy S_xy + sx S_xz + sy S_yz)] +- 3 w2 (c.u)
+    const float w2 = a.w2, w23 = 3.f * a.w2, w245 = 4.5f * a.w2, w2x2 = 2.f * a.w2;
     const float T0 = w2 * (P + ASxx + ASyy + ASzz);
     const float s1 = ux + uy, d1 = ux - uy;
     const float q1 = ASxz + ASyz, q2 = ASyz - ASxz;
     {   // (+,+,+) / (-,-,-)
-        const float cu = s1 + uz, off = ASxy + q1;
-        const float sym = T0 + w245 * cu * cu + w2A2 * off;
-        sF[4 * FS + fi] = sym + w23 * cu;
-        sF[11 * FS + fi] = sym - w23 * cu;
+        const float cu = s1 + uz;
+        const float sym = T0 + w245 * cu * cu + w2x2 * (ASxy + q1);
+        sFn[4 * FS] = sym + w23 * cu;
+        sFn[11 * FS] = sym - w23 * cu;
     }
     {   // (-,+,+) / (+,-,-)
-        const float cu = uz - d1, off = q2 - ASxy;
-        const float sym = T0 + w245 * cu * cu + w2A2 * off;
-        sF[5 * FS + fi] = sym + w23 * cu;
-        sF[10 * FS + fi] = sym - w23 * cu;
+        const float cu = uz - d1;
+        const float sym = T0 + w245 * cu * cu + w2x2 * (q2 - ASxy);
+        sFn[5 * FS] = sym + w23 * cu;
+        sFn[10 * FS] = sym - w23 * cu;
     }
     {   // (+,-,+) / (-,+,-)
-        const float cu = uz + d1, off = -ASxy - q2;
-        const float sym = T0 + w245 * cu * cu + w2A2 * off;
-        sF[6 * FS + fi] = sym + w23 * cu;
-        sF[9 * FS + fi] = sym - w23 * cu;
+        const float cu = uz + d1;
+        const float sym = T0 + w245 * cu * cu - w2x2 * (ASxy + q2);
+        sFn[6 * FS] = sym + w23 * cu;
+        sFn[9 * FS] = sym - w23 * cu;
     }
     {   // (-,-,+) / (+,+,-)
-        const float cu = uz - s1, off = ASxy - q1;
-        const float sym = T0 + w245 * cu * cu + w2A2 * off;
-        sF[7 * FS + fi] = sym + w23 * cu;
-        sF[8 * FS + fi] = sym - w23 * cu;
+        const float cu = uz - s1;
+        const float sym = T0 + w245 * cu * cu + w2x2 * (ASxy - q1);
+        sFn[7 * FS] = sym + w23 * cu;
+        sFn[8 * FS] = sym - w23 * cu;
     }
+}
+
+__device__ __forceinline__ int axis_mode(int gcoord, int n) {
+    return gcoord == 0 ? 1 : (gcoord == n - 1 ? 2 : 0);
 }
 
 __global__ void __launch_bounds__(NTHR, 2)
@@ -219,14 +173,15 @@ __global__ void __launch_bounds__(NTHR, 2)
     float* sF = reinterpret_cast<float*>(smem + OFF_F);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + OFF_BAR);
     const Geom& g = a.g;
+    const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
     const int tid = threadIdx.x;
     const int tx = tid % TX, ty = tid / TX;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const int q0 = blockIdx.z * a.zchunk;
-    const int q1 = min(g.n[2], q0 + a.zchunk);
+    const int q1 = min(nz, q0 + a.zchunk);
     const int nplanes = q1 - q0 + 4;   // raw planes q0-2 .. q1+1
     // rim node handled by this thread (tid < NHALO)
-    int hfx = -1, hfy = -1;
+    int hfx = 0, hfy = 0;
     if (tid < NHALO) {
         if (tid < FX) {
             hfx = tid;
@@ -249,90 +204,133 @@ __global__ void __launch_bounds__(NTHR, 2)
     if (tid == 0) {
         for (int s = 0; s < NSLOT; ++s) mbar_init(smem_addr(&bars[s]));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        for (int k = 0; k < 4 && k < nplanes; ++k)
-            tma_load_plane(smem_addr(raw + (size_t)k * HX * HY), &tmap, x0 - 2, y0 - 2,
-                           q0 - 2 + k, smem_addr(&bars[k]));
+        for (int k = 0; k < NSLOT - 1 && k < nplanes; ++k)
+            tma_load_box(smem_addr(raw + (size_t)k * HX * HY), &tmap, x0 - 2, y0 - 2,
+                         q0 - 2 + k, smem_addr(&bars[k]), PLANE_BYTES);
     }
     __syncthreads();
 
+    // ---- per-thread constants of the column ----
     const int gx = x0 + tx, gy = y0 + ty;
-    const bool col_in = gx < g.n[0] && gy < g.n[1];
-    const bool col_inner = gx >= 1 && gx <= g.n[0] - 2 && gy >= 1 && gy <= g.n[1] - 2;
+    const int hgx = x0 - 1 + hfx, hgy = y0 - 1 + hfy;
+    const bool edge = (x0 - 1 <= 0) || (x0 + TX >= nx - 1) || (y0 - 1 <= 0) || (y0 + TY >= ny - 1);
+    const int pxm = axis_mode(gx, nx), pym = axis_mode(gy, ny);
+    const int rxm = axis_mode(hgx, nx), rym = axis_mode(hgy, ny);
+    const int hp = (ty + 2) * HX + (tx + 2);      // primary node in the raw tile
+    const int hr = (hfy + 1) * HX + (hfx + 1);    // rim node in the raw tile
+    float* sFp = sF + (ty + 1) * FX + (tx + 1);
+    float* sFr = sF + hfy * FX + hfx;
+    const bool has_rim = tid < NHALO;
+    const bool out_col = gx >= 1 && gx <= nx - 2 && gy >= 1 && gy <= ny - 2;
+    const bool bc_col = gx == 1 || gx == nx - 2 || gy == 1 || gy == ny - 2;
+    const int bxx = gx - g.blo[0], byy = gy - g.blo[1];
+    const bool box_col = g.boxN > 0 && bxx >= 0 && byy >= 0 && bxx < g.bn[0] && byy < g.bn[1];
+    const long long box_plane = (long long)g.bn[0] * g.bn[1];
+    const float4* kus_col = a.kus + ((long long)byy * g.bn[0] + bxx) - (long long)g.blo[2] * box_plane;
+    const long long zstride = (long long)nx * ny;
+    const bool in_xy = gx < nx && gy < ny;
+    const bool rim_in_xy = hgx >= 0 && hgx < nx && hgy >= 0 && hgy < ny;
+    float4* out_col_ptr = a.out + ((long long)gy * nx + gx);
+    const int zlo = max(q0, 1), zhi = nz - 2;
+    const float bfx = (float)g.body[0], bfy = (float)g.body[1], bfz = (float)g.body[2];
+
     float acc0[4] = {0.f, 0.f, 0.f, 0.f};  // plane p (c_z = 0 and -1 groups still to come)
     float acc1[4] = {0.f, 0.f, 0.f, 0.f};  // plane p + 1
     constexpr int FS = FX * FY;
-    const int fo = (ty + 1) * FX + (tx + 1);
     bool ok = true;
+    // ring bookkeeping: slot holding plane p-1, p, p+1; next load slot; wait slot/parity
+    int sm = 0, s0 = 1, sp = 2;
+    int wslot = 0, wpar = 0;              // next load to wait for
+    int islot = NSLOT - 1, ik = NSLOT - 1;  // next load to issue: slot and load index
 
     for (int p = q0 - 1; p <= q1; ++p) {
-        const int k_new = p - q0 + 3;  // plane p + 1 must have landed
         bool good = true;
-        if (p == q0 - 1) {
-            for (int k = 0; k <= 2 && good; ++k) good = mbar_wait(smem_addr(&bars[k % NSLOT]), (k / NSLOT) & 1);
-        } else {
-            good = mbar_wait(smem_addr(&bars[k_new % NSLOT]), (k_new / NSLOT) & 1);
+        if (tid == 0) {
+            // refill the slot of plane p-2 (last read before the previous iteration's second
+            // barrier) with plane p + NSLOT - 2
+            if (ik < nplanes) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                tma_load_box(smem_addr(raw + (size_t)islot * HX * HY), &tmap, x0 - 2, y0 - 2,
+                             q0 - 2 + ik, smem_addr(&bars[islot]), PLANE_BYTES);
+            }
+            // first iteration waits for loads 0..2, later ones for the newest plane
+            const int nwait = (p == q0 - 1) ? 3 : 1;
+            for (int i = 0; i < nwait && good; ++i) {
+                good = mbar_wait(smem_addr(&bars[wslot]), wpar);
+                if (++wslot == NSLOT) {
+                    wslot = 0;
+                    wpar ^= 1;
+                }
+            }
         }
         if (__syncthreads_or(!good)) {
             ok = false;
             break;
         }
-        if (tid == 0) {
-            const int k = p - q0 + 5;
-            if (k < nplanes) {
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                tma_load_plane(smem_addr(raw + (size_t)(k % NSLOT) * HX * HY), &tmap, x0 - 2,
-                               y0 - 2, q0 - 2 + k, smem_addr(&bars[k % NSLOT]));
+        ++ik;
+        if (++islot == NSLOT) islot = 0;
+        const float4* rm = raw + (size_t)sm * HX * HY;
+        const float4* r0 = raw + (size_t)s0 * HX * HY;
+        const float4* rp = raw + (size_t)sp * HX * HY;
+        float f_rest, f_pz, f_mz;
+        const int zm = (p == 0) ? 1 : (p == nz - 1 ? 2 : 0);
+        if (!edge && zm == 0) {
+            const float4 z0 = make_float4(0.f, 0.f, 0.f, 0.f);
+            feq_node<false>(a, r0 + hp, rm + hp, rp + hp, sFp, 0, 0, 0, z0, f_rest, f_pz, f_mz);
+            if (has_rim) {
+                float d0, d1, d2;
+                feq_node<false>(a, r0 + hr, rm + hr, rp + hr, sFr, 0, 0, 0, z0, d0, d1, d2);
+            }
+        } else {
+            // plane two away for one-sided z differences, straight from global memory
+            const int z2 = (zm == 1) ? 2 : nz - 3;
+            float4 zf = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (zm != 0 && in_xy) zf = a.src[((long long)z2 * ny + gy) * nx + gx];
+            feq_node<true>(a, r0 + hp, rm + hp, rp + hp, sFp, pxm, pym, zm, zf, f_rest, f_pz,
+                           f_mz);
+            if (has_rim) {
+                float4 zr = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (zm != 0 && rim_in_xy) zr = a.src[((long long)z2 * ny + hgy) * nx + hgx];
+                float d0, d1, d2;
+                feq_node<true>(a, r0 + hr, rm + hr, rp + hr, sFr, rxm, rym, zm, zr, d0, d1, d2);
             }
         }
-        const int km = p - q0 + 1;
-        const float4* rm = raw + (size_t)(km % NSLOT) * HX * HY;
-        const float4* r0 = raw + (size_t)((km + 1) % NSLOT) * HX * HY;
-        const float4* rp = raw + (size_t)((km + 2) % NSLOT) * HX * HY;
-        float f_rest, f_pz, f_mz;
-        feq_node(a, rm, r0, rp, sF, tx + 1, ty + 1, gx, gy, p, f_rest, f_pz, f_mz);
-        if (tid < NHALO) {
-            float d0, d1, d2;
-            feq_node(a, rm, r0, rp, sF, hfx, hfy, x0 - 1 + hfx, y0 - 1 + hfy, p, d0, d1, d2);
-        }
         __syncthreads();
-        // gather the three z-groups of plane p's f^eq into planes p-1, p, p+1
-        const float fpx = sF[0 * FS + fo - 1], fmx = sF[1 * FS + fo + 1];
-        const float fpy = sF[2 * FS + fo - FX], fmy = sF[3 * FS + fo + FX];
-        // corners (sx, sy, sz) come from (x - sx, y - sy)
-        const float cpp_p = sF[4 * FS + fo - 1 - FX], cmp_p = sF[5 * FS + fo + 1 - FX];
-        const float cpm_p = sF[6 * FS + fo - 1 + FX], cmm_p = sF[7 * FS + fo + 1 + FX];
-        const float cpp_m = sF[8 * FS + fo - 1 - FX], cmp_m = sF[9 * FS + fo + 1 - FX];
-        const float cpm_m = sF[10 * FS + fo - 1 + FX], cmm_m = sF[11 * FS + fo + 1 + FX];
+        // gather the three z-groups of plane p's f^eq into planes p-1, p, p+1; a value of
+        // direction c comes from the node at (x - c_x, y - c_y)
+        const float fpx = sFp[0 * FS - 1], fmx = sFp[1 * FS + 1];
+        const float fpy = sFp[2 * FS - FX], fmy = sFp[3 * FS + FX];
+        const float cpp_p = sFp[4 * FS - 1 - FX], cmp_p = sFp[5 * FS + 1 - FX];
+        const float cpm_p = sFp[6 * FS - 1 + FX], cmm_p = sFp[7 * FS + 1 + FX];
+        const float cpp_m = sFp[8 * FS - 1 - FX], cmp_m = sFp[9 * FS + 1 - FX];
+        const float cpm_m = sFp[10 * FS - 1 + FX], cmm_m = sFp[11 * FS + 1 + FX];
         // c_z = -1 group completes plane p-1
         {
             const float sxp = cpp_m + cpm_m, sxm = cmp_m + cmm_m;
             const float syp = cpp_m + cmp_m, sym = cpm_m + cmm_m;
             const float all = sxp + sxm + f_mz;
-            const float r = acc0[0] + all;
-            const float ux = acc0[1] + (sxp - sxm);
-            const float uy = acc0[2] + (syp - sym);
-            const float uz = acc0[3] - all;
             const int qz = p - 1;
-            if (qz >= q0 && col_inner && qz >= 1 && qz <= g.n[2] - 2) {
+            if (out_col && qz >= zlo && qz <= zhi) {
+                const float r = acc0[0] + all;
+                const float ux = acc0[1] + (sxp - sxm) + bfx;
+                const float uy = acc0[2] + (syp - sym) + bfy;
+                const float uz = acc0[3] - all + bfz;
                 float4 o;
                 o.x = r;
-                long long bi;
-                const float bfx = (float)g.body[0], bfy = (float)g.body[1], bfz = (float)g.body[2];
-                if (in_box(g, gx, gy, qz, bi)) {
-                    const float4 ks = a.kus[bi];
+                const int bz = qz - g.blo[2];
+                if (box_col && bz >= 0 && bz < g.bn[2]) {
+                    const float4 ks = kus_col[(long long)qz * box_plane];
                     const float inv = 1.f / (1.f + ks.x);
-                    o.y = (ux + bfx + ks.x * ks.y) * inv;
-                    o.z = (uy + bfy + ks.x * ks.z) * inv;
-                    o.w = (uz + bfz + ks.x * ks.w) * inv;
+                    o.y = fmaf(ks.x, ks.y, ux) * inv;
+                    o.z = fmaf(ks.x, ks.z, uy) * inv;
+                    o.w = fmaf(ks.x, ks.w, uz) * inv;
                 } else {
-                    o.y = ux + bfx;
-                    o.z = uy + bfy;
-                    o.w = uz + bfz;
+                    o.y = ux;
+                    o.z = uy;
+                    o.w = uz;
                 }
-                const long long m = ((long long)qz * g.n[1] + gy) * g.n[0] + gx;
-                a.out[m] = o;
-                if (gx == 1 || gy == 1 || qz == 1 || gx == g.n[0] - 2 || gy == g.n[1] - 2 ||
-                    qz == g.n[2] - 2) {
+                out_col_ptr[(long long)qz * zstride] = o;
+                if (bc_col || qz == 1 || qz == nz - 2) {
                     V4<float> v;
                     v.r = o.x;
                     v.x = o.y;
@@ -356,24 +354,17 @@ __global__ void __launch_bounds__(NTHR, 2)
             acc1[2] = syp - sym;
             acc1[3] = all;
         }
+        sm = s0;
+        s0 = sp;
+        if (++sp == NSLOT) sp = 0;
     }
-    (void)col_in;
     if (!ok) {
         // a copy did not land in time: record it, then give the copies still in flight a
         // bounded chance to finish before the block's shared memory goes away
         if (tid == 0) {
             atomicOr(a.err, 8);
-            for (int s = 0; s < NSLOT; ++s) {
-                uint32_t st;
-                asm volatile(
-                    "{ .reg .pred p; mbarrier.test_wait.parity.shared::cta.b64 p, [%1], 0;"
-                    " selp.u32 %0, 1, 0, p; }"
-                    : "=r"(st)
-                    : "r"(smem_addr(&bars[s]))
-                    : "memory");
-                const long long t0 = clock64();
-                while (clock64() - t0 < (1LL << 28)) {
-                }
+            const long long t0 = clock64();
+            while (clock64() - t0 < (1LL << 28)) {
             }
         }
         __syncthreads();
@@ -400,20 +391,36 @@ bool fused3d_eligible(const Geom& g) {
            g.n[1] >= 3 && g.n[2] >= 4 && get_encode() != nullptr;
 }
 
+// Tensor map over a float4-per-node state array {4, nx, ny, nz} with a {4, bx, by, 1} box;
+// coordinates outside the grid read as zeros.
+bool encode_state_map(CUtensorMap* map, const void* base, const Geom& g, int bx, int by) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = get_encode();
+    if (!enc) return false;
+    cuuint64_t dims[4] = {4, (cuuint64_t)g.n[0], (cuuint64_t)g.n[1], (cuuint64_t)g.n[2]};
+    cuuint64_t strides[3] = {16, (cuuint64_t)g.n[0] * 16, (cuuint64_t)g.n[0] * g.n[1] * 16};
+    cuuint32_t box[4] = {4, (cuuint32_t)bx, (cuuint32_t)by, 1};
+    cuuint32_t estr[4] = {1, 1, 1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void*>(base), dims, strides, box,
+               estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+           CUDA_SUCCESS;
+}
+
+// Planes per z chunk: about three resident waves of two blocks per SM, chunks of >= 16 planes.
+int fused_zchunk(const Geom& g, long long tiles) {
+    int dev = 0, nsm = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    int chunks = (int)std::max(1LL, (6LL * nsm + tiles - 1) / tiles);
+    chunks = std::min(chunks, std::max(1, g.n[2] / 16));
+    return (g.n[2] + chunks - 1) / chunks;
+}
+
 // One fused forward step src -> dst.  Returns a CUDA error code (cudaSuccess on success).
 cudaError_t launch_fused_step3d(const Geom& g, const V4<float>* src, const V4<float>* kus,
                                 V4<float>* dst, int* err, cudaStream_t st) {
-    PFN_cuTensorMapEncodeTiled_v12000 enc = get_encode();
-    if (!enc) return cudaErrorNotSupported;
     CUtensorMap map;
-    cuuint64_t dims[4] = {4, (cuuint64_t)g.n[0], (cuuint64_t)g.n[1], (cuuint64_t)g.n[2]};
-    cuuint64_t strides[3] = {16, (cuuint64_t)g.n[0] * 16, (cuuint64_t)g.n[0] * g.n[1] * 16};
-    cuuint32_t box[4] = {4, HX, HY, 1};
-    cuuint32_t estr[4] = {1, 1, 1, 1};
-    CUresult r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, (void*)src, dims, strides, box,
-                     estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    if (!encode_state_map(&map, src, g, HX, HY)) return cudaErrorInvalidValue;
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(k_fused_step3d,
@@ -433,15 +440,8 @@ cudaError_t launch_fused_step3d(const Geom& g, const V4<float>* src, const V4<fl
     a.w1 = (float)(1.0 / 9.0);
     a.w2 = (float)(1.0 / 72.0);
     const int tiles_x = (g.n[0] + TX - 1) / TX, tiles_y = (g.n[1] + TY - 1) / TY;
-    // z chunks: about three resident waves of two blocks per SM
-    int dev = 0, nsm = 148;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    const long long tiles = (long long)tiles_x * tiles_y;
-    int chunks = (int)std::max(1LL, (6LL * nsm + tiles - 1) / tiles);
-    chunks = std::min(chunks, std::max(1, g.n[2] / 16));
-    a.zchunk = (g.n[2] + chunks - 1) / chunks;
-    chunks = (g.n[2] + a.zchunk - 1) / a.zchunk;
+    a.zchunk = fused_zchunk(g, (long long)tiles_x * tiles_y);
+    const int chunks = (g.n[2] + a.zchunk - 1) / a.zchunk;
     dim3 grid(tiles_x, tiles_y, chunks);
     k_fused_step3d<<<grid, NTHR, SMEM_BYTES, st>>>(map, a);
     return cudaGetLastError();

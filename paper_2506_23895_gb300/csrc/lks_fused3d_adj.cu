@@ -1,0 +1,450 @@
+// Fused D3Q15 adjoint step for the FP32 path on non-periodic grids (exact discrete adjoint of
+// the fused forward step; structure of Alg. 2, Eqs. arho, au, as and the adjoint equilibrium).
+//
+// Input lambda^n has already received the boundary copies (transpose of Eqs. bc_rho, bc_u) on
+// its interior nodes.  Per z plane, a block of 32 x 16 columns:
+//   1. receives lambda^n (float4 per node, two-cell halo) by TMA into a five-slot ring and
+//      converts it in place to mu: 0 on boundary nodes and outside the grid, otherwise
+//      (lambda_rho + d j/d rho, (lambda_u + d j/d u) / (1 + kappa)) -- the transpose of the
+//      Brinkman update (Eq. u_ex_2) -- and, on the tile's nodes inside the footprint box,
+//      e = mu_u . (u_S - u^n), the sensitivity density dJ/dkappa;
+//   2. gathers F~_i(y) = mu_rho(y + c_i) + c_i . mu_u(y + c_i) on the tile and a one-cell rim
+//      into R~ = sum w F~, U~ = sum w c F~, S~ = sum w c c F~ (corner sums by a butterfly);
+//   3. writes lambda^{n-1} = (R~, 3 U~ + 9 S~ u^{n-1} - 3 R~ u^{n-1} + D^T(2 A S~)) for the
+//      tile, with the transposed gradient in its central form; boundary rows' one-sided parts
+//      are added afterwards by k_adj_bcorr from the 2 A S~ values this kernel stores for
+//      boundary nodes.
+// HBM traffic per node: lambda^n in, u^{n-1} in, lambda^{n-1} out (and u^n, kappa, e on the box).
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+
+#include "lks_device.cuh"
+#include "lks_tma.cuh"
+
+namespace lks {
+
+namespace {
+
+constexpr int TX = 32, TY = 16;
+constexpr int HX = TX + 4, HY = TY + 4;     // lambda tile with a two-cell halo
+constexpr int FX = TX + 2, FY = TY + 2;     // moment region with a one-cell halo
+constexpr int NSLOT = 5;
+constexpr int NTHR = TX * TY;
+constexpr int NRIM1 = FX * FY - TX * TY;    // 100 rim nodes of the moment region
+constexpr int NRIM2 = HX * HY - TX * TY;    // 208 halo nodes to convert
+constexpr int NS = 5;                       // S~ components shared in-plane: xx xy xz yy yz
+constexpr unsigned PLANE_BYTES = HX * HY * 16;
+constexpr size_t OFF_RAW = 0;
+constexpr size_t OFF_S = OFF_RAW + (size_t)NSLOT * PLANE_BYTES;
+constexpr size_t OFF_BAR = OFF_S + (size_t)2 * NS * FX * FY * 4;
+constexpr size_t SMEM_BYTES = OFF_BAR + NSLOT * 8;
+
+struct AdjArgs {
+    Geom g;
+    float4* lam_out;
+    const float4* kus;
+    const float4* sn;      // state at level n (u^n for e)
+    const float4* sp;      // state at level n-1
+    float* e;              // footprint box
+    float* face;           // 2 A S~_{.beta} on the six faces
+    long long face_off[6];
+    int* err;
+    int zchunk;
+    float A, w0, w1, w2;
+    float obj_r, obj_u[3]; // d j / d s at target nodes, times the window weight
+};
+
+// Convert lambda to mu at raw-tile slot position v (node gx, gy, gz).  `own` marks a node of the
+// tile: only those write e.
+__device__ __forceinline__ void to_mu(const AdjArgs& a, float4& v, int gx, int gy, int gz,
+                                      bool own) {
+    const Geom& g = a.g;
+    if (gx <= 0 || gy <= 0 || gz <= 0 || gx >= g.n[0] - 1 || gy >= g.n[1] - 1 ||
+        gz >= g.n[2] - 1) {
+        v = make_float4(0.f, 0.f, 0.f, 0.f);   // boundary node or outside the grid
+        return;
+    }
+    float4 l = v;
+    if ((a.obj_r != 0.f || a.obj_u[0] != 0.f || a.obj_u[1] != 0.f || a.obj_u[2] != 0.f) &&
+        in_target(g, gx, gy, gz)) {
+        l.x += a.obj_r;
+        l.y += a.obj_u[0];
+        l.z += a.obj_u[1];
+        l.w += a.obj_u[2];
+    }
+    long long bi;
+    if (in_box(g, gx, gy, gz, bi)) {
+        const float4 ks = a.kus[bi];
+        const float inv = 1.f / (1.f + ks.x);
+        l.y *= inv;
+        l.z *= inv;
+        l.w *= inv;
+        if (own) {
+            const float4 un = a.sn[((long long)gz * g.n[1] + gy) * g.n[0] + gx];
+            a.e[bi] = l.y * (ks.y - un.y) + l.z * (ks.z - un.z) + l.w * (ks.w - un.w);
+        }
+    }
+    v = l;
+}
+
+struct Mom {
+    float R, Ux, Uy, Uz, Sxx, Sxy, Sxz, Syy, Syz, Szz;
+};
+
+// Moments of F~ at one node from mu in planes p-1 (cm), p (c0), p+1 (cp); pointers at the node.
+__device__ __forceinline__ Mom moments(const AdjArgs& a, const float4* __restrict__ c0,
+                                       const float4* __restrict__ cm,
+                                       const float4* __restrict__ cp) {
+    const float4 s = c0[0], xp = c0[1], xm = c0[-1], yp = c0[HX], ym = c0[-HX];
+    const float4 zp = cp[0], zm = cm[0];
+    const float gpx = xp.x + xp.y, gmx = xm.x - xm.y;
+    const float gpy = yp.x + yp.z, gmy = ym.x - ym.z;
+    const float gpz = zp.x + zp.w, gmz = zm.x - zm.w;
+    // corners (sx, sy, sz): F~ = mu_rho + sx mu_x + sy mu_y + sz mu_z at y + (sx, sy, sz)
+    float a_[2][2], b_[2][2];   // [sy>0?0:1][sz>0?0:1]: sums/differences over sx
+#pragma unroll
+    for (int jz = 0; jz < 2; ++jz) {
+        const float4* pl = jz == 0 ? cp : cm;
+        const float sz = jz == 0 ? 1.f : -1.f;
+#pragma unroll
+        for (int jy = 0; jy < 2; ++jy) {
+            const int oy = jy == 0 ? HX : -HX;
+            const float sy = jy == 0 ? 1.f : -1.f;
+            const float4 np = pl[oy + 1], nm = pl[oy - 1];
+            const float base_p = np.x + sy * np.z + sz * np.w;
+            const float base_m = nm.x + sy * nm.z + sz * nm.w;
+            const float gp = base_p + np.y;   // sx = +1
+            const float gm = base_m - nm.y;   // sx = -1
+            a_[jy][jz] = gp + gm;
+            b_[jy][jz] = gp - gm;
+        }
+    }
+    const float Ap = a_[0][0] + a_[1][0], Am = a_[0][1] + a_[1][1];
+    const float Adp = a_[0][0] - a_[1][0], Adm = a_[0][1] - a_[1][1];
+    const float Bp = b_[0][0] + b_[1][0], Bm = b_[0][1] + b_[1][1];
+    const float Bdp = b_[0][0] - b_[1][0], Bdm = b_[0][1] - b_[1][1];
+    const float sG = Ap + Am, szG = Ap - Am, syG = Adp + Adm, syzG = Adp - Adm;
+    const float sxG = Bp + Bm, sxzG = Bp - Bm, sxyG = Bdp + Bdm;
+    const float w0 = a.w0, w1 = a.w1, w2 = a.w2;
+    Mom m;
+    const float ax = gpx + gmx, ay = gpy + gmy, az = gpz + gmz;
+    const float w2G = w2 * sG;
+    m.R = w0 * s.x + w1 * (ax + ay + az) + w2G;
+    m.Ux = w1 * (gpx - gmx) + w2 * sxG;
+    m.Uy = w1 * (gpy - gmy) + w2 * syG;
+    m.Uz = w1 * (gpz - gmz) + w2 * szG;
+    m.Sxx = w1 * ax + w2G;
+    m.Syy = w1 * ay + w2G;
+    m.Szz = w1 * az + w2G;
+    m.Sxy = w2 * sxyG;
+    m.Sxz = w2 * sxzG;
+    m.Syz = w2 * syzG;
+    return m;
+}
+
+__global__ void __launch_bounds__(NTHR, 2)
+    k_fused_adj3d(const __grid_constant__ CUtensorMap tmap, const AdjArgs a) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    float4* raw = reinterpret_cast<float4*>(smem + OFF_RAW);
+    float* sS = reinterpret_cast<float*>(smem + OFF_S);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + OFF_BAR);
+    const Geom& g = a.g;
+    const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+    const int tid = threadIdx.x;
+    const int tx = tid % TX, ty = tid / TX;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int q0 = blockIdx.z * a.zchunk;
+    const int q1 = min(nz, q0 + a.zchunk);
+    const int nplanes = q1 - q0 + 4;   // lambda planes q0-2 .. q1+1
+    if ((smem_addr(smem) & 127u) != 0u) {
+        if (tid == 0) atomicOr(a.err, 16);
+        return;
+    }
+    // halo node to convert (tid < NRIM2), in raw-tile coordinates
+    int cx = 0, cy = 0;
+    if (tid < NRIM2) {
+        if (tid < 2 * HX) {
+            cx = tid % HX;
+            cy = tid / HX;
+        } else if (tid < 4 * HX) {
+            cx = (tid - 2 * HX) % HX;
+            cy = HY - 2 + (tid - 2 * HX) / HX;
+        } else {
+            const int t = tid - 4 * HX;   // 64 nodes: columns 0, 1, HX-2, HX-1 of rows 2..HY-3
+            const int col = t / TY, row = t % TY;
+            cx = col < 2 ? col : HX - 4 + col;
+            cy = 2 + row;
+        }
+    }
+    // rim node of the moment region (tid < NRIM1), in moment-region coordinates
+    int rfx = 0, rfy = 0;
+    if (tid < NRIM1) {
+        if (tid < FX) {
+            rfx = tid;
+            rfy = 0;
+        } else if (tid < 2 * FX) {
+            rfx = tid - FX;
+            rfy = FY - 1;
+        } else if (tid < 2 * FX + TY) {
+            rfx = 0;
+            rfy = 1 + (tid - 2 * FX);
+        } else {
+            rfx = FX - 1;
+            rfy = 1 + (tid - 2 * FX - TY);
+        }
+    }
+    if (tid == 0) {
+        for (int s = 0; s < NSLOT; ++s) mbar_init(smem_addr(&bars[s]));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        for (int k = 0; k < 2 && k < nplanes; ++k)
+            tma_load_box(smem_addr(raw + (size_t)k * HX * HY), &tmap, x0 - 2, y0 - 2,
+                         q0 - 2 + k, smem_addr(&bars[k]), PLANE_BYTES);
+    }
+    __syncthreads();
+
+    const int gx = x0 + tx, gy = y0 + ty;
+    const bool own_in = gx < nx && gy < ny;
+    const int hp = (ty + 2) * HX + (tx + 2);       // own node in the raw tile
+    const int hc = cy * HX + cx;                   // halo node to convert
+    const int hr = (rfy + 1) * HX + (rfx + 1);     // rim node of the moment region
+    constexpr int FS = FX * FY;
+    const int fo = (ty + 1) * FX + (tx + 1);
+    const int fr = rfy * FX + rfx;
+    const long long zstride = (long long)nx * ny;
+    const long long col = (long long)gy * nx + gx;
+    const float A = a.A;
+
+    Mom prev = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    float szm_x = 0.f, szm_y = 0.f, szm_z = 0.f;   // S~_{.z} of plane p-2
+    bool ok = true;
+    int cslot = 0;                 // slot of the plane being converted (k = p - q0 + 3)
+    int wpar = 0;                  // parity of the load in cslot
+    int ik = 2, islot = 2;         // next load to issue
+
+    for (int p = q0 - 3; p <= q1; ++p) {
+        bool good = true;
+        if (tid == 0) good = mbar_wait(smem_addr(&bars[cslot]), wpar);
+        if (__syncthreads_or(!good)) {
+            ok = false;
+            break;
+        }
+        if (tid == 0 && ik < nplanes) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            tma_load_box(smem_addr(raw + (size_t)islot * HX * HY), &tmap, x0 - 2, y0 - 2,
+                         q0 - 2 + ik, smem_addr(&bars[islot]), PLANE_BYTES);
+        }
+        ++ik;
+        if (++islot == NSLOT) islot = 0;
+        // 1. lambda -> mu for plane p + 1
+        {
+            float4* pl = raw + (size_t)cslot * HX * HY;
+            const int gz = p + 1;
+            to_mu(a, pl[hp], gx, gy, gz, own_in);
+            if (tid < NRIM2) to_mu(a, pl[hc], x0 - 2 + cx, y0 - 2 + cy, gz, false);
+        }
+        const int sl_p = cslot;                                   // plane p + 1
+        const int sl_0 = cslot == 0 ? NSLOT - 1 : cslot - 1;      // plane p
+        const int sl_m = sl_0 == 0 ? NSLOT - 1 : sl_0 - 1;        // plane p - 1
+        if (++cslot == NSLOT) {
+            cslot = 0;
+            wpar ^= 1;
+        }
+        __syncthreads();
+        if (p < q0 - 1) continue;
+        // 2. moments of plane p on the tile and its rim
+        const float4* rm = raw + (size_t)sl_m * HX * HY;
+        const float4* r0 = raw + (size_t)sl_0 * HX * HY;
+        const float4* rp = raw + (size_t)sl_p * HX * HY;
+        float* sw = sS + (size_t)(p & 1) * NS * FS;
+        const Mom m = moments(a, r0 + hp, rm + hp, rp + hp);
+        sw[0 * FS + fo] = m.Sxx;
+        sw[1 * FS + fo] = m.Sxy;
+        sw[2 * FS + fo] = m.Sxz;
+        sw[3 * FS + fo] = m.Syy;
+        sw[4 * FS + fo] = m.Syz;
+        if (tid < NRIM1) {
+            const Mom mr = moments(a, r0 + hr, rm + hr, rp + hr);
+            sw[0 * FS + fr] = mr.Sxx;
+            sw[1 * FS + fr] = mr.Sxy;
+            sw[2 * FS + fr] = mr.Sxz;
+            sw[3 * FS + fr] = mr.Syy;
+            sw[4 * FS + fr] = mr.Syz;
+        }
+        // 3. lambda^{n-1} of plane q = p - 1 (its in-plane S~ was stored last iteration)
+        const int q = p - 1;
+        if (q >= q0 && own_in) {
+            const float* sr = sS + (size_t)(q & 1) * NS * FS;
+            const float4 u = a.sp[q * zstride + col];
+            // D^T (2 A S~) in central form: A [S~_a.(x-1) - S~_a.(x+1) + ... ]
+            const float tx_x = sr[0 * FS + fo - 1] - sr[0 * FS + fo + 1];
+            const float tx_y = sr[1 * FS + fo - 1] - sr[1 * FS + fo + 1];
+            const float tx_z = sr[2 * FS + fo - 1] - sr[2 * FS + fo + 1];
+            const float ty_x = sr[1 * FS + fo - FX] - sr[1 * FS + fo + FX];
+            const float ty_y = sr[3 * FS + fo - FX] - sr[3 * FS + fo + FX];
+            const float ty_z = sr[4 * FS + fo - FX] - sr[4 * FS + fo + FX];
+            const float tz_x = szm_x - m.Sxz, tz_y = szm_y - m.Syz, tz_z = szm_z - m.Szz;
+            const Mom& c = prev;
+            float4 o;
+            o.x = c.R;
+            o.y = 3.f * (c.Ux - c.R * u.y) + 9.f * (c.Sxx * u.y + c.Sxy * u.z + c.Sxz * u.w) +
+                  A * (tx_x + ty_x + tz_x);
+            o.z = 3.f * (c.Uy - c.R * u.z) + 9.f * (c.Sxy * u.y + c.Syy * u.z + c.Syz * u.w) +
+                  A * (tx_y + ty_y + tz_y);
+            o.w = 3.f * (c.Uz - c.R * u.w) + 9.f * (c.Sxz * u.y + c.Syz * u.z + c.Szz * u.w) +
+                  A * (tx_z + ty_z + tz_z);
+            a.lam_out[q * zstride + col] = o;
+            // boundary nodes keep 2 A S~_{.beta} for the one-sided parts of D^T
+            const float A2 = 2.f * A;
+            if (gx == 0 || gx == nx - 1) {
+                float* f = a.face + a.face_off[gx == 0 ? 0 : 1] + 3 * ((long long)q * ny + gy);
+                f[0] = A2 * c.Sxx;
+                f[1] = A2 * c.Sxy;
+                f[2] = A2 * c.Sxz;
+            }
+            if (gy == 0 || gy == ny - 1) {
+                float* f = a.face + a.face_off[gy == 0 ? 2 : 3] + 3 * ((long long)q * nx + gx);
+                f[0] = A2 * c.Sxy;
+                f[1] = A2 * c.Syy;
+                f[2] = A2 * c.Syz;
+            }
+            if (q == 0 || q == nz - 1) {
+                float* f = a.face + a.face_off[q == 0 ? 4 : 5] + 3 * col;
+                f[0] = A2 * c.Sxz;
+                f[1] = A2 * c.Syz;
+                f[2] = A2 * c.Szz;
+            }
+        }
+        szm_x = prev.Sxz;
+        szm_y = prev.Syz;
+        szm_z = prev.Szz;
+        prev = m;
+    }
+    if (!ok) {
+        if (tid == 0) {
+            atomicOr(a.err, 8);
+            const long long t0 = clock64();
+            while (clock64() - t0 < (1LL << 28)) {
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// One-sided parts of the transposed gradient on non-periodic axes: node z within two rows of
+// a face gets delta * (2 A S~_{.beta}) of the face node it projects to, with delta = -3/2,
+// +3/2, -1/2 at rows 0, 1, 2 (low face) and +3/2, -3/2, +1/2 at rows n-1, n-2, n-3 (high face):
+// the exact one-sided stencil minus the central one the fused kernel applied.
+__global__ void k_adj_bcorr(Geom g, const float* __restrict__ face, FaceOffsets fo,
+                            float4* __restrict__ lam) {
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    // enumerate slabs of thickness 3 next to each face; a node near several faces is owned by
+    // the first slab containing it
+    const long long per[3] = {3LL * g.n[1] * g.n[2], 3LL * g.n[0] * g.n[2], 3LL * g.n[0] * g.n[1]};
+    long long r = t;
+    int slab = 0;
+    while (slab < 6 && r >= per[slab / 2]) {
+        r -= per[slab / 2];
+        ++slab;
+    }
+    if (slab >= 6) return;
+    const int ax = slab / 2;
+    int c[3];
+    const int b0 = (ax == 0) ? 1 : 0, b1 = (ax == 2) ? 1 : 2;
+    const int layer = (int)(r % 3);
+    const long long rr = r / 3;
+    c[ax] = (slab & 1) ? g.n[ax] - 1 - layer : layer;
+    c[b0] = (int)(rr % g.n[b0]);
+    c[b1] = (int)(rr / g.n[b0]);
+    for (int e = 0; e < slab; ++e) {
+        const int ae = e / 2;
+        const int d = (e & 1) ? g.n[ae] - 1 - c[ae] : c[ae];
+        if (d >= 0 && d <= 2) return;
+    }
+    float sx = 0.f, sy = 0.f, sz = 0.f;
+#pragma unroll
+    for (int f = 0; f < 6; ++f) {
+        const int a = f / 2;
+        const int d = (f & 1) ? g.n[a] - 1 - c[a] : c[a];
+        if (d > 2) continue;
+        const float lo[3] = {-1.5f, 1.5f, -0.5f};
+        const float delta = (f & 1) ? -lo[d] : lo[d];
+        const int e0 = (a == 0) ? 1 : 0, e1 = (a == 2) ? 1 : 2;
+        const float* fp = face + fo.off[f] + 3 * ((long long)c[e1] * g.n[e0] + c[e0]);
+        sx += delta * fp[0];
+        sy += delta * fp[1];
+        sz += delta * fp[2];
+    }
+    const long long m = ((long long)c[2] * g.n[1] + c[1]) * g.n[0] + c[0];
+    float4 v = lam[m];
+    v.y += sx;
+    v.z += sy;
+    v.w += sz;
+    lam[m] = v;
+}
+
+}  // namespace
+
+void face_offsets(const Geom& g, FaceOffsets& fo, long long& total) {
+    long long off = 0;
+    for (int f = 0; f < 6; ++f) {
+        const int a = f / 2;
+        const int e0 = (a == 0) ? 1 : 0, e1 = (a == 2) ? 1 : 2;
+        fo.off[f] = off;
+        off += 3LL * g.n[e0] * g.n[e1];
+    }
+    total = off;
+}
+
+cudaError_t launch_fused_adj3d(const Geom& g, const V4<float>* lam_in, V4<float>* lam_out,
+                               const V4<float>* kus, const V4<float>* sn, const V4<float>* sp,
+                               float* e, float* face, double h, int* err, cudaStream_t st) {
+    CUtensorMap map;
+    if (!encode_state_map(&map, lam_in, g, HX, HY)) return cudaErrorInvalidValue;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t r = cudaFuncSetAttribute(k_fused_adj3d,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)SMEM_BYTES);
+        if (r != cudaSuccess) return r;
+        attr = true;
+    }
+    AdjArgs a;
+    a.g = g;
+    a.lam_out = reinterpret_cast<float4*>(lam_out);
+    a.kus = reinterpret_cast<const float4*>(kus);
+    a.sn = reinterpret_cast<const float4*>(sn);
+    a.sp = reinterpret_cast<const float4*>(sp);
+    a.e = e;
+    a.face = face;
+    FaceOffsets fo;
+    long long tot;
+    face_offsets(g, fo, tot);
+    for (int f = 0; f < 6; ++f) a.face_off[f] = fo.off[f];
+    a.err = err;
+    a.A = (float)g.A;
+    a.w0 = (float)(2.0 / 9.0);
+    a.w1 = (float)(1.0 / 9.0);
+    a.w2 = (float)(1.0 / 72.0);
+    a.obj_r = 0.f;
+    a.obj_u[0] = a.obj_u[1] = a.obj_u[2] = 0.f;
+    if (h != 0.0) {
+        if (g.okind == 0) a.obj_r = (float)(-h / (3.0 * g.ocount));
+        else
+            for (int k = 0; k < 3; ++k) a.obj_u[k] = (float)(-h * g.odir[k] / g.ocount);
+    }
+    const int tiles_x = (g.n[0] + TX - 1) / TX, tiles_y = (g.n[1] + TY - 1) / TY;
+    a.zchunk = fused_zchunk(g, tiles_x * tiles_y);
+    const int chunks = (g.n[2] + a.zchunk - 1) / a.zchunk;
+    k_fused_adj3d<<<dim3(tiles_x, tiles_y, chunks), NTHR, SMEM_BYTES, st>>>(map, a);
+    cudaError_t r = cudaGetLastError();
+    if (r != cudaSuccess) return r;
+    const long long shell = 6LL * ((long long)g.n[1] * g.n[2] + (long long)g.n[0] * g.n[2] +
+                                   (long long)g.n[0] * g.n[1]);
+    k_adj_bcorr<<<(unsigned)((shell + 255) / 256), 256, 0, st>>>(g, face, fo,
+                                                                reinterpret_cast<float4*>(lam_out));
+    return cudaGetLastError();
+}
+
+}  // namespace lks

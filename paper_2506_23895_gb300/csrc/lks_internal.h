@@ -95,20 +95,29 @@ void launch_adj_divT(const Geom& g, const T* phi, V4<T>* lam_out, cudaStream_t s
 template <class T>
 void launch_check_state(const Geom& g, const V4<T>* s, int* flag, cudaStream_t st);
 
-// Fused FP32 D3Q15 step (non-periodic grids, TMA-fed z-march).
+// Fused FP32 D3Q15 step and adjoint step (non-periodic grids, TMA-fed z-march).
+struct FaceOffsets {
+    long long off[6];
+};
 bool fused3d_eligible(const Geom& g);
+int fused_zchunk(const Geom& g, long long tiles);
 cudaError_t launch_fused_step3d(const Geom& g, const V4<float>* src, const V4<float>* kus,
                                 V4<float>* dst, int* err, cudaStream_t st);
+// Offsets of the six face arrays (3 floats per face node) and their total length.
+void face_offsets(const Geom& g, FaceOffsets& fo, long long& total);
+cudaError_t launch_fused_adj3d(const Geom& g, const V4<float>* lam_in, V4<float>* lam_out,
+                               const V4<float>* kus, const V4<float>* sn, const V4<float>* sp,
+                               float* e, float* face, double h, int* err, cudaStream_t st);
 
 template <class T>
 void launch_design_prep(const Design& d, const double* gamma, double kappa_max, double q,
-                        T* kref, T* kprime, int* bad, cudaStream_t st);
+                        T* kref, T* kref_t, T* kprime, int* bad, cudaStream_t st);
 template <class T>
 void launch_design_pos(const Design& d, const Geom& g, const Motion& m, TransferScratch ts,
                        cudaStream_t st);
 template <class T>
 void launch_transfer(const Design& d, const Geom& g, const Motion& m, TransferScratch ts,
-                     const T* kref, V4<T>* kus, cudaStream_t st);
+                     const T* kref_t, T* k2, V4<T>* kus, cudaStream_t st);
 template <class T>
 void launch_sens(const Design& d, const Geom& g, TransferScratch ts, const T* e,
                  const T* kprime, double* gacc, cudaStream_t st);

@@ -11,8 +11,9 @@
 //   k_tap_lists   for each analysis column of the box, the design columns whose support covers
 //                 it (found through the inverse rigid map) with their x-y weights, in design
 //                 index order, plus the moments m0 = sum W, m1 = sum W (xi - xi_G);
-//   k_fill        kappa = sum_z sum_taps W kappa_ref and u_S = omega R'(theta) m1 + u_G m0 on the
-//                 box: a deterministic gather, no atomics;
+//   k_col_planes  for every box column and design plane, the x-y transfer of kappa_ref;
+//   k_fill        kappa = sum over the z taps of that, u_S = omega R'(theta) m1 + u_G m0, on
+//                 the box: deterministic gathers, no atomics;
 //   k_sens        for each design node, sum_x W(x - x_ref) e(x) over its 4^d support (the
 //                 transpose of the kappa transfer), accumulated into dJ/dgamma in FP64.
 #include "lks_device.cuh"
@@ -32,13 +33,17 @@ __global__ void k_design_prep_check(long long nd, const double* gamma, int* bad)
 }
 
 template <class T>
-__global__ void k_design_prep(long long nd, const double* __restrict__ gamma, double kmax,
-                              double q, T* __restrict__ kref, T* __restrict__ kprime) {
+__global__ void k_design_prep(long long nd, long long ncol, int lz,
+                              const double* __restrict__ gamma, double kmax, double q,
+                              T* __restrict__ kref, T* __restrict__ kref_t,
+                              T* __restrict__ kprime) {
     long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (k >= nd) return;
     const double gm = gamma[k];
     const double d = (1.0 - gm) + q;
-    kref[k] = (T)(kmax * q * gm / d);                 // kappa_ref (Sec. 2.3)
+    const T kr = (T)(kmax * q * gm / d);             // kappa_ref (Sec. 2.3)
+    kref[k] = kr;
+    kref_t[(k % ncol) * lz + k / ncol] = kr;         // [column][zeta] copy for the transfer
     kprime[k] = (T)(kmax * q * (1.0 + q) / (d * d));   // d kappa_ref / d gamma
 }
 
@@ -151,31 +156,44 @@ __global__ void k_tap_lists(Design d, Geom g, Motion m, TransferScratch ts) {
     cm[2] = m1y;
 }
 
+// Stage 1: K2[col][zeta] = sum over the column's taps of W_xy * kappa_ref(zeta, tap): the x-y
+// transfer of every design plane, lanes running over zeta (coalesced in kref_t).
 template <class T>
-__global__ void k_fill(Design d, Geom g, Motion m, TransferScratch ts,
-                       const T* __restrict__ kref, V4<T>* __restrict__ kus) {
+__global__ void k_col_planes(Design d, Geom g, TransferScratch ts, const T* __restrict__ kref_t,
+                             T* __restrict__ k2) {
+    const int zeta = blockIdx.x * blockDim.x + threadIdx.x;
+    const long long col = blockIdx.y * (long long)blockDim.y + threadIdx.y;
+    const long long ncols = (long long)g.bn[0] * g.bn[1];
+    if (zeta >= d.L[2] || col >= ncols) return;
+    const int cnt = ts.tap_cnt[col];
+    const int* tidx = ts.tap_idx + col * kMaxTaps;
+    const T* tw = (const T*)ts.tap_w + col * kMaxTaps;
+    T acc = (T)0;
+    for (int e = 0; e < cnt; ++e) acc += tw[e] * kref_t[(long long)tidx[e] * d.L[2] + zeta];
+    k2[col * d.L[2] + zeta] = acc;
+}
+
+// Stage 2: kappa = sum over the z taps of w_z K2 and u_S = m_z (omega R'(theta) m1 + u_G m0)
+// on every node of the footprint box (u_ref is affine in xi, Eq. rigid_body_velocity).
+template <class T>
+__global__ void k_fill(Design d, Geom g, Motion m, TransferScratch ts, const T* __restrict__ k2,
+                       V4<T>* __restrict__ kus) {
     long long bi = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (bi >= g.boxN) return;
     const long long ncols = (long long)g.bn[0] * g.bn[1];
     const long long col = bi % ncols;
     const int bz = (int)(bi / ncols);
-    const int cnt = ts.tap_cnt[col];
-    const int* tidx = ts.tap_idx + col * kMaxTaps;
-    const T* tw = (const T*)ts.tap_w + col * kMaxTaps;
     const int* zi = ts.zt_idx + 4 * bz;
     const T* zw = (const T*)ts.zt_w + 4 * bz;
     T kap = (T)0, mz = (T)0;
     for (int t = 0; t < 4; ++t) {
         const int zeta = zi[t];
         if (zeta < 0) continue;
-        const T wz = zw[t];
-        mz += wz;
-        const T* kp = kref + (long long)zeta * d.ncol;
-        for (int e = 0; e < cnt; ++e) kap += (tw[e] * wz) * kp[tidx[e]];
+        mz += zw[t];
+        kap += zw[t] * k2[col * d.L[2] + zeta];
     }
     const T* cm = (const T*)ts.col_m + 3 * col;
     const T om = (T)m.om, c = (T)m.c, s = (T)m.s;
-    // u_ref is affine in xi (Eq. rigid_body_velocity): sum W u_ref = omega R'(theta) m1 + u_G m0
     V4<T> o;
     o.r = kap;
     o.x = mz * ((-s * cm[1] - c * cm[2]) * om + (T)m.uG[0] * cm[0]);
@@ -254,10 +272,11 @@ __global__ void k_box_to_grid(Geom g, const V4<T>* __restrict__ kus, double* kap
 
 template <class T>
 void launch_design_prep(const Design& d, const double* gamma, double kappa_max, double q,
-                        T* kref, T* kprime, int* bad, cudaStream_t st) {
+                        T* kref, T* kref_t, T* kprime, int* bad, cudaStream_t st) {
     if (d.nd == 0) return;
     k_design_prep_check<<<grid_for(d.nd), kThreads, 0, st>>>(d.nd, gamma, bad);
-    k_design_prep<T><<<grid_for(d.nd), kThreads, 0, st>>>(d.nd, gamma, kappa_max, q, kref, kprime);
+    k_design_prep<T><<<grid_for(d.nd), kThreads, 0, st>>>(d.nd, d.ncol, d.L[2], gamma, kappa_max,
+                                                          q, kref, kref_t, kprime);
 }
 
 template <class T>
@@ -270,11 +289,16 @@ void launch_design_pos(const Design& d, const Geom& g, const Motion& m, Transfer
 
 template <class T>
 void launch_transfer(const Design& d, const Geom& g, const Motion& m, TransferScratch ts,
-                     const T* kref, V4<T>* kus, cudaStream_t st) {
+                     const T* kref_t, T* k2, V4<T>* kus, cudaStream_t st) {
     if (d.nd == 0 || g.boxN == 0) return;
     const long long ncols = (long long)g.bn[0] * g.bn[1];
     k_tap_lists<T><<<grid_for(ncols), kThreads, 0, st>>>(d, g, m, ts);
-    k_fill<T><<<grid_for(g.boxN), kThreads, 0, st>>>(d, g, m, ts, kref, kus);
+    const int lanes = d.L[2] >= 32 ? 32 : (d.L[2] >= 8 ? 8 : 1);
+    const dim3 blk(lanes, kThreads / lanes);
+    const dim3 grd((unsigned)((d.L[2] + lanes - 1) / lanes),
+                   (unsigned)((ncols + blk.y - 1) / blk.y));
+    k_col_planes<T><<<grd, blk, 0, st>>>(d, g, ts, kref_t, k2);
+    k_fill<T><<<grid_for(g.boxN), kThreads, 0, st>>>(d, g, m, ts, k2, kus);
 }
 
 template <class T>
@@ -292,11 +316,11 @@ void launch_box_to_grid(const Geom& g, const V4<T>* kus, double* kappa, double* 
 
 #define LKS_INST_T(T)                                                                        \
     template void launch_design_prep<T>(const Design&, const double*, double, double, T*, T*, \
-                                        int*, cudaStream_t);                                 \
+                                        T*, int*, cudaStream_t);                             \
     template void launch_design_pos<T>(const Design&, const Geom&, const Motion&,             \
                                        TransferScratch, cudaStream_t);                       \
     template void launch_transfer<T>(const Design&, const Geom&, const Motion&,               \
-                                     TransferScratch, const T*, V4<T>*, cudaStream_t);       \
+                                     TransferScratch, const T*, T*, V4<T>*, cudaStream_t);   \
     template void launch_sens<T>(const Design&, const Geom&, TransferScratch, const T*,       \
                                  const T*, double*, cudaStream_t);                           \
     template void launch_box_to_grid<T>(const Geom&, const V4<T>*, double*, double*,          \
