@@ -177,6 +177,8 @@ class Solver:
         if st != 0:
             raise LksError(st, "lks_create failed")
         self._f64 = torch.float64
+        self.generation = 0        # counts forward runs
+        self.adjoint_ready = False  # a forward run whose adjoint has not been taken yet
         self.nd = problem.design_nodes
         self.design_shape = (1 if problem.dim == 2 else problem.L[2], problem.L[1], problem.L[0])
         self.state_shape = (4, problem.n[2], problem.n[1], problem.n[0])
@@ -214,7 +216,10 @@ class Solver:
     def forward(self, n_steps: Optional[int] = None) -> float:
         n = self.problem.n_steps if n_steps is None else n_steps
         J = ctypes.c_double(0.0)
+        self.adjoint_ready = False
         self._check(self.lib.lks_forward(self.ctx, n, ctypes.byref(J)))
+        self.generation += 1
+        self.adjoint_ready = True
         return J.value
 
     def adjoint(self, out=None):
@@ -222,10 +227,12 @@ class Solver:
         numpy array."""
         if out is not None and hasattr(out, "data_ptr"):
             assert out.element_size() == 8 and out.is_contiguous()
+            self.adjoint_ready = False
             self._check(self.lib.lks_adjoint(self.ctx, ctypes.c_void_p(out.data_ptr()),
                                              1 if out.is_cuda else 0))
             return out
         g = np.zeros(self.design_shape, dtype=np.float64)
+        self.adjoint_ready = False
         self._check(self.lib.lks_adjoint(self.ctx, g.ctypes.data_as(ctypes.c_void_p), 0))
         return g
 
