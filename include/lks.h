@@ -160,6 +160,27 @@ lks_status lks_read_timing(lks_ctx* ctx, double* out4);
  * Host only; needs no device. */
 int lks_checkpoint_schedule(int n_segments, int free_slots, int* triples, int cap);
 
+/* One forward LKS step without any device allocation.  The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory when they need a step --
+ * code running while a stream is captured into a CUDA graph, frameworks that own all device
+ * memory through their own pool, loops that must not block on the driver's allocator.
+ *
+ * It runs the plain per-node step (f^eq of every node, gather from x - c_i, Brinkman update,
+ * boundary rules) from state_in to state_out, both device arrays of one node record per node
+ * in cfg->precision ((rho - rho0, ux, uy, uz) as float4 or double4, x fastest).  kappa_us is
+ * a device array of (kappa, u_S x, u_S y, u_S z) per node over the whole grid in the same
+ * precision, or NULL when no body is present.  Work goes to cfg->stream; nothing is
+ * synchronised.  The f^eq planes live in a file-scope device array of 32 MiB that stays on
+ * every device that loads the library until the process exits: grids needing more
+ * (nodes x Q x element size > 32 MiB, e.g. more than about 559k nodes for D3Q15 in FP32) are
+ * rejected with LKS_ERR_ARG and a message in err (err_len bytes, may be NULL).  The first call
+ * on each device looks up that array's device address (keep it outside stream capture).  All
+ * calls share the array, so calls that overlap on the GPU race and must be serialised by the
+ * caller; each call rewrites all the scratch it reads.  cudaMalloc, cudaFree and allocating
+ * library routines are never called. */
+lks_status lks_step_noalloc(const lks_config* cfg, const void* state_in, void* state_out,
+                            const void* kappa_us, char* err, size_t err_len);
+
 const char* lks_last_error(const lks_ctx* ctx);
 void lks_destroy(lks_ctx* ctx);
 

@@ -23,7 +23,7 @@ STATUS = {0: "LKS_OK", 1: "LKS_ERR_ARG", 2: "LKS_ERR_ORDER", 3: "LKS_ERR_NOMEM",
 EXPORTS = ("lks_workspace_bytes", "lks_create", "lks_set_design", "lks_set_motion",
            "lks_set_initial_state", "lks_forward", "lks_adjoint", "lks_get_state",
            "lks_transfer", "lks_uses_fused", "lks_get_stats", "lks_set_timing", "lks_read_timing",
-           "lks_checkpoint_schedule", "lks_last_error", "lks_destroy")
+           "lks_checkpoint_schedule", "lks_step_noalloc", "lks_last_error", "lks_destroy")
 
 
 class LksError(RuntimeError):
