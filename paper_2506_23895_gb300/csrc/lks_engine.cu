@@ -167,6 +167,10 @@ bool validate(const lks_config* cfg, std::string& why) {
             why = "every active axis needs at least 3 nodes";
             return false;
         }
+    if ((double)n[0] * n[1] * n[2] >= 2147483648.0) {
+        why = "grids of 2^31 nodes or more are not supported";
+        return false;
+    }
     if (cfg->dim == 2 && cfg->nz != 1) {
         why = "nz must be 1 in 2D";
         return false;

@@ -2,9 +2,9 @@
 //
 // Algorithm 1's stencil part (Eqs. rho, u with the viscosity term of f^eq, the Brinkman update
 // of Eq. u_ex_2 and the boundary rules of Eqs. bc_rho, bc_u) in one pass over the state:
-//   * a block owns a 32 x 16 tile of output columns and marches along z over a chunk of planes;
+//   * a block owns a 32 x 8 tile of output columns and marches along z over a chunk of planes;
 //   * raw state planes (rho - rho0, u as one float4 per node) with a halo of two cells arrive in
-//     a seven-slot shared-memory ring through cp.async.bulk.tensor (TMA) completing on mbarriers;
+//     a five-slot shared-memory ring through cp.async.bulk.tensor (TMA) completing on mbarriers;
 //     the waits are bounded and a stalled copy sets an error flag instead of hanging;
 //   * every node's f_i^eq is evaluated once, at its source, with the opposite-direction pairs
 //     sharing their symmetric part; the 12 directions that leave the column go through shared
@@ -24,12 +24,12 @@ namespace lks {
 
 namespace {
 
-constexpr int TX = 32, TY = 16;             // output tile
+constexpr int TX = 32, TY = 8;              // output tile
 constexpr int HX = TX + 4, HY = TY + 4;     // raw tile with a two-cell halo
 constexpr int FX = TX + 2, FY = TY + 2;     // f^eq region with a one-cell halo
-constexpr int NSLOT = 7;                    // raw-plane ring depth (5 planes in flight)
-constexpr int NTHR = TX * TY;               // 512
-constexpr int NHALO = FX * FY - TX * TY;    // 100 extra f^eq nodes on the tile rim
+constexpr int NSLOT = 5;                    // raw-plane ring depth (3 planes in flight)
+constexpr int NTHR = TX * TY;               // 256
+constexpr int NHALO = FX * FY - TX * TY;    // 84 extra f^eq nodes on the tile rim
 constexpr int NCROSS = 12;                  // directions leaving the column
 constexpr unsigned PLANE_BYTES = HX * HY * 16;
 
@@ -166,7 +166,7 @@ __device__ __forceinline__ int axis_mode(int gcoord, int n) {
     return gcoord == 0 ? 1 : (gcoord == n - 1 ? 2 : 0);
 }
 
-__global__ void __launch_bounds__(NTHR, 2)
+__global__ void __launch_bounds__(NTHR, 4)
     k_fused_step3d(const __grid_constant__ CUtensorMap tmap, const FusedArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     float4* raw = reinterpret_cast<float4*>(smem + OFF_RAW);
@@ -406,6 +406,31 @@ bool encode_state_map(CUtensorMap* map, const void* base, const Geom& g, int bx,
            CUDA_SUCCESS;
 }
 
+// Planes per z chunk so that the grid fills a whole number of waves of `per_sm` resident
+// blocks per SM (the smallest such count with chunks of at least 24 planes), else as few
+// chunks as that floor allows.
+int fused_zchunk_waves(const Geom& g, long long tiles, int per_sm) {
+    int dev = 0, nsm = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const long long slots = (long long)nsm * per_sm;
+    const int maxc = std::max(1, g.n[2] / 24);
+    int best = 1;
+    double best_eff = 0.0;
+    for (int c = 1; c <= maxc; ++c) {
+        const long long blocks = tiles * c;
+        const long long waves = (blocks + slots - 1) / slots;
+        const int zc = (g.n[2] + c - 1) / c;
+        // useful fraction: filled wave slots x planes that are not pipeline warm-up
+        const double eff = (double)blocks / (double)(waves * slots) * zc / (zc + 3.0);
+        if (eff > best_eff + 1e-9) {
+            best_eff = eff;
+            best = c;
+        }
+    }
+    return (g.n[2] + best - 1) / best;
+}
+
 // Planes per z chunk: about three resident waves of two blocks per SM, chunks of >= 16 planes.
 int fused_zchunk(const Geom& g, long long tiles) {
     int dev = 0, nsm = 148;
@@ -440,7 +465,7 @@ cudaError_t launch_fused_step3d(const Geom& g, const V4<float>* src, const V4<fl
     a.w1 = (float)(1.0 / 9.0);
     a.w2 = (float)(1.0 / 72.0);
     const int tiles_x = (g.n[0] + TX - 1) / TX, tiles_y = (g.n[1] + TY - 1) / TY;
-    a.zchunk = fused_zchunk(g, (long long)tiles_x * tiles_y);
+    a.zchunk = fused_zchunk_waves(g, (long long)tiles_x * tiles_y, 4);
     const int chunks = (g.n[2] + a.zchunk - 1) / a.zchunk;
     dim3 grid(tiles_x, tiles_y, chunks);
     k_fused_step3d<<<grid, NTHR, SMEM_BYTES, st>>>(map, a);

@@ -27,13 +27,13 @@ namespace lks {
 
 namespace {
 
-constexpr int TX = 32, TY = 16;
+constexpr int TX = 32, TY = 8;
 constexpr int HX = TX + 4, HY = TY + 4;     // lambda tile with a two-cell halo
 constexpr int FX = TX + 2, FY = TY + 2;     // moment region with a one-cell halo
 constexpr int NSLOT = 5;
 constexpr int NTHR = TX * TY;
-constexpr int NRIM1 = FX * FY - TX * TY;    // 100 rim nodes of the moment region
-constexpr int NRIM2 = HX * HY - TX * TY;    // 208 halo nodes to convert
+constexpr int NRIM1 = FX * FY - TX * TY;    // 84 rim nodes of the moment region
+constexpr int NRIM2 = HX * HY - TX * TY;    // 176 halo nodes to convert
 constexpr int NS = 5;                       // S~ components shared in-plane: xx xy xz yy yz
 constexpr unsigned PLANE_BYTES = HX * HY * 16;
 constexpr size_t OFF_RAW = 0;
@@ -144,7 +144,7 @@ __device__ __forceinline__ Mom moments(const AdjArgs& a, const float4* __restric
     return m;
 }
 
-__global__ void __launch_bounds__(NTHR, 2)
+__global__ void __launch_bounds__(NTHR, 4)
     k_fused_adj3d(const __grid_constant__ CUtensorMap tmap, const AdjArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     float4* raw = reinterpret_cast<float4*>(smem + OFF_RAW);
@@ -352,11 +352,11 @@ __global__ void k_adj_bcorr(Geom g, const float* __restrict__ face, FaceOffsets 
     const int ax = slab / 2;
     int c[3];
     const int b0 = (ax == 0) ? 1 : 0, b1 = (ax == 2) ? 1 : 2;
-    const int layer = (int)(r % 3);
-    const long long rr = r / 3;
+    const int layer = (int)((unsigned)r % 3u);
+    const unsigned rr = (unsigned)r / 3u;
     c[ax] = (slab & 1) ? g.n[ax] - 1 - layer : layer;
-    c[b0] = (int)(rr % g.n[b0]);
-    c[b1] = (int)(rr / g.n[b0]);
+    c[b0] = (int)(rr % (unsigned)g.n[b0]);
+    c[b1] = (int)(rr / (unsigned)g.n[b0]);
     for (int e = 0; e < slab; ++e) {
         const int ae = e / 2;
         const int d = (e & 1) ? g.n[ae] - 1 - c[ae] : c[ae];
@@ -435,7 +435,7 @@ cudaError_t launch_fused_adj3d(const Geom& g, const V4<float>* lam_in, V4<float>
             for (int k = 0; k < 3; ++k) a.obj_u[k] = (float)(-h * g.odir[k] / g.ocount);
     }
     const int tiles_x = (g.n[0] + TX - 1) / TX, tiles_y = (g.n[1] + TY - 1) / TY;
-    a.zchunk = fused_zchunk(g, tiles_x * tiles_y);
+    a.zchunk = fused_zchunk_waves(g, (long long)tiles_x * tiles_y, 4);
     const int chunks = (g.n[2] + a.zchunk - 1) / a.zchunk;
     k_fused_adj3d<<<dim3(tiles_x, tiles_y, chunks), NTHR, SMEM_BYTES, st>>>(map, a);
     cudaError_t r = cudaGetLastError();

@@ -101,6 +101,7 @@ struct FaceOffsets {
 };
 bool fused3d_eligible(const Geom& g);
 int fused_zchunk(const Geom& g, long long tiles);
+int fused_zchunk_waves(const Geom& g, long long tiles, int per_sm);
 cudaError_t launch_fused_step3d(const Geom& g, const V4<float>* src, const V4<float>* kus,
                                 V4<float>* dst, int* err, cudaStream_t st);
 // Offsets of the six face arrays (3 floats per face node) and their total length.

@@ -21,10 +21,12 @@ constexpr int kThreads = 256;
 inline unsigned grid_for(long long n) { return (unsigned)((n + kThreads - 1) / kThreads); }
 
 __device__ __forceinline__ void node_coords(const Geom& g, long long m, int& x, int& y, int& z) {
-    x = (int)(m % g.n[0]);
-    long long t = m / g.n[0];
-    y = (int)(t % g.n[1]);
-    z = (int)(t / g.n[1]);
+    // node counts are below 2^31 (checked at create): 32-bit division
+    const unsigned mu = (unsigned)m, nx = (unsigned)g.n[0], ny = (unsigned)g.n[1];
+    const unsigned t = mu / nx;
+    x = (int)(mu - t * nx);
+    y = (int)(t % ny);
+    z = (int)(t / ny);
 }
 
 template <class T>
@@ -218,8 +220,8 @@ __device__ __forceinline__ bool shell_node(const Geom& g, long long t, int& x, i
     int c[3];
     const int b0 = (a == 0) ? 1 : 0, b1 = (a == 2) ? 1 : 2;
     c[a] = fixed;
-    c[b0] = (int)(t % g.n[b0]);
-    c[b1] = (int)(t / g.n[b0]);
+    c[b0] = (int)((unsigned)t % (unsigned)g.n[b0]);
+    c[b1] = (int)((unsigned)t / (unsigned)g.n[b0]);
     // owned by an earlier slab?
     for (int e = 0; e < slab; ++e) {
         const int ae = e / 2;
@@ -407,8 +409,8 @@ __global__ void k_check_state(Geom g, const V4<T>* __restrict__ s, int* flag) {
     long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (m >= g.nodes) return;
     const V4<T> v = s[m];
-    const double a = fabs((double)v.x) + fabs((double)v.y) + fabs((double)v.z);
-    if (!(a < 0.5) || !isfinite((double)v.r)) atomicOr(flag, 1);
+    const T a = fabs(v.x) + fabs(v.y) + fabs(v.z);
+    if (!(a < (T)0.5) || !(fabs(v.r) < (T)1e30)) atomicOr(flag, 1);
 }
 
 template <class T>

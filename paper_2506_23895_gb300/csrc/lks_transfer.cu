@@ -52,7 +52,7 @@ __global__ void k_design_pos(Design d, Geom g, Motion m, TransferScratch ts) {
     long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     T* frac = (T*)ts.col_frac;
     if (k < d.ncol) {
-        const int i = (int)(k % d.L[0]), j = (int)(k / d.L[0]);
+        const int i = (int)((unsigned)k % (unsigned)d.L[0]), j = (int)((unsigned)k / (unsigned)d.L[0]);
         const double dx = i - d.xiG[0], dy = j - d.xiG[1];
         const double xr = m.c * dx - m.s * dy + m.xG[0];   // Eq. rigid_body_position
         const double yr = m.s * dx + m.c * dy + m.xG[1];
@@ -181,8 +181,8 @@ __global__ void k_fill(Design d, Geom g, Motion m, TransferScratch ts, const T* 
     long long bi = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (bi >= g.boxN) return;
     const long long ncols = (long long)g.bn[0] * g.bn[1];
-    const long long col = bi % ncols;
-    const int bz = (int)(bi / ncols);
+    const long long col = (unsigned)bi % (unsigned)ncols;
+    const int bz = (int)((unsigned)bi / (unsigned)ncols);
     const int* zi = ts.zt_idx + 4 * bz;
     const T* zw = (const T*)ts.zt_w + 4 * bz;
     T kap = (T)0, mz = (T)0;
@@ -202,57 +202,74 @@ __global__ void k_fill(Design d, Geom g, Motion m, TransferScratch ts, const T* 
     kus[bi] = o;
 }
 
+// Sensitivity gather: for each design node, sum_x W(x - x_ref) e(x) over its support (the
+// transpose of the kappa transfer), times kappa', added to dJ/dgamma in FP64.  The z shift is
+// the same for every design plane, so one thread takes a design column and kSensRun planes:
+// each analysis plane's 4 x 4 x-y tap sum is formed once and the four z weights slide over them.
+constexpr int kSensRun = 8;
+
 template <class T>
 __global__ void k_sens(Design d, Geom g, TransferScratch ts, const T* __restrict__ e,
                        const T* __restrict__ kprime, double* __restrict__ gacc) {
-    long long dn = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (dn >= d.nd) return;
-    const long long k = dn % d.ncol;
-    const int zeta = (int)(dn / d.ncol);
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const unsigned runs = (unsigned)((d.L[2] + kSensRun - 1) / kSensRun);
+    if (t >= (long long)d.ncol * runs) return;
+    const unsigned k = (unsigned)t % (unsigned)d.ncol;   // design column
+    const int z0 = (int)((unsigned)t / (unsigned)d.ncol) * kSensRun;
+    const int z1 = min(d.L[2], z0 + kSensRun);
     const T* frac = (const T*)ts.col_frac;
     const int bx = ts.col_base[2 * k], by = ts.col_base[2 * k + 1];
     const T fx = frac[2 * k], fy = frac[2 * k + 1];
-    const int bzz = ts.dz_base[zeta];
-    const T fz = ((const T*)ts.dz_frac)[zeta];
     T wx[4], wy[4], wz[4];
+    const T fz = ((const T*)ts.dz_frac)[0];
 #pragma unroll
-    for (int t = 0; t < 4; ++t) {
-        wx[t] = peskin((T)(t - 1) - fx);
-        wy[t] = peskin((T)(t - 1) - fy);
-        wz[t] = (g.dim == 3) ? peskin((T)(t - 1) - fz) : (t == 1 ? (T)1 : (T)0);
+    for (int q = 0; q < 4; ++q) {
+        wx[q] = peskin((T)(q - 1) - fx);
+        wy[q] = peskin((T)(q - 1) - fy);
+        wz[q] = (g.dim == 3) ? peskin((T)(q - 1) - fz) : (q == 1 ? (T)1 : (T)0);
     }
-    T acc = (T)0;
-#pragma unroll
-    for (int tz = 0; tz < 4; ++tz) {
-        if (wz[tz] == (T)0) continue;
-        const int z = (g.dim == 3) ? bzz - 1 + tz : 0;
+    const int ex0 = bx - 1 - g.blo[0], ey0 = by - 1 - g.blo[1];
+    // x-y tap sum of analysis plane z (0 outside the box, where W vanishes)
+    auto plane_sum = [&](int z) -> T {
+        const int ez = z - g.blo[2];
+        if (ez < 0 || ez >= g.bn[2]) return (T)0;
+        const T* ep = e + (long long)ez * g.bn[1] * g.bn[0];
+        T acc = (T)0;
 #pragma unroll
         for (int ty = 0; ty < 4; ++ty) {
-            const int y = by - 1 + ty;
+            const int ey = ey0 + ty;
+            if (ey < 0 || ey >= g.bn[1] || wy[ty] == (T)0) continue;
 #pragma unroll
             for (int tx = 0; tx < 4; ++tx) {
-                const T W = (wx[tx] * wy[ty]) * wz[tz];
-                if (W == (T)0) continue;
-                const int x = bx - 1 + tx;
-                const int ex = x - g.blo[0], ey = y - g.blo[1], ez = z - g.blo[2];
-                // the box is the union of all supports; a tap can only fall outside it at
-                // |r| -> 2, where W vanishes, through host/device rounding of x_ref
-                if (ex < 0 || ey < 0 || ez < 0 || ex >= g.bn[0] || ey >= g.bn[1] || ez >= g.bn[2])
-                    continue;
-                acc += W * e[((long long)ez * g.bn[1] + ey) * g.bn[0] + ex];
+                const int ex = ex0 + tx;
+                const T W = wx[tx] * wy[ty];
+                if (ex < 0 || ex >= g.bn[0] || W == (T)0) continue;
+                acc += W * ep[(long long)ey * g.bn[0] + ex];
             }
         }
+        return acc;
+    };
+    const int zb0 = (g.dim == 3) ? ts.dz_base[z0] : 0;   // analysis base plane of design plane z0
+    T s0 = plane_sum(zb0 - 1), s1 = plane_sum(zb0), s2 = plane_sum(zb0 + 1);
+    for (int zeta = z0; zeta < z1; ++zeta) {
+        const int zb = zb0 + (zeta - z0);
+        const T s3 = (g.dim == 3) ? plane_sum(zb + 2) : (T)0;
+        const T acc = wz[0] * s0 + wz[1] * s1 + wz[2] * s2 + wz[3] * s3;
+        const long long dn = (long long)zeta * d.ncol + k;
+        gacc[dn] += (double)kprime[dn] * (double)acc;
+        s0 = s1;
+        s1 = s2;
+        s2 = s3;
     }
-    gacc[dn] += (double)kprime[dn] * (double)acc;
 }
 
 template <class T>
 __global__ void k_box_to_grid(Geom g, const V4<T>* __restrict__ kus, double* kappa, double* us) {
     long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (m >= g.nodes) return;
-    const int x = (int)(m % g.n[0]);
-    const long long t = m / g.n[0];
-    const int y = (int)(t % g.n[1]), z = (int)(t / g.n[1]);
+    const unsigned t = (unsigned)m / (unsigned)g.n[0];
+    const int x = (int)((unsigned)m - t * (unsigned)g.n[0]);
+    const int y = (int)(t % (unsigned)g.n[1]), z = (int)(t / (unsigned)g.n[1]);
     long long bi;
     double k = 0, a = 0, b = 0, c = 0;
     if (in_box(g, x, y, z, bi)) {
@@ -305,7 +322,8 @@ template <class T>
 void launch_sens(const Design& d, const Geom& g, TransferScratch ts, const T* e,
                  const T* kprime, double* gacc, cudaStream_t st) {
     if (d.nd == 0 || g.boxN == 0) return;
-    k_sens<T><<<grid_for(d.nd), kThreads, 0, st>>>(d, g, ts, e, kprime, gacc);
+    const long long n = d.ncol * ((d.L[2] + kSensRun - 1) / kSensRun);
+    k_sens<T><<<grid_for(n), kThreads, 0, st>>>(d, g, ts, e, kprime, gacc);
 }
 
 template <class T>
