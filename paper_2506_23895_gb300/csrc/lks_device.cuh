@@ -123,8 +123,67 @@ __device__ __forceinline__ V4<T> bc_value(const Geom& g, int f, const V4<T>& v) 
     return b;
 }
 
-// Options per axis for boundary nodes sourced from interior node coordinate ci along axis a:
-// returns how many (1..3) and fills coordinates (first is ci itself) and sides.
+// Visit every boundary node whose copy source is interior node (x, y, z): fn(bx, by, bz, face)
+// with the winning face of that boundary node.  Along each non-periodic axis the node can step
+// out to the low face (coordinate 1) and/or the high face (coordinate n-2); every non-empty
+// combination of such steps is one boundary node.  Fully unrolled, so no local arrays.
+template <class F>
+__device__ __forceinline__ void for_each_sourced_boundary(const Geom& g, int x, int y, int z,
+                                                          F&& fn) {
+    const int c[3] = {x, y, z};
+#pragma unroll
+    for (int mx = 0; mx < 3; ++mx)
+#pragma unroll
+        for (int my = 0; my < 3; ++my)
+#pragma unroll
+            for (int mz = 0; mz < 3; ++mz) {
+                if (mx == 0 && my == 0 && mz == 0) continue;
+                const int m[3] = {mx, my, mz};
+                bool ok = true;
+                int b[3], side[3];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    b[a] = c[a];
+                    side[a] = -1;
+                    if (m[a] == 0) continue;
+                    const bool active = a < g.dim && !g.periodic[a];
+                    if (m[a] == 1) {
+                        ok = ok && active && c[a] == 1;
+                        b[a] = 0;
+                        side[a] = 0;
+                    } else {
+                        ok = ok && active && c[a] == g.n[a] - 2;
+                        b[a] = g.n[a] - 1;
+                        side[a] = 1;
+                    }
+                }
+                if (!ok) continue;
+                fn(b[0], b[1], b[2], winning_face(g, side));
+            }
+}
+
+// True if interior node (x, y, z) is the copy source of some boundary node.
+__device__ __forceinline__ bool sources_boundary(const Geom& g, int x, int y, int z) {
+    const int c[3] = {x, y, z};
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+        if (a < g.dim && !g.periodic[a] && (c[a] == 1 || c[a] == g.n[a] - 2)) return true;
+    return false;
+}
+
+// Write every boundary node whose copy source is interior node (x,y,z) holding value v.
+template <class T>
+__device__ __forceinline__ void write_bc_from(const Geom& g, int x, int y, int z,
+                                              const V4<T>& v, V4<T>* s) {
+    if (!sources_boundary(g, x, y, z)) return;
+    for_each_sourced_boundary(g, x, y, z, [&](int bx, int by, int bz, int f) {
+        s[node_index(g, bx, by, bz)] = bc_value(g, f, v);
+    });
+}
+
+// The same in compact loop form, for kernels where the unrolled visitor costs registers on the
+// common path: the options per axis are listed (first the node's own coordinate) and all
+// non-trivial combinations written.
 __device__ __forceinline__ int bc_axis_options(const Geom& g, int a, int ci, int opt[3],
                                                int side[3]) {
     opt[0] = ci;
@@ -145,20 +204,20 @@ __device__ __forceinline__ int bc_axis_options(const Geom& g, int a, int ci, int
     return k;
 }
 
-// Write every boundary node whose copy source is interior node (x,y,z) holding value v.
 template <class T>
-__device__ void write_bc_from(const Geom& g, int x, int y, int z, const V4<T>& v, V4<T>* s) {
+__device__ void write_bc_from_compact(const Geom& g, int x, int y, int z, const V4<T>& v,
+                                      V4<T>* s) {
     int ox[3], oy[3], oz[3], sx[3], sy[3], sz[3];
-    int nx = bc_axis_options(g, 0, x, ox, sx);
-    int ny = bc_axis_options(g, 1, y, oy, sy);
-    int nz = bc_axis_options(g, 2, z, oz, sz);
+    const int nx = bc_axis_options(g, 0, x, ox, sx);
+    const int ny = bc_axis_options(g, 1, y, oy, sy);
+    const int nz = bc_axis_options(g, 2, z, oz, sz);
     if (nx == 1 && ny == 1 && nz == 1) return;
     for (int k = 0; k < nz; ++k)
         for (int j = 0; j < ny; ++j)
             for (int i = 0; i < nx; ++i) {
                 if (i == 0 && j == 0 && k == 0) continue;
-                int side[3] = {sx[i], sy[j], sz[k]};
-                int f = winning_face(g, side);
+                const int side[3] = {sx[i], sy[j], sz[k]};
+                const int f = winning_face(g, side);
                 s[node_index(g, ox[i], oy[j], oz[k])] = bc_value(g, f, v);
             }
 }

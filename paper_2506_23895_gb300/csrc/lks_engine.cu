@@ -218,6 +218,24 @@ bool validate(const lks_config* cfg, std::string& why) {
     return true;
 }
 
+// Node indices of the objective's target region in ascending order (box, then cylinder).
+std::vector<int> target_list(const lks_config* c) {
+    std::vector<int> out;
+    const int* b = c->obj_box;
+    const int nz = c->dim == 3 ? c->nz : 1;
+    const int z0 = c->dim == 3 ? b[4] : 0, z1 = c->dim == 3 ? b[5] : 0;
+    for (int z = std::max(0, z0); z <= std::min(z1, nz - 1); ++z)
+        for (int y = std::max(0, b[2]); y <= std::min(b[3], c->ny - 1); ++y)
+            for (int x = std::max(0, b[0]); x <= std::min(b[1], c->nx - 1); ++x) {
+                if (c->obj_cyl_r > 0.0) {
+                    const double dx = x - c->obj_cyl_c[0], dy = y - c->obj_cyl_c[1];
+                    if (dx * dx + dy * dy > c->obj_cyl_r * c->obj_cyl_r) continue;
+                }
+                out.push_back((int)(((long long)z * c->ny + y) * c->nx + x));
+            }
+    return out;
+}
+
 // Count target nodes on the host (the same membership test the kernels use).
 double count_target(const lks_config* c) {
     const int* b = c->obj_box;
@@ -245,7 +263,7 @@ struct Layout {
 enum {
     L_S0, L_S1, L_SINIT, L_L0, L_L1, L_F, L_MU, L_PHI, L_KUS, L_E, L_GAMMA, L_KREF, L_KPRIME,
     L_GACC, L_JSTEP, L_CBASE, L_CFRAC, L_ZTI, L_ZTW, L_TCNT, L_TIDX, L_TW, L_CM, L_DZB, L_DZF,
-    L_FLAGS, L_KREFT, L_K2, L_FACE, L_POOL, L_COUNT
+    L_FLAGS, L_KREFT, L_K2, L_FACE, L_TGT, L_POOL, L_COUNT
 };
 
 Layout make_layout(const lks_config* cfg) {
@@ -281,6 +299,7 @@ Layout make_layout(const lks_config* cfg) {
     sz[L_DZB] = (size_t)std::max(cfg->lz, 1) * 4;
     sz[L_DZF] = (size_t)std::max(cfg->lz, 1) * T;
     sz[L_FLAGS] = 64;
+    sz[L_TGT] = (size_t)std::max(1.0, count_target(cfg)) * 4;
     sz[L_KREFT] = (size_t)std::max(nd, 1LL) * T;
     sz[L_K2] = nd ? (size_t)cols * std::max(cfg->lz, 1) * T : 0;
     {
@@ -728,6 +747,18 @@ lks_status lks_create(const lks_config* cfg, void* workspace, size_t ws_bytes, l
     c->ts.dz_base = (int*)(w + L.off[L_DZB]);
     c->ts.dz_frac = w + L.off[L_DZF];
     c->flags = (int*)(w + L.off[L_FLAGS]);
+    {
+        const std::vector<int> tl = target_list(cfg);
+        int* dt = (int*)(w + L.off[L_TGT]);
+        if (cudaMemcpy(dt, tl.data(), tl.size() * sizeof(int), cudaMemcpyHostToDevice) !=
+            cudaSuccess) {
+            cudaGetLastError();
+            if (c->own_ws) cudaFree(c->ws);
+            delete c;
+            return LKS_ERR_CUDA;
+        }
+        c->g.otarget = dt;
+    }
     c->ts.err = c->flags + 1;
     c->fused3d = (c->prec == LKS_FP32) && !(cfg->flags & LKS_FLAG_PLAIN_KERNELS) &&
                  fused3d_eligible(g);

@@ -336,7 +336,7 @@ __global__ void __launch_bounds__(NTHR, 4)
                     v.x = o.y;
                     v.y = o.z;
                     v.z = o.w;
-                    write_bc_from(g, gx, gy, qz, v, reinterpret_cast<V4<float>*>(a.out));
+                    write_bc_from_compact(g, gx, gy, qz, v, reinterpret_cast<V4<float>*>(a.out));
                 }
             }
         }

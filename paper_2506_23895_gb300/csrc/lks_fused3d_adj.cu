@@ -237,6 +237,11 @@ __global__ void __launch_bounds__(NTHR, 4)
         }
         ++ik;
         if (++islot == NSLOT) islot = 0;
+        // u^{n-1} of this column's output plane p - 1, fetched before the stencil work
+        const int q = p - 1;
+        const bool write_out = q >= q0 && own_in;
+        float4 u = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (write_out) u = a.sp[q * zstride + col];
         // 1. lambda -> mu for plane p + 1
         {
             float4* pl = raw + (size_t)cslot * HX * HY;
@@ -273,10 +278,8 @@ __global__ void __launch_bounds__(NTHR, 4)
             sw[4 * FS + fr] = mr.Syz;
         }
         // 3. lambda^{n-1} of plane q = p - 1 (its in-plane S~ was stored last iteration)
-        const int q = p - 1;
-        if (q >= q0 && own_in) {
+        if (write_out) {
             const float* sr = sS + (size_t)(q & 1) * NS * FS;
-            const float4 u = a.sp[q * zstride + col];
             // D^T (2 A S~) in central form: A [S~_a.(x-1) - S~_a.(x+1) + ... ]
             const float tx_x = sr[0 * FS + fo - 1] - sr[0 * FS + fo + 1];
             const float tx_y = sr[1 * FS + fo - 1] - sr[1 * FS + fo + 1];

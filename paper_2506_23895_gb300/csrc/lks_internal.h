@@ -36,6 +36,7 @@ struct Geom {
     double odir[3];
     double ocyl_r, ocyl_c[2];
     double ocount;
+    const int* otarget;   // node indices of the target region, ascending (device)
 };
 
 // Design grid and per-step rigid motion.

@@ -157,18 +157,10 @@ __global__ void k_gather(Geom g, const T* __restrict__ F, const V4<T>* __restric
 template <class T>
 __global__ void k_objective(Geom g, const V4<T>* __restrict__ s, double* jstep) {
     __shared__ double red[kThreads];
-    const int x0 = g.obox[0], x1 = g.obox[1], y0 = g.obox[2], y1 = g.obox[3];
-    const int z0 = (g.dim == 3) ? g.obox[4] : 0, z1 = (g.dim == 3) ? g.obox[5] : 0;
-    const int bx = x1 - x0 + 1, by = y1 - y0 + 1, bz = z1 - z0 + 1;
-    const long long tot = (long long)bx * by * bz;
+    const int tot = (int)g.ocount;
     double acc = 0.0;
-    for (long long k = threadIdx.x; k < tot; k += blockDim.x) {
-        int x = x0 + (int)(k % bx);
-        long long t = k / bx;
-        int y = y0 + (int)(t % by);
-        int z = z0 + (int)(t / by);
-        if (!in_target(g, x, y, z)) continue;
-        const V4<T> v = s[node_index(g, x, y, z)];
+    for (int k = threadIdx.x; k < tot; k += blockDim.x) {
+        const V4<T> v = s[g.otarget[k]];
         if (g.okind == 0)
             acc += (double)v.r;
         else
@@ -206,13 +198,17 @@ __device__ __forceinline__ void obj_source(const Geom& g, int x, int y, int z, d
 // Shell enumeration: slab s (0..5) is the interior layer next to face s (axis s/2, low or
 // high side); a node next to several faces is handled by the first slab that contains it.
 __device__ __forceinline__ bool shell_node(const Geom& g, long long t, int& x, int& y, int& z) {
-    const long long per[3] = {(long long)g.n[1] * g.n[2], (long long)g.n[0] * g.n[2],
-                              (long long)g.n[0] * g.n[1]};
+    const unsigned per0 = (unsigned)g.n[1] * g.n[2], per1 = (unsigned)g.n[0] * g.n[2],
+                   per2 = (unsigned)g.n[0] * g.n[1];
+    unsigned r = (unsigned)t;
     int slab = 0;
-    while (slab < 6 && t >= per[slab / 2]) {
-        t -= per[slab / 2];
+    while (slab < 6) {
+        const unsigned pa = slab < 2 ? per0 : (slab < 4 ? per1 : per2);
+        if (r < pa) break;
+        r -= pa;
         ++slab;
     }
+    t = r;
     if (slab >= 6) return false;
     const int a = slab / 2;
     if (a >= g.dim || g.periodic[a]) return false;
@@ -240,30 +236,21 @@ __global__ void k_adj_bcT(Geom g, V4<T>* lam, double h) {
     int x, y, z;
     if (!shell_node(g, t, x, y, z)) return;
     const long long m = node_index(g, x, y, z);
-    int ox[3], oy[3], oz[3], sx[3], sy[3], sz[3];
-    int nx = bc_axis_options(g, 0, x, ox, sx);
-    int ny = bc_axis_options(g, 1, y, oy, sy);
-    int nz = bc_axis_options(g, 2, z, oz, sz);
-    if (nx == 1 && ny == 1 && nz == 1) return;
+    if (!sources_boundary(g, x, y, z)) return;
     V4<T> acc = lam[m];
-    for (int k = 0; k < nz; ++k)
-        for (int j = 0; j < ny; ++j)
-            for (int i = 0; i < nx; ++i) {
-                if (i == 0 && j == 0 && k == 0) continue;
-                int side[3] = {sx[i], sy[j], sz[k]};
-                int f = winning_face(g, side);
-                V4<T> lb = lam[node_index(g, ox[i], oy[j], oz[k])];
-                obj_source(g, ox[i], oy[j], oz[k], h, lb);
-                int t = g.bc[f];
-                if (t == BC_WALL || t == BC_INLET) {
-                    acc.r += lb.r;
-                } else {
-                    int na = f / 2;
-                    if (na == 0) acc.x += lb.x;
-                    if (na == 1) acc.y += lb.y;
-                    if (na == 2) acc.z += lb.z;
-                }
-            }
+    for_each_sourced_boundary(g, x, y, z, [&](int bx, int by, int bz, int f) {
+        V4<T> lb = lam[node_index(g, bx, by, bz)];
+        obj_source(g, bx, by, bz, h, lb);
+        const int t = g.bc[f];
+        if (t == BC_WALL || t == BC_INLET) {
+            acc.r += lb.r;
+        } else {
+            const int na = f / 2;
+            if (na == 0) acc.x += lb.x;
+            if (na == 1) acc.y += lb.y;
+            if (na == 2) acc.z += lb.z;
+        }
+    });
     lam[m] = acc;
 }
 
