@@ -84,18 +84,22 @@ def peaks():
     return 6800.0, "fallback"
 
 
-def kernel_sources_sha1():
+FWD_KERNEL_SOURCES = ("lks_fused3d.cu", "lks_device.cuh", "lks_tma.cuh", "lks_internal.h")
+
+
+def kernel_sources_sha1(names=FWD_KERNEL_SOURCES):
+    """SHA-1 over the source files a kernel is built from (to tell stale counters)."""
     h = hashlib.sha1()
     csrc = os.path.join(ROOT, "paper_2506_23895_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh", ".h")):
-            with open(os.path.join(csrc, name), "rb") as f:
-                h.update(f.read())
+    for name in names:
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(f.read())
     return h.hexdigest()
 
 
 def ncu_traffic(kernel_key):
-    """DRAM bytes per launch from the committed ncu summary, if taken on the current sources."""
+    """DRAM bytes per launch of the forward step kernel from the committed ncu summary
+    (profiles/ncu_traffic.json), or None when the kernel's sources changed since."""
     p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(p):
         return None
