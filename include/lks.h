@@ -91,6 +91,11 @@ typedef struct {
 
 /* Run every step on the plain per-node kernels even where the fused FP32 3D step applies. */
 #define LKS_FLAG_PLAIN_KERNELS 1
+/* Adjoint source update as printed in Sec. 2.4 instead of the exact discrete adjoint: the
+ * (1 + kappa)^-1 of the Brinkman source (Eq. au_ex) divides only the gathered first moment and
+ * the objective source.  For comparing the printed scheme's gradient with the exact one; uses
+ * the plain kernels. */
+#define LKS_FLAG_PAPER_ALKS 2
 
 /* Prescribed rigid motion, rows n = 0..n_rows-1 for time t_n = n (Delta t = 1).
  * Each row: theta, omega, xG[3], uG[3] (8 doubles, host memory, copied).  In 3D the rotation

@@ -65,6 +65,7 @@ def _load():
             D = ctypes.POINTER(ctypes.c_double)
             lib.orc_forward.argtypes = [P, D, D, ctypes.c_int, D, D, D]
             lib.orc_gradient.argtypes = [P, D, D, ctypes.c_int, D, D, D]
+            lib.orc_gradient_printed.argtypes = [P, D, D, ctypes.c_int, D, D]
             lib.orc_complex_step.argtypes = [P, D, D, ctypes.c_int, D, ctypes.c_double, D, D]
             lib.orc_transfer.argtypes = [P, D, D, D, D]
             lib.orc_transfer_T.argtypes = [P, D, D, D]
@@ -144,6 +145,19 @@ def gradient(p, gamma, motion, n_steps=None, init_state=None):
     out = np.zeros_like(g)
     _check(lib.orc_gradient(ctypes.byref(st), _dp(g), _dp(m), N, _dp(_c64(init_state)),
                             ctypes.byref(J), _dp(out)))
+    return J.value, out
+
+
+def gradient_printed(p, gamma, motion, n_steps=None):
+    """Sec. 2.4's adjoint as printed (not the exact discrete adjoint); returns (J, dJ/dgamma)."""
+    lib = _load()
+    N = p.n_steps if n_steps is None else n_steps
+    st = to_struct(p)
+    g = _c64(gamma)
+    J = ctypes.c_double(0.0)
+    out = np.zeros_like(g)
+    _check(lib.orc_gradient_printed(ctypes.byref(st), _dp(g), _dp(_c64(motion)), N,
+                                    ctypes.byref(J), _dp(out)))
     return J.value, out
 
 

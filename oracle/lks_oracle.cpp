@@ -545,8 +545,12 @@ void set_kref_real(Solver<T>& S) {
 // through the transposed transfer (Sec. 2.4, J' = sum 3 kappa'(u - u_S) u~ in the paper's
 // form, here with the exact factor), then transpose the gather and the equilibrium
 // (Eqs. arho, au, as and the adjoint equilibrium) including the transposed gradient stencil.
+// paper = true follows Sec. 2.4's source update as printed instead: the (1 + kappa)^-1 of the
+// Brinkman source (Eq. au_ex) divides only the gathered first moment 3 U~ and the objective
+// source, not the whole adjoint velocity.  (Boundary values keep the transposed copies: with a
+// boundary objective such as J1, dropping them would discard the whole sensitivity.)
 bool adjoint(Solver<double>& S, const std::vector<State<double>>& hist, int N,
-             std::vector<double>& gout) {
+             std::vector<double>& gout, bool paper = false) {
     const orc_problem& p = S.p;
     const Grid& g = S.g;
     const Lattice& L = S.L;
@@ -564,11 +568,17 @@ bool adjoint(Solver<double>& S, const std::vector<State<double>>& hist, int N,
     std::vector<double> kappa;
     std::vector<double> us[3];
     const int sidx[3][3] = {{0, 3, 4}, {3, 1, 5}, {4, 5, 2}};
+    std::vector<double> U3[3], src[3];   // printed variant: 3 U~ of the last moments, J source
+    for (int a = 0; a < 3; ++a) {
+        U3[a].assign(g.nodes, 0.0);
+        src[a].assign(g.nodes, 0.0);
+    }
 
     for (int n = N; n >= 1; --n) {
         const State<double>& sn = hist[n];
         const State<double>& sp = hist[n - 1];
         // (i) direct objective term at level n
+        for (int a = 0; a < 3; ++a) std::fill(src[a].begin(), src[a].end(), 0.0);
         if (n >= p.win_begin && n <= p.win_end) {
             for (int z = 0; z < g.n[2]; ++z)
                 for (int y = 0; y < g.n[1]; ++y)
@@ -577,8 +587,10 @@ bool adjoint(Solver<double>& S, const std::vector<State<double>>& hist, int N,
                         long m = g.idx(x, y, z);
                         if (p.obj_kind == 0) lam.rho[m] += -h / (3.0 * (double)S.count);
                         else
-                            for (int a = 0; a < 3; ++a)
+                            for (int a = 0; a < 3; ++a) {
                                 lam.u[a][m] += -h * p.obj_dir[a] / (double)S.count;
+                                src[a][m] = -h * p.obj_dir[a] / (double)S.count;
+                            }
                     }
         }
         // (ii) transpose of the boundary conditions
@@ -590,13 +602,13 @@ bool adjoint(Solver<double>& S, const std::vector<State<double>>& hist, int N,
                     int f = winning_face(p, g, xa);
                     int sx[3];
                     inward(g, xa, sx);
-                    long b = g.idx(x, y, z), src = g.idx(sx[0], sx[1], sx[2]);
+                    long b = g.idx(x, y, z), so = g.idx(sx[0], sx[1], sx[2]);
                     int t = p.bc[f];
                     if (t == BC_WALL || t == BC_INLET) {
-                        lam.rho[src] += lam.rho[b];
+                        lam.rho[so] += lam.rho[b];
                     } else {
                         int na = f / 2;
-                        lam.u[na][src] += lam.u[na][b];
+                        lam.u[na][so] += lam.u[na][b];
                     }
                     lam.rho[b] = 0.0;
                     for (int a = 0; a < 3; ++a) lam.u[a][b] = 0.0;
@@ -608,7 +620,10 @@ bool adjoint(Solver<double>& S, const std::vector<State<double>>& hist, int N,
             mr[m] = lam.rho[m];
             double ee = 0.0;
             for (int a = 0; a < 3; ++a) {
-                mu[a][m] = lam.u[a][m] / (1.0 + kappa[m]);
+                if (paper)  // only 3 U~ and the source are divided (Eq. au_ex as printed)
+                    mu[a][m] = lam.u[a][m] - (U3[a][m] + src[a][m]) * kappa[m] / (1.0 + kappa[m]);
+                else
+                    mu[a][m] = lam.u[a][m] / (1.0 + kappa[m]);
                 ee += mu[a][m] * (us[a][m] - sn.u[a][m]);
             }
             e[m] = ee;  // boundary nodes carry lam = 0 here, so mu = e = 0 there
@@ -644,6 +659,7 @@ bool adjoint(Solver<double>& S, const std::vector<State<double>>& hist, int N,
                                 Sm[al][be] += (double)(L.c[i][al] * L.c[i][be]) * wF;
                     }
                     nl.rho[m] = R;
+                    for (int a = 0; a < 3; ++a) U3[a][m] = (a < d) ? 3.0 * U[a] : 0.0;
                     for (int al = 0; al < 3; ++al) {
                         double v = 0.0;
                         if (al < d) {
@@ -727,6 +743,24 @@ int orc_gradient(const orc_problem* p, const double* gamma, const double* motion
     if (!S.forward(n_steps, init_state, J, &hist, fin)) return 1;
     std::vector<double> g;
     if (!adjoint(S, hist, n_steps, g)) return 1;
+    if (J_out) *J_out = J;
+    if (g_out) std::memcpy(g_out, g.data(), g.size() * sizeof(double));
+    return 0;
+}
+
+/* The adjoint of Sec. 2.4 as printed (see adjoint()): J and its dJ/dgamma. */
+int orc_gradient_printed(const orc_problem* p, const double* gamma, const double* motion,
+                         int n_steps, double* J_out, double* g_out) {
+    g_err.clear();
+    Solver<double> S;
+    if (!S.init(*p, gamma, motion)) return 1;
+    set_kref_real(S);
+    double J;
+    State<double> fin;
+    std::vector<State<double>> hist;
+    if (!S.forward(n_steps, nullptr, J, &hist, fin)) return 1;
+    std::vector<double> g;
+    if (!adjoint(S, hist, n_steps, g, true)) return 1;
     if (J_out) *J_out = J;
     if (g_out) std::memcpy(g_out, g.data(), g.size() * sizeof(double));
     return 0;

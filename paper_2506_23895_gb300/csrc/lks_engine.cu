@@ -96,6 +96,7 @@ struct lks_ctx {
     void* kref_t;
     void* k2;
     float* face;
+    void* u3;           // 3 U~ of the previous adjoint step (printed-ALKS variant only)
     double* gacc;
     double* jstep;
     TransferScratch ts;
@@ -263,7 +264,7 @@ struct Layout {
 enum {
     L_S0, L_S1, L_SINIT, L_L0, L_L1, L_F, L_MU, L_PHI, L_KUS, L_E, L_GAMMA, L_KREF, L_KPRIME,
     L_GACC, L_JSTEP, L_CBASE, L_CFRAC, L_ZTI, L_ZTW, L_TCNT, L_TIDX, L_TW, L_CM, L_DZB, L_DZF,
-    L_FLAGS, L_KREFT, L_K2, L_FACE, L_TGT, L_POOL, L_COUNT
+    L_FLAGS, L_KREFT, L_K2, L_FACE, L_TGT, L_U3, L_POOL, L_COUNT
 };
 
 Layout make_layout(const lks_config* cfg) {
@@ -300,6 +301,7 @@ Layout make_layout(const lks_config* cfg) {
     sz[L_DZF] = (size_t)std::max(cfg->lz, 1) * T;
     sz[L_FLAGS] = 64;
     sz[L_TGT] = (size_t)std::max(1.0, count_target(cfg)) * 4;
+    sz[L_U3] = (cfg->flags & LKS_FLAG_PAPER_ALKS) ? state : 0;
     sz[L_KREFT] = (size_t)std::max(nd, 1LL) * T;
     sz[L_K2] = nd ? (size_t)cols * std::max(cfg->lz, 1) * T : 0;
     {
@@ -531,9 +533,10 @@ lks_status adjoint_step(lks_ctx* c, int n, const void* sn, const void* sp) {
         return LKS_OK;
     }
     launch_adj_mu<T>(c->g, lc, (const V4<T>*)c->kus, (const V4<T>*)sn, st4<T>(c->mu),
-                     (T*)c->e, hn, c->st);
+                     (T*)c->e, hn, c->st, (const V4<T>*)c->u3);
     LAUNCHED();
-    launch_adj_moments<T>(c->g, st4<T>(c->mu), (const V4<T>*)sp, ln, (T*)c->phi, c->st);
+    launch_adj_moments<T>(c->g, st4<T>(c->mu), (const V4<T>*)sp, ln, (T*)c->phi, c->st,
+                          (V4<T>*)c->u3);
     LAUNCHED();
     launch_adj_divT<T>(c->g, (const T*)c->phi, ln, c->st);
     LAUNCHED();
@@ -609,6 +612,7 @@ template <class T>
 lks_status do_adjoint(lks_ctx* c) {
     CU(cudaMemsetAsync(c->flags, 0, 64, c->st));
     CU(cudaMemsetAsync(c->lam[0], 0, c->snap_bytes, c->st));
+    if (c->u3) CU(cudaMemsetAsync(c->u3, 0, c->snap_bytes, c->st));
     if (c->d.nd > 0) CU(cudaMemsetAsync(c->gacc, 0, (size_t)c->d.nd * 8, c->st));
     for (size_t i = c->adj_begin - 1; i < c->acts.size(); ++i) {
         const Act& a = c->acts[i];
@@ -734,6 +738,7 @@ lks_status lks_create(const lks_config* cfg, void* workspace, size_t ws_bytes, l
     c->kref_t = w + L.off[L_KREFT];
     c->k2 = w + L.off[L_K2];
     c->face = (float*)(w + L.off[L_FACE]);
+    c->u3 = (cfg->flags & LKS_FLAG_PAPER_ALKS) ? (void*)(w + L.off[L_U3]) : nullptr;
     c->gacc = (double*)(w + L.off[L_GACC]);
     c->jstep = (double*)(w + L.off[L_JSTEP]);
     c->ts.col_base = (int*)(w + L.off[L_CBASE]);
@@ -760,7 +765,8 @@ lks_status lks_create(const lks_config* cfg, void* workspace, size_t ws_bytes, l
         c->g.otarget = dt;
     }
     c->ts.err = c->flags + 1;
-    c->fused3d = (c->prec == LKS_FP32) && !(cfg->flags & LKS_FLAG_PLAIN_KERNELS) &&
+    c->fused3d = (c->prec == LKS_FP32) &&
+                 !(cfg->flags & (LKS_FLAG_PLAIN_KERNELS | LKS_FLAG_PAPER_ALKS)) &&
                  fused3d_eligible(g);
     c->pool = w + L.off[L_POOL];
     c->pool_slots = L.pool_slots;

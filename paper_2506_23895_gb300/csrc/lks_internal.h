@@ -85,12 +85,13 @@ template <class T>
 void launch_objective(const Geom& g, const V4<T>* s, double* jstep, cudaStream_t st);
 template <class T>
 void launch_adj_bcT(const Geom& g, V4<T>* lam, double h, cudaStream_t st);
+// u3 (optional): 3 U~ of the last moments, for the printed-ALKS variant (else nullptr).
 template <class T>
 void launch_adj_mu(const Geom& g, const V4<T>* lam, const V4<T>* kus, const V4<T>* sn,
-                   V4<T>* mu, T* e, double h, cudaStream_t st);
+                   V4<T>* mu, T* e, double h, cudaStream_t st, const V4<T>* u3 = nullptr);
 template <class T>
 void launch_adj_moments(const Geom& g, const V4<T>* mu, const V4<T>* sp, V4<T>* lam_out,
-                        T* phi, cudaStream_t st);
+                        T* phi, cudaStream_t st, V4<T>* u3 = nullptr);
 template <class T>
 void launch_adj_divT(const Geom& g, const T* phi, V4<T>* lam_out, cudaStream_t st);
 template <class T>

@@ -10,7 +10,7 @@
 // into the moments of Eqs. arho, au, as and the adjoint equilibrium, k_adj_divT adds the
 // transposed velocity-gradient term.  These kernels are templated on the scalar type; the
 // double instantiation is the plain FP64 path.
-#include "lks_device.cuh"
+#include "lks_units.cuh"
 
 namespace lks {
 
@@ -152,44 +152,10 @@ __global__ void k_gather(Geom g, const T* __restrict__ F, const V4<T>* __restric
     write_bc_from(g, x, y, z, o, out);
 }
 
-// Objective at one level (Sec. 2.5): j = -mean(rho)/3 or -mean(n.u) over the target region,
-// one block, fixed-order FP64 reduction.
+// Objective at one level (Sec. 2.5): one block (objective_block).
 template <class T>
 __global__ void k_objective(Geom g, const V4<T>* __restrict__ s, double* jstep) {
-    __shared__ double red[kThreads];
-    const int tot = (int)g.ocount;
-    double acc = 0.0;
-    for (int k = threadIdx.x; k < tot; k += blockDim.x) {
-        const V4<T> v = s[g.otarget[k]];
-        if (g.okind == 0)
-            acc += (double)v.r;
-        else
-            acc += g.odir[0] * (double)v.x + g.odir[1] * (double)v.y + g.odir[2] * (double)v.z;
-    }
-    red[threadIdx.x] = acc;
-    __syncthreads();
-    for (int w = kThreads / 2; w > 0; w >>= 1) {
-        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        double sum = red[0];
-        jstep[0] = (g.okind == 0) ? -(g.rho0 + sum / g.ocount) / 3.0 : -sum / g.ocount;
-    }
-}
-
-// Objective's direct adjoint source at one node (h = window weight or 0 outside the window).
-template <class T>
-__device__ __forceinline__ void obj_source(const Geom& g, int x, int y, int z, double h,
-                                           V4<T>& l) {
-    if (h == 0.0 || !in_target(g, x, y, z)) return;
-    if (g.okind == 0) {
-        l.r += (T)(-h / (3.0 * g.ocount));
-    } else {
-        l.x += (T)(-h * g.odir[0] / g.ocount);
-        l.y += (T)(-h * g.odir[1] / g.ocount);
-        l.z += (T)(-h * g.odir[2] / g.ocount);
-    }
+    objective_block<T>(g, s, jstep);
 }
 
 // Transpose of the boundary copies: each interior node adjacent to the boundary collects the
@@ -235,23 +201,7 @@ __global__ void k_adj_bcT(Geom g, V4<T>* lam, double h) {
     const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     int x, y, z;
     if (!shell_node(g, t, x, y, z)) return;
-    const long long m = node_index(g, x, y, z);
-    if (!sources_boundary(g, x, y, z)) return;
-    V4<T> acc = lam[m];
-    for_each_sourced_boundary(g, x, y, z, [&](int bx, int by, int bz, int f) {
-        V4<T> lb = lam[node_index(g, bx, by, bz)];
-        obj_source(g, bx, by, bz, h, lb);
-        const int t = g.bc[f];
-        if (t == BC_WALL || t == BC_INLET) {
-            acc.r += lb.r;
-        } else {
-            const int na = f / 2;
-            if (na == 0) acc.x += lb.x;
-            if (na == 1) acc.y += lb.y;
-            if (na == 2) acc.z += lb.z;
-        }
-    });
-    lam[m] = acc;
+    bcT_node<T>(g, lam, h, x, y, z);
 }
 
 // mu = (lam_rho, lam_u / (1 + kappa)) on interior nodes, 0 on boundary nodes; in the
@@ -259,7 +209,7 @@ __global__ void k_adj_bcT(Geom g, V4<T>* lam, double h) {
 template <class T>
 __global__ void k_adj_mu(Geom g, const V4<T>* __restrict__ lam, const V4<T>* __restrict__ kus,
                          const V4<T>* __restrict__ sn, V4<T>* __restrict__ mu,
-                         T* __restrict__ e, double h) {
+                         T* __restrict__ e, double h, const V4<T>* __restrict__ u3) {
     long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (m >= g.nodes) return;
     int x, y, z;
@@ -277,9 +227,23 @@ __global__ void k_adj_mu(Geom g, const V4<T>* __restrict__ lam, const V4<T>* __r
     if (in_box(g, x, y, z, bi)) {
         const V4<T> ks = kus[bi];
         const T inv = (T)1 / ((T)1 + ks.r);
-        o.x = l.x * inv;
-        o.y = l.y * inv;
-        o.z = l.z * inv;
+        if (u3) {
+            // printed ALKS (Eqs. au, au_ex): only the gathered first moment 3 U~ and the
+            // objective source take the (1 + kappa)^-1 of the Brinkman term
+            const V4<T> a3 = u3[m];
+            V4<T> src = l;
+            src.x = l.x - lam[m].x;
+            src.y = l.y - lam[m].y;
+            src.z = l.z - lam[m].z;
+            const T fac = ks.r * inv;
+            o.x = l.x - (a3.x + src.x) * fac;
+            o.y = l.y - (a3.y + src.y) * fac;
+            o.z = l.z - (a3.z + src.z) * fac;
+        } else {
+            o.x = l.x * inv;
+            o.y = l.y * inv;
+            o.z = l.z * inv;
+        }
         const V4<T> v = sn[m];
         e[bi] = o.x * (ks.x - v.x) + o.y * (ks.y - v.y) + o.z * (ks.z - v.z);
     } else {
@@ -299,7 +263,7 @@ __device__ __forceinline__ int sym6(int a, int b) {
 template <class T, int D>
 __global__ void k_adj_moments(Geom g, const V4<T>* __restrict__ mu,
                               const V4<T>* __restrict__ sp, V4<T>* __restrict__ lo,
-                              T* __restrict__ phi) {
+                              T* __restrict__ phi, V4<T>* __restrict__ u3) {
     using L = Lat<D>;
     long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (m >= g.nodes) return;
@@ -353,6 +317,14 @@ __global__ void k_adj_moments(Geom g, const V4<T>* __restrict__ mu,
     o.y = lu[1];
     o.z = lu[2];
     lo[m] = o;
+    if (u3) {
+        V4<T> a;
+        a.r = (T)0;
+        a.x = (T)3 * U[0];
+        a.y = (T)3 * U[1];
+        a.z = (D == 3) ? (T)3 * U[2] : (T)0;
+        u3[m] = a;
+    }
     const T twoA = (T)(2.0 * g.A);
 #pragma unroll
     for (int k = 0; k < 6; ++k) phi[(long long)k * g.nodes + m] = twoA * S[k];
@@ -455,7 +427,7 @@ void launch_gather(const Geom& g, const T* F, const V4<T>* kus, V4<T>* out, cuda
 
 template <class T>
 void launch_objective(const Geom& g, const V4<T>* s, double* jstep, cudaStream_t st) {
-    k_objective<T><<<1, kThreads, 0, st>>>(g, s, jstep);
+    k_objective<T><<<1, kObjThreads, 0, st>>>(g, s, jstep);
 }
 
 template <class T>
@@ -467,17 +439,17 @@ void launch_adj_bcT(const Geom& g, V4<T>* lam, double h, cudaStream_t st) {
 
 template <class T>
 void launch_adj_mu(const Geom& g, const V4<T>* lam, const V4<T>* kus, const V4<T>* sn,
-                   V4<T>* mu, T* e, double h, cudaStream_t st) {
-    k_adj_mu<T><<<grid_for(g.nodes), kThreads, 0, st>>>(g, lam, kus, sn, mu, e, h);
+                   V4<T>* mu, T* e, double h, cudaStream_t st, const V4<T>* u3) {
+    k_adj_mu<T><<<grid_for(g.nodes), kThreads, 0, st>>>(g, lam, kus, sn, mu, e, h, u3);
 }
 
 template <class T>
 void launch_adj_moments(const Geom& g, const V4<T>* mu, const V4<T>* sp, V4<T>* lam_out,
-                        T* phi, cudaStream_t st) {
+                        T* phi, cudaStream_t st, V4<T>* u3) {
     if (g.dim == 2)
-        k_adj_moments<T, 2><<<grid_for(g.nodes), kThreads, 0, st>>>(g, mu, sp, lam_out, phi);
+        k_adj_moments<T, 2><<<grid_for(g.nodes), kThreads, 0, st>>>(g, mu, sp, lam_out, phi, u3);
     else
-        k_adj_moments<T, 3><<<grid_for(g.nodes), kThreads, 0, st>>>(g, mu, sp, lam_out, phi);
+        k_adj_moments<T, 3><<<grid_for(g.nodes), kThreads, 0, st>>>(g, mu, sp, lam_out, phi, u3);
 }
 
 template <class T>
@@ -510,9 +482,9 @@ void launch_state_from_f64(const Geom& g, const double* in, V4<T>* s, cudaStream
     template void launch_objective<T>(const Geom&, const V4<T>*, double*, cudaStream_t);     \
     template void launch_adj_bcT<T>(const Geom&, V4<T>*, double, cudaStream_t);              \
     template void launch_adj_mu<T>(const Geom&, const V4<T>*, const V4<T>*, const V4<T>*,    \
-                                   V4<T>*, T*, double, cudaStream_t);                        \
+                                   V4<T>*, T*, double, cudaStream_t, const V4<T>*);          \
     template void launch_adj_moments<T>(const Geom&, const V4<T>*, const V4<T>*, V4<T>*, T*, \
-                                        cudaStream_t);                                       \
+                                        cudaStream_t, V4<T>*);                               \
     template void launch_adj_divT<T>(const Geom&, const T*, V4<T>*, cudaStream_t);           \
     template void launch_check_state<T>(const Geom&, const V4<T>*, int*, cudaStream_t);      \
     template void launch_state_to_f64<T>(const Geom&, const V4<T>*, double*, cudaStream_t);  \

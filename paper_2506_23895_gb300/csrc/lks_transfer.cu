@@ -16,7 +16,7 @@
 //                 the box: deterministic gathers, no atomics;
 //   k_sens        for each design node, sum_x W(x - x_ref) e(x) over its 4^d support (the
 //                 transpose of the kappa transfer), accumulated into dJ/dgamma in FP64.
-#include "lks_device.cuh"
+#include "lks_units.cuh"
 
 namespace lks {
 
@@ -50,17 +50,8 @@ __global__ void k_design_prep(long long nd, long long ncol, int lz,
 template <class T>
 __global__ void k_design_pos(Design d, Geom g, Motion m, TransferScratch ts) {
     long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    T* frac = (T*)ts.col_frac;
     if (k < d.ncol) {
-        const int i = (int)((unsigned)k % (unsigned)d.L[0]), j = (int)((unsigned)k / (unsigned)d.L[0]);
-        const double dx = i - d.xiG[0], dy = j - d.xiG[1];
-        const double xr = m.c * dx - m.s * dy + m.xG[0];   // Eq. rigid_body_position
-        const double yr = m.s * dx + m.c * dy + m.xG[1];
-        const double bx = floor(xr), by = floor(yr);
-        ts.col_base[2 * k] = (int)bx;
-        ts.col_base[2 * k + 1] = (int)by;
-        frac[2 * k] = (T)(xr - bx);
-        frac[2 * k + 1] = (T)(yr - by);
+        design_col_pos<T>(d, m, ts, k);
         return;
     }
     k -= d.ncol;
@@ -202,65 +193,14 @@ __global__ void k_fill(Design d, Geom g, Motion m, TransferScratch ts, const T* 
     kus[bi] = o;
 }
 
-// Sensitivity gather: for each design node, sum_x W(x - x_ref) e(x) over its support (the
-// transpose of the kappa transfer), times kappa', added to dJ/dgamma in FP64.  The z shift is
-// the same for every design plane, so one thread takes a design column and kSensRun planes:
-// each analysis plane's 4 x 4 x-y tap sum is formed once and the four z weights slide over them.
-constexpr int kSensRun = 8;
-
+// Sensitivity gather: one thread per design column and kSensRun planes (sens_run).
 template <class T>
 __global__ void k_sens(Design d, Geom g, TransferScratch ts, const T* __restrict__ e,
                        const T* __restrict__ kprime, double* __restrict__ gacc) {
     const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const unsigned runs = (unsigned)((d.L[2] + kSensRun - 1) / kSensRun);
     if (t >= (long long)d.ncol * runs) return;
-    const unsigned k = (unsigned)t % (unsigned)d.ncol;   // design column
-    const int z0 = (int)((unsigned)t / (unsigned)d.ncol) * kSensRun;
-    const int z1 = min(d.L[2], z0 + kSensRun);
-    const T* frac = (const T*)ts.col_frac;
-    const int bx = ts.col_base[2 * k], by = ts.col_base[2 * k + 1];
-    const T fx = frac[2 * k], fy = frac[2 * k + 1];
-    T wx[4], wy[4], wz[4];
-    const T fz = ((const T*)ts.dz_frac)[0];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        wx[q] = peskin((T)(q - 1) - fx);
-        wy[q] = peskin((T)(q - 1) - fy);
-        wz[q] = (g.dim == 3) ? peskin((T)(q - 1) - fz) : (q == 1 ? (T)1 : (T)0);
-    }
-    const int ex0 = bx - 1 - g.blo[0], ey0 = by - 1 - g.blo[1];
-    // x-y tap sum of analysis plane z (0 outside the box, where W vanishes)
-    auto plane_sum = [&](int z) -> T {
-        const int ez = z - g.blo[2];
-        if (ez < 0 || ez >= g.bn[2]) return (T)0;
-        const T* ep = e + (long long)ez * g.bn[1] * g.bn[0];
-        T acc = (T)0;
-#pragma unroll
-        for (int ty = 0; ty < 4; ++ty) {
-            const int ey = ey0 + ty;
-            if (ey < 0 || ey >= g.bn[1] || wy[ty] == (T)0) continue;
-#pragma unroll
-            for (int tx = 0; tx < 4; ++tx) {
-                const int ex = ex0 + tx;
-                const T W = wx[tx] * wy[ty];
-                if (ex < 0 || ex >= g.bn[0] || W == (T)0) continue;
-                acc += W * ep[(long long)ey * g.bn[0] + ex];
-            }
-        }
-        return acc;
-    };
-    const int zb0 = (g.dim == 3) ? ts.dz_base[z0] : 0;   // analysis base plane of design plane z0
-    T s0 = plane_sum(zb0 - 1), s1 = plane_sum(zb0), s2 = plane_sum(zb0 + 1);
-    for (int zeta = z0; zeta < z1; ++zeta) {
-        const int zb = zb0 + (zeta - z0);
-        const T s3 = (g.dim == 3) ? plane_sum(zb + 2) : (T)0;
-        const T acc = wz[0] * s0 + wz[1] * s1 + wz[2] * s2 + wz[3] * s3;
-        const long long dn = (long long)zeta * d.ncol + k;
-        gacc[dn] += (double)kprime[dn] * (double)acc;
-        s0 = s1;
-        s1 = s2;
-        s2 = s3;
-    }
+    sens_run<T>(d, g, ts, e, kprime, gacc, t);
 }
 
 template <class T>

@@ -55,6 +55,7 @@ class LksConfig(ctypes.Structure):
 
 
 FLAG_PLAIN_KERNELS = 1
+FLAG_PAPER_ALKS = 2
 
 
 class LksMotion(ctypes.Structure):

@@ -68,3 +68,17 @@ def test_taylor_remainder_is_second_order():
         Jh, _ = oracle.forward(w.problem, w.gamma + h * d, w.motion)
         rem.append(abs(Jh - J - h * (g * d).sum()))
     assert 3.2 < rem[0] / rem[1] < 4.8 and 3.2 < rem[1] / rem[2] < 4.8
+
+
+def test_printed_alks_variant_reduces_to_exact_without_body():
+    """The printed source update (Eq. au_ex, 1/(1+kappa) on the first moment only) differs from
+    the exact adjoint only through kappa: with gamma = 0 (kappa = 0) the two coincide, and with
+    a body they differ."""
+    w = CASES["3d_J2"]()
+    zero = np.zeros_like(w.gamma)
+    _, g0 = oracle.gradient(w.problem, zero, w.motion)
+    _, p0 = oracle.gradient_printed(w.problem, zero, w.motion)
+    assert np.max(np.abs(p0 - g0)) <= 1e-13 * np.max(np.abs(g0))
+    _, g = oracle.gradient(w.problem, w.gamma, w.motion)
+    _, p = oracle.gradient_printed(w.problem, w.gamma, w.motion)
+    assert np.linalg.norm(p - g) > 1e-3 * np.linalg.norm(g)
