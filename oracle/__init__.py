@@ -63,10 +63,11 @@ def _load():
             lib = ctypes.CDLL(_SO)
             P = ctypes.POINTER(OrcProblem)
             D = ctypes.POINTER(ctypes.c_double)
-            lib.orc_forward.argtypes = [P, D, D, ctypes.c_int, D, D, D]
-            lib.orc_gradient.argtypes = [P, D, D, ctypes.c_int, D, D, D]
+            lib.orc_forward.argtypes = [P, D, D, ctypes.c_int, D, D, D, D, D]
+            lib.orc_gradient.argtypes = [P, D, D, ctypes.c_int, D, D, D, D, D, D]
             lib.orc_gradient_printed.argtypes = [P, D, D, ctypes.c_int, D, D]
-            lib.orc_complex_step.argtypes = [P, D, D, ctypes.c_int, D, ctypes.c_double, D, D]
+            lib.orc_complex_step.argtypes = [P, D, D, ctypes.c_int, D, D, D, ctypes.c_double, D,
+                                             D]
             lib.orc_transfer.argtypes = [P, D, D, D, D]
             lib.orc_transfer_T.argtypes = [P, D, D, D]
             lib.orc_error.restype = ctypes.c_char_p
@@ -119,23 +120,28 @@ def _gamma_or_empty(p, gamma):
     return _c64(gamma)
 
 
-def forward(p, gamma, motion, n_steps=None, init_state=None):
-    """Alg. 1 from the initial state; returns (J, final_state[4, nz, ny, nx])."""
+def forward(p, gamma, motion, n_steps=None, init_state=None, kstatic=None, lam_term=None):
+    """Alg. 1 from the initial state; returns (J, final_state[4, nz, ny, nx]).
+
+    kstatic: static Brinkman coefficient per analysis node (solid at rest), shape
+    (nz, ny, nx); lam_term: planes (4, nz, ny, nx) of a terminal term <lam_term, s^N> added
+    to J."""
     lib = _load()
     N = p.n_steps if n_steps is None else n_steps
     st = to_struct(p)
     g = _gamma_or_empty(p, gamma)
     m = _c64(motion)
-    init = _c64(init_state)
     J = ctypes.c_double(0.0)
     out = np.zeros((4, p.n[2], p.n[1], p.n[0]), dtype=np.float64)
-    _check(lib.orc_forward(ctypes.byref(st), _dp(g), _dp(m), N, _dp(init), ctypes.byref(J),
-                           _dp(out)))
+    _check(lib.orc_forward(ctypes.byref(st), _dp(g), _dp(m), N, _dp(_c64(init_state)),
+                           _dp(_c64(kstatic)), _dp(_c64(lam_term)), ctypes.byref(J), _dp(out)))
     return J.value, out
 
 
-def gradient(p, gamma, motion, n_steps=None, init_state=None):
-    """Forward plus exact discrete adjoint; returns (J, dJ/dgamma with gamma's shape)."""
+def gradient(p, gamma, motion, n_steps=None, init_state=None, kstatic=None, lam_term=None,
+             want_lam0=False):
+    """Forward plus exact discrete adjoint; returns (J, dJ/dgamma with gamma's shape), plus
+    lambda^0 (planes) when want_lam0."""
     lib = _load()
     N = p.n_steps if n_steps is None else n_steps
     st = to_struct(p)
@@ -143,9 +149,11 @@ def gradient(p, gamma, motion, n_steps=None, init_state=None):
     m = _c64(motion)
     J = ctypes.c_double(0.0)
     out = np.zeros_like(g)
+    lam0 = np.zeros((4, p.n[2], p.n[1], p.n[0]), dtype=np.float64) if want_lam0 else None
     _check(lib.orc_gradient(ctypes.byref(st), _dp(g), _dp(m), N, _dp(_c64(init_state)),
-                            ctypes.byref(J), _dp(out)))
-    return J.value, out
+                            _dp(_c64(kstatic)), _dp(_c64(lam_term)), ctypes.byref(J), _dp(out),
+                            _dp(lam0)))
+    return (J.value, out, lam0) if want_lam0 else (J.value, out)
 
 
 def gradient_printed(p, gamma, motion, n_steps=None):
@@ -161,7 +169,8 @@ def gradient_printed(p, gamma, motion, n_steps=None):
     return J.value, out
 
 
-def complex_step(p, gamma, motion, direction, h=1e-30, n_steps=None):
+def complex_step(p, gamma, motion, direction, h=1e-30, n_steps=None, kstatic=None,
+                 lam_term=None):
     """Directional derivative dJ/dgamma . direction by the complex step; returns (dJ, J)."""
     lib = _load()
     N = p.n_steps if n_steps is None else n_steps
@@ -171,8 +180,9 @@ def complex_step(p, gamma, motion, direction, h=1e-30, n_steps=None):
     m = _c64(motion)
     dJ = ctypes.c_double(0.0)
     J = ctypes.c_double(0.0)
-    _check(lib.orc_complex_step(ctypes.byref(st), _dp(g), _dp(m), N, _dp(d), h,
-                                ctypes.byref(dJ), ctypes.byref(J)))
+    _check(lib.orc_complex_step(ctypes.byref(st), _dp(g), _dp(m), N, _dp(_c64(kstatic)),
+                                _dp(_c64(lam_term)), _dp(d), h, ctypes.byref(dJ),
+                                ctypes.byref(J)))
     return dJ.value, J.value
 
 

@@ -363,6 +363,7 @@ struct Solver {
     Lattice L;
     std::vector<T> kref;
     std::vector<double> gamma;
+    std::vector<double> ks;   // static Brinkman coefficient per analysis node (empty: none)
     const double* motion;
     long count;
 
@@ -496,15 +497,19 @@ struct Solver {
                     }
                     out.rho[m] = rs;
                     T k = kappa[m];
+                    // implicit Brinkman update (Eq. u_ex_2); a static solid adds kappa_s with
+                    // zero solid velocity to the denominator
+                    const double kst = ks.empty() ? 0.0 : ks[m];
                     for (int a = 0; a < 3; ++a)
-                        out.u[a][m] = (us_[a] + p.body_force[a] + k * us[a][m]) / (1.0 + k);
+                        out.u[a][m] = (us_[a] + p.body_force[a] + k * us[a][m]) / (1.0 + k + kst);
                     if (d == 2) out.u[2][m] = T(0);
                 }
         apply_bc(out);
         return true;
     }
 
-    bool forward(int N, const double* init, T& J, std::vector<State<T>>* hist, State<T>& fin) {
+    bool forward(int N, const double* init, T& J, std::vector<State<T>>* hist, State<T>& fin,
+                 const double* lam_term = nullptr) {
         State<T> s, t;
         initial(s, init);
         if (hist) {
@@ -522,6 +527,11 @@ struct Solver {
             if (hist) hist->push_back(s);
         }
         fin = s;
+        if (lam_term)   // terminal term <lam_term, s^N> of an augmented objective
+            for (long m = 0; m < g.nodes; ++m) {
+                J += lam_term[m] * s.rho[m];
+                for (int a = 0; a < 3; ++a) J += lam_term[(1 + a) * g.nodes + m] * s.u[a][m];
+            }
         return true;
     }
 };
@@ -550,7 +560,8 @@ void set_kref_real(Solver<T>& S) {
 // source, not the whole adjoint velocity.  (Boundary values keep the transposed copies: with a
 // boundary objective such as J1, dropping them would discard the whole sensitivity.)
 bool adjoint(Solver<double>& S, const std::vector<State<double>>& hist, int N,
-             std::vector<double>& gout, bool paper = false) {
+             std::vector<double>& gout, bool paper = false, const double* lam_term = nullptr,
+             double* lam0_out = nullptr) {
     const orc_problem& p = S.p;
     const Grid& g = S.g;
     const Lattice& L = S.L;
@@ -563,6 +574,11 @@ bool adjoint(Solver<double>& S, const std::vector<State<double>>& hist, int N,
 
     State<double> lam, nl;
     lam.resize(g.nodes);
+    if (lam_term)   // adjoint of a terminal term <lam_term, s^N>: lambda^N starts there
+        for (long m = 0; m < g.nodes; ++m) {
+            lam.rho[m] = lam_term[m];
+            for (int a = 0; a < 3; ++a) lam.u[a][m] = lam_term[(1 + a) * g.nodes + m];
+        }
     std::vector<double> mr(g.nodes), mu[3], e(g.nodes), St((size_t)6 * g.nodes), tmp;
     for (int a = 0; a < 3; ++a) mu[a].assign(g.nodes, 0.0);
     std::vector<double> kappa;
@@ -619,11 +635,12 @@ bool adjoint(Solver<double>& S, const std::vector<State<double>>& hist, int N,
         for (long m = 0; m < g.nodes; ++m) {
             mr[m] = lam.rho[m];
             double ee = 0.0;
+            const double kt = kappa[m] + (S.ks.empty() ? 0.0 : S.ks[m]);
             for (int a = 0; a < 3; ++a) {
                 if (paper)  // only 3 U~ and the source are divided (Eq. au_ex as printed)
-                    mu[a][m] = lam.u[a][m] - (U3[a][m] + src[a][m]) * kappa[m] / (1.0 + kappa[m]);
+                    mu[a][m] = lam.u[a][m] - (U3[a][m] + src[a][m]) * kt / (1.0 + kt);
                 else
-                    mu[a][m] = lam.u[a][m] / (1.0 + kappa[m]);
+                    mu[a][m] = lam.u[a][m] / (1.0 + kt);
                 ee += mu[a][m] * (us[a][m] - sn.u[a][m]);
             }
             e[m] = ee;  // boundary nodes carry lam = 0 here, so mu = e = 0 there
@@ -695,6 +712,11 @@ bool adjoint(Solver<double>& S, const std::vector<State<double>>& hist, int N,
                 }
         std::swap(lam, nl);
     }
+    if (lam0_out)
+        for (long m = 0; m < g.nodes; ++m) {
+            lam0_out[m] = lam.rho[m];
+            for (int a = 0; a < 3; ++a) lam0_out[(1 + a) * g.nodes + m] = lam.u[a][m];
+        }
     return true;
 }
 
@@ -715,34 +737,46 @@ extern "C" {
 
 const char* orc_error(void) { return g_err.c_str(); }
 
+/* kstatic (may be NULL): static Brinkman coefficient per analysis node (solid velocity 0).
+ * lam_term (may be NULL): planes (rho, ux, uy, uz) of a terminal term <lam_term, s^N> added
+ * to J; the adjoint then starts from lambda^N = lam_term (a warm-started adjoint). */
+static void set_static(Solver<double>& S, const double* kstatic) {
+    if (kstatic) S.ks.assign(kstatic, kstatic + S.g.nodes);
+}
+
 /* Forward run (Alg. 1): returns J; optionally the final state as planes (rho, ux, uy, uz). */
 int orc_forward(const orc_problem* p, const double* gamma, const double* motion, int n_steps,
-                const double* init_state, double* J_out, double* final_state) {
+                const double* init_state, const double* kstatic, const double* lam_term,
+                double* J_out, double* final_state) {
     g_err.clear();
     Solver<double> S;
     if (!S.init(*p, gamma, motion)) return 1;
     set_kref_real(S);
+    set_static(S, kstatic);
     double J;
     State<double> fin;
-    if (!S.forward(n_steps, init_state, J, nullptr, fin)) return 1;
+    if (!S.forward(n_steps, init_state, J, nullptr, fin, lam_term)) return 1;
     if (J_out) *J_out = J;
     if (final_state) copy_state_out(S.g, fin, final_state);
     return 0;
 }
 
-/* Forward run keeping every level, then the exact discrete adjoint: J and dJ/dgamma. */
+/* Forward run keeping every level, then the exact discrete adjoint: J and dJ/dgamma, and
+ * optionally lambda^0 (planes) at the end of the sweep. */
 int orc_gradient(const orc_problem* p, const double* gamma, const double* motion, int n_steps,
-                 const double* init_state, double* J_out, double* g_out) {
+                 const double* init_state, const double* kstatic, const double* lam_term,
+                 double* J_out, double* g_out, double* lam0_out) {
     g_err.clear();
     Solver<double> S;
     if (!S.init(*p, gamma, motion)) return 1;
     set_kref_real(S);
+    set_static(S, kstatic);
     double J;
     State<double> fin;
     std::vector<State<double>> hist;
-    if (!S.forward(n_steps, init_state, J, &hist, fin)) return 1;
+    if (!S.forward(n_steps, init_state, J, &hist, fin, lam_term)) return 1;
     std::vector<double> g;
-    if (!adjoint(S, hist, n_steps, g)) return 1;
+    if (!adjoint(S, hist, n_steps, g, false, lam_term, lam0_out)) return 1;
     if (J_out) *J_out = J;
     if (g_out) std::memcpy(g_out, g.data(), g.size() * sizeof(double));
     return 0;
@@ -768,14 +802,16 @@ int orc_gradient_printed(const orc_problem* p, const double* gamma, const double
 
 /* Complex-step directional derivative: dJ = Im J(gamma + i h dir) / h, and Re J. */
 int orc_complex_step(const orc_problem* p, const double* gamma, const double* motion,
-                     int n_steps, const double* dir, double h, double* dJ_out, double* J_out) {
+                     int n_steps, const double* kstatic, const double* lam_term,
+                     const double* dir, double h, double* dJ_out, double* J_out) {
     g_err.clear();
     Solver<cplx> S;
     if (!S.init(*p, gamma, motion)) return 1;
     S.set_kref_complex(dir, h);
+    if (kstatic) S.ks.assign(kstatic, kstatic + S.g.nodes);
     cplx J;
     State<cplx> fin;
-    if (!S.forward(n_steps, nullptr, J, nullptr, fin)) return 1;
+    if (!S.forward(n_steps, nullptr, J, nullptr, fin, lam_term)) return 1;
     if (dJ_out) *dJ_out = J.imag() / h;
     if (J_out) *J_out = J.real();
     return 0;

@@ -259,6 +259,26 @@ def config(idx: int, n_steps: Optional[int] = None) -> Workload:
     return Workload(p, g, m)
 
 
+def batch_config2(n_inst: int = 64, n_steps: int = 5000, side: Tuple[int, int] = (128, 512),
+                  seed: int = 2) -> List[Workload]:
+    """The batched 2D workload: n_inst independent channels with square analysis grids of side
+    N drawn uniformly from side[0]..side[1], a centred design grid of side round(0.4 N) with its
+    own gamma (sigma 3) rotating at a rim speed drawn from U[0.025, 0.1], viscosity from
+    Re = 100 on the design side (nu = 0.05 L_D / 100), J1 over the last 10 % of the steps."""
+    r = splitmix64_uniform(seed, 2 * n_inst)
+    out = []
+    for i in range(n_inst):
+        N = side[0] + min(side[1] - side[0], int(r[2 * i] * (side[1] - side[0] + 1)))
+        LD = max(4, int(round(0.4 * N)))
+        rim = 0.025 + 0.075 * r[2 * i + 1]
+        p, c = channel2d(N, LD, n_steps, _last_fraction(n_steps), nu=0.05 * LD / 100.0,
+                         name=f"batch2d_{i}_{N}")
+        m = motion_table(n_steps, (c, c, 0.0), omega=rim / (LD / 2.0))
+        g = make_gamma((LD, LD, 1), 3.0, seed=1000 * seed + i)
+        out.append(Workload(p, g, m))
+    return out
+
+
 def small_channel2d(nx: int = 24, ny: int = 20, LD: int = 8, n_steps: int = 40,
                     omega: float = 0.02, trans_amp: float = 1.5, seed: int = 11,
                     obj_kind: int = OBJ_PRESSURE, A: float = 0.45) -> Workload:
@@ -309,6 +329,38 @@ def periodic_box(dim: int, n: Tuple[int, int, int], A: float = 0.4,
     return Problem(dim=dim, n=n, L=L, A=A, bc=(PERIODIC,) * 6,
                    obj_kind=OBJ_PRESSURE, obj_box=(0, n[0] - 1, 0, n[1] - 1, 0, n[2] - 1),
                    win=(1, n_steps), n_steps=n_steps, name="periodic")
+
+
+def static_box(p: Problem, box: Tuple[int, int, int, int, int, int], kappa: float) -> np.ndarray:
+    """Static Brinkman field (nz, ny, nx): kappa on the inclusive box x0,x1,y0,y1,z0,z1."""
+    nx, ny, nz = p.n
+    k = np.zeros((nz, ny, nx), dtype=np.float64)
+    k[box[4]:box[5] + 1, box[2]:box[3] + 1, box[0]:box[1] + 1] = kappa
+    return k
+
+
+def taylor_couette(N: int = 200, r1: float = 45.0, r2: float = 70.0, u_d: float = 0.01,
+                   A: float = 0.3, n_steps: int = 12000, kappa_max: float = 100.0) -> Tuple[
+                       Workload, np.ndarray]:
+    """The appendix's verification case: in a periodic N x N box an inner disk of radius r1
+    (a solid design, gamma = 1) rotates at omega = u_d / r1 about the centre inside a fixed
+    outer wall, a static solid outside radius r2.  Returns the workload and the static field."""
+    LD = int(2 * math.ceil(r1) + 10)
+    c = (N - 1) / 2.0
+    p = periodic_box(2, (N, N, 1), A=A, L=(LD, LD, 1), n_steps=n_steps)
+    p.kappa_max = kappa_max
+    p.xi_G = ((LD - 1) / 2.0, (LD - 1) / 2.0, 0.0)
+    p.obj_kind = OBJ_VELOCITY
+    p.obj_dir = (1.0, 0.0, 0.0)
+    p.obj_box = (0, N - 1, 0, N - 1, 0, 0)
+    p.win = (n_steps, n_steps)
+    p.name = "taylor_couette"
+    ii, jj = np.meshgrid(np.arange(LD), np.arange(LD))
+    g = ((ii - p.xi_G[0]) ** 2 + (jj - p.xi_G[1]) ** 2 <= r1 * r1).astype(np.float64)[None]
+    m = motion_table(n_steps, (c, c, 0.0), omega=u_d / r1)
+    xx, yy = np.meshgrid(np.arange(N), np.arange(N))
+    ks = np.where((xx - c) ** 2 + (yy - c) ** 2 >= r2 * r2, kappa_max, 0.0)[None]
+    return Workload(p, g, m), ks
 
 
 def initial_state(p: Problem, rho: Optional[np.ndarray] = None,
