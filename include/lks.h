@@ -118,6 +118,44 @@ lks_status lks_create(const lks_config* cfg, void* workspace, size_t ws_bytes, l
  * Values must lie in [0,1] (LKS_ERR_ARG otherwise).  Invalidates any forward run. */
 lks_status lks_set_design(lks_ctx* ctx, const double* gamma, int on_device);
 
+/* Design chain around the solver: the density filter and Heaviside projection the paper uses
+ * to binarise designs (Secs. 1 and 3.1: filter radius R = 2.4 cells, steepness beta from 1 in
+ * continuation).  With R > 0 the solver sees gb = H(F gamma), F the linear-weight density
+ * filter gt_i = sum_j w_ij gamma_j / sum_j w_ij, w_ij = max(0, R - |xi_i - xi_j|) over the
+ * design grid, H(t) = [tanh(beta eta) + tanh(beta (t - eta))] / [tanh(beta eta) +
+ * tanh(beta (1 - eta))]; lks_adjoint then returns dJ/dgamma = F^T (H'(F gamma) dJ/dgb).
+ * R = 0 (the default) switches the chain off.  Re-applies to the current design and
+ * invalidates any forward run.  LKS_ERR_ARG unless R >= 0 and, for R > 0, beta > 0 and
+ * 0 < eta < 1. */
+lks_status lks_set_filter(lks_ctx* ctx, double R, double beta, double eta);
+
+/* Volume constraint of Sec. 2.1 (Eq. constraint) on the field the solver sees (gb with the
+ * filter chain, else gamma), unit cell volumes: G = sum / (vmax * design nodes) - 1, written to
+ * *G_out (host).  dGdgamma (design nodes doubles, host or device if on_device; may be NULL)
+ * receives dG/dgamma through the chain.  LKS_ERR_ORDER without a design, LKS_ERR_ARG if
+ * vmax <= 0.  Synchronises. */
+lks_status lks_volume(lks_ctx* ctx, double vmax, double* G_out, double* dGdgamma, int on_device);
+
+/* Static solids: a Brinkman coefficient kappa_s >= 0 per analysis node (host, nodes doubles,
+ * copied; NULL removes it) for solid walls at rest inside the fluid, such as the inner wall of
+ * the paper's 2D pump (Sec. 3.2) or the fixed outer cylinder of its rotating-cylinder check
+ * (appendix).  The Brinkman update becomes u = (u* + kappa u_S) / (1 + kappa + kappa_s) and the
+ * adjoint follows exactly.  The FP32 D3Q15 context then runs the plain kernels (the fused D2Q9
+ * kernels support it).  Invalidates any forward run; LKS_ERR_ARG on a negative or non-finite
+ * value. */
+lks_status lks_set_static(lks_ctx* ctx, const double* kappa_s);
+
+/* Warm starts for periodic flows (Secs. 3.2 and 3.3 reuse the terminal fields of the previous
+ * optimisation step).  lks_warm_start: the initial state becomes the final state of the last
+ * forward run (LKS_ERR_ORDER without one).  lks_set_adjoint_start(warm = 1): every later adjoint
+ * starts from lambda^0 of the previous adjoint run instead of zero, which makes it the exact
+ * adjoint of J + <lambda_prev, s^N>; warm = 0 (the default) returns to the exact adjoint of J.
+ * lks_get_adjoint_state: lambda^0 of the last adjoint run as (rho, ux, uy, uz) planes of nodes
+ * doubles (host); it is dJ/ds^0, the gradient with respect to the initial state. */
+lks_status lks_warm_start(lks_ctx* ctx);
+lks_status lks_set_adjoint_start(lks_ctx* ctx, int warm);
+lks_status lks_get_adjoint_state(const lks_ctx* ctx, double* lambda_out);
+
 /* Set the motion schedule; needs n_rows >= max_steps + 1.  The transfer footprint (every
  * analysis node within two cells of a moved design node) must stay inside the grid and off
  * boundary nodes for every step, else LKS_ERR_ARG.  Invalidates any forward run. */
@@ -142,7 +180,9 @@ lks_status lks_get_state(const lks_ctx* ctx, double* state_out);
  * u_S (3 planes) on the whole analysis grid, host memory. */
 lks_status lks_transfer(lks_ctx* ctx, int step, double* kappa_out, double* us_out);
 
-/* 1 if forward steps of this context run the fused FP32 D3Q15 kernel, else 0. */
+/* Which kernels run the steps of this context: 1 the fused FP32 D3Q15 step and adjoint, 2 the
+ * fused FP32 D2Q9 kernels (the instance-table kernels of the batches), 0 the plain per-node
+ * kernels. */
 int lks_uses_fused(const lks_ctx* ctx);
 
 /* Counters of the last forward+adjoint: [0] forward steps, [1] recomputed steps,
@@ -188,6 +228,53 @@ lks_status lks_step_noalloc(const lks_config* cfg, const void* state_in, void* s
 
 const char* lks_last_error(const lks_ctx* ctx);
 void lks_destroy(lks_ctx* ctx);
+
+/* ---- batches: many problems in lock step (designs, finite-difference perturbations, grids of
+ * different sizes).  The paper solves one problem at a time; a batch runs the same Algorithm 1
+ * and adjoint sweep for every member context, with each phase of a step one persistent kernel
+ * launch over all members, runs of steps captured into CUDA graphs and replayed, and the tile
+ * shape of the fused step and adjoint kernels chosen by timing every candidate on the batch.
+ * Each member keeps its own design, motion, objective, state and gradient: results are bitwise
+ * those of the member run alone with lks_forward / lks_adjoint. */
+typedef struct lks_batch lks_batch;
+
+/* Group n contexts (not copied; they must outlive the batch).  Every member must be a D2Q9
+ * FP32 context without LKS_FLAG_PLAIN_KERNELS / LKS_FLAG_PAPER_ALKS, with equal max_steps,
+ * equal snapshot slots (ckpt_bytes = slots x state bytes of the member) and the same stream,
+ * each context at most once; else LKS_ERR_ARG (*out = NULL).  The batch allocates a small
+ * device table and its own CUDA stream, ordered after / before the members' stream by events
+ * at every call.  LKS_ERR_NOMEM if that fails. */
+lks_status lks_batch_create(lks_ctx* const* ctxs, int n, lks_batch** out);
+
+/* use_graphs: 1 (default) capture and replay runs of steps, 0 launch directly.  tile_fwd,
+ * tile_adj: index into lks_batch_tile_shapes for the fused step / adjoint kernel, or -1
+ * (default) to autotune at the next forward.  LKS_ERR_ARG on an index out of range. */
+lks_status lks_batch_set_options(lks_batch* b, int use_graphs, int tile_fwd, int tile_adj);
+
+/* lks_forward for every member: J_out (host, n doubles, may be NULL) receives each member's
+ * J.  Needs design and motion on every member (LKS_ERR_ORDER).  On an error the message of the
+ * first failing member is in lks_batch_last_error.  Synchronises. */
+lks_status lks_batch_forward(lks_batch* b, int n_steps, double* J_out);
+
+/* lks_adjoint for every member: dJdgamma[i] (n pointers; an entry may be NULL) receives member
+ * i's lx*ly doubles, host memory or device memory if on_device.  LKS_ERR_ORDER without a valid
+ * forward on every member. */
+lks_status lks_batch_adjoint(lks_batch* b, double* const* dJdgamma, int on_device);
+
+/* The candidate tile shapes as (tx, ty) pairs; returns their number (writes <= cap pairs) or
+ * -1 on bad arguments.  Host only. */
+int lks_batch_tile_shapes(int* txty, int cap);
+
+/* chosen2: tile shape indices in use for [step, adjoint] (-1 before the first forward);
+ * ms (may be NULL): 2 x shapes autotune timings in ms per launch, -1 where not timed. */
+lks_status lks_batch_tuning(const lks_batch* b, int* chosen2, float* ms);
+
+/* [0] kernels launched by the last forward or adjoint call (graph nodes included), [1] graphs
+ * held, [2] kernel nodes in them. */
+lks_status lks_batch_stats(const lks_batch* b, long long* stats3);
+
+const char* lks_batch_last_error(const lks_batch* b);
+void lks_batch_destroy(lks_batch* b);
 
 #ifdef __cplusplus
 }

@@ -7,11 +7,14 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "lks.h"
 #include "lks_internal.h"
+#include "lks_table.h"
 
 using namespace lks;
 
@@ -84,7 +87,8 @@ struct lks_ctx {
     bool own_ws = false;
     void* s[2];
     void* s0;
-    void* lam[2];
+    void* lam[2];       // the two adjoint buffers; lam[lam_par] holds lambda^n
+    int lam_par = 0;
     void* F;
     void* mu;
     void* phi;
@@ -119,6 +123,30 @@ struct lks_ctx {
     long long stats[5] = {0, 0, 0, 0, 0};
     const void* last = nullptr;  // buffer holding the newest forward level
     bool fused3d = false;        // FP32 3D non-periodic: one fused kernel per forward step
+    // instance table of this context (D2Q9 FP32: the table kernels of lks_fused2d.cu)
+    bool fused2d = false;
+    Motion* dmotion = nullptr;   // device motion rows
+    void** dbufs = nullptr;      // device buffer table (BUF_*)
+    std::vector<void*> hbufs;    // its host copy
+    Inst* dinst = nullptr;
+    int* dpre = nullptr;         // device prefix arrays, U_COUNT x 2
+    int* nbase = nullptr;        // device step base of this context's own runs
+    Plan plan;
+    int geo_gen = 0;             // bumped when the footprint box changes
+    int tile_fwd = 0, tile_adj = 0;   // tile shapes of the fused 2D kernels
+    // design chain: density filter radius (0 = off), projection steepness and threshold
+    double fR = 0.0, fbeta = 1.0, feta = 0.5;
+    double* gbar = nullptr;      // projected field the solver sees
+    double* hp = nullptr;        // H'(filtered gamma)
+    double* fws = nullptr;       // filter normaliser per design node
+    double* gout = nullptr;      // dJ/dgamma through the chain
+    double* gtmp = nullptr;      // design-grid scratch
+    double* scal = nullptr;      // device scalars
+    // static solids and warm starts
+    void* ks = nullptr;          // static Brinkman field storage (g.ks points here when set)
+    void* s_end = nullptr;       // final state of the last forward run
+    void* l_end = nullptr;       // lambda^0 of the last adjoint run
+    bool have_end = false, have_lend = false, adj_warm = false;
     // optional event timing of the stencil kernels, sampled every timing_stride steps
     int timing_stride = 0;
     std::vector<cudaEvent_t> tev[2];
@@ -255,7 +283,7 @@ double count_target(const lks_config* c) {
 }
 
 struct Layout {
-    size_t off[32];
+    size_t off[48];
     size_t total;
     int pool_slots;
     size_t snap;
@@ -264,8 +292,11 @@ struct Layout {
 enum {
     L_S0, L_S1, L_SINIT, L_L0, L_L1, L_F, L_MU, L_PHI, L_KUS, L_E, L_GAMMA, L_KREF, L_KPRIME,
     L_GACC, L_JSTEP, L_CBASE, L_CFRAC, L_ZTI, L_ZTW, L_TCNT, L_TIDX, L_TW, L_CM, L_DZB, L_DZF,
-    L_FLAGS, L_KREFT, L_K2, L_FACE, L_TGT, L_U3, L_POOL, L_COUNT
+    L_FLAGS, L_KREFT, L_K2, L_FACE, L_TGT, L_U3, L_MOTION, L_BUFS, L_INST, L_PRE, L_GBAR,
+    L_HP, L_FWS, L_GOUT, L_GTMP, L_SCAL, L_CSC, L_KS, L_SEND, L_LEND, L_POOL,
+    L_COUNT
 };
+static_assert(L_COUNT <= 48, "Layout::off holds 48 regions");
 
 Layout make_layout(const lks_config* cfg) {
     Layout L;
@@ -299,15 +330,6 @@ Layout make_layout(const lks_config* cfg) {
     sz[L_CM] = nd ? (size_t)cols * 3 * T : 0;
     sz[L_DZB] = (size_t)std::max(cfg->lz, 1) * 4;
     sz[L_DZF] = (size_t)std::max(cfg->lz, 1) * T;
-    sz[L_FLAGS] = 64;
-    sz[L_TGT] = (size_t)std::max(1.0, count_target(cfg)) * 4;
-    sz[L_U3] = (cfg->flags & LKS_FLAG_PAPER_ALKS) ? state : 0;
-    sz[L_KREFT] = (size_t)std::max(nd, 1LL) * T;
-    sz[L_K2] = nd ? (size_t)cols * std::max(cfg->lz, 1) * T : 0;
-    {
-        const long long n0 = cfg->nx, n1 = cfg->ny, n2 = dim == 3 ? cfg->nz : 1;
-        sz[L_FACE] = (size_t)6 * (n1 * n2 + n0 * n2 + n0 * n1) * 4;
-    }
     // snapshot pool
     const long long N = cfg->max_steps;
     long long P;
@@ -323,6 +345,24 @@ Layout make_layout(const lks_config* cfg) {
     } else {
         P = std::max(3LL, (long long)(cfg->ckpt_bytes / state));
         P = std::min(P, N + 1);
+    }
+    sz[L_FLAGS] = 64;
+    sz[L_MOTION] = (size_t)(cfg->max_steps + 1) * sizeof(Motion);
+    sz[L_BUFS] = (size_t)(BUF_POOL + P) * sizeof(void*);
+    sz[L_INST] = sizeof(Inst);
+    sz[L_PRE] = (size_t)U_COUNT * 2 * sizeof(int);
+    sz[L_GBAR] = sz[L_HP] = sz[L_FWS] = sz[L_GOUT] = sz[L_GTMP] = (size_t)std::max(nd, 1LL) * 8;
+    sz[L_SCAL] = 64;
+    sz[L_CSC] = (size_t)std::max(ncol, 1LL) * 16;
+    sz[L_KS] = (size_t)nodes * T;
+    sz[L_SEND] = sz[L_LEND] = state;
+    sz[L_TGT] = (size_t)std::max(1.0, count_target(cfg)) * 4;
+    sz[L_U3] = (cfg->flags & LKS_FLAG_PAPER_ALKS) ? state : 0;
+    sz[L_KREFT] = (size_t)std::max(nd, 1LL) * T;
+    sz[L_K2] = nd ? (size_t)cols * std::max(cfg->lz, 1) * T : 0;
+    {
+        const long long n0 = cfg->nx, n1 = cfg->ny, n2 = dim == 3 ? cfg->nz : 1;
+        sz[L_FACE] = (size_t)6 * (n1 * n2 + n0 * n2 + n0 * n1) * 4;
     }
     sz[L_POOL] = (size_t)P * state;
     size_t off = 0;
@@ -391,9 +431,18 @@ Motion motion_row(const lks_ctx* c, int n) {
     return m;
 }
 
+// ---------------------------------------------------------------- single-context steps
+
 template <class T>
 lks_status transfer_at(lks_ctx* c, int n) {
     if (c->d.nd == 0 || c->g.boxN == 0) return LKS_OK;
+    if (c->fused2d) {
+        CU(launch_set_int(c->nbase, n, c->st));
+        CU(launch_t_design_pos(c->plan, 0, c->st));
+        CU(launch_t_transfer2d(c->plan, 0, c->st));
+        c->stats[4] += 3;
+        return LKS_OK;
+    }
     const Motion m = motion_row(c, n);
     launch_design_pos<T>(c->d, c->g, m, c->ts, c->st);
     LAUNCHED();
@@ -403,13 +452,13 @@ lks_status transfer_at(lks_ctx* c, int n) {
     return LKS_OK;
 }
 
-// One forward step n: s[src] -> s[dst].
+// One forward step n: src -> dst (3D / FP64 / plain paths).
 template <class T>
 lks_status forward_step(lks_ctx* c, int n, const void* src, void* dst) {
     lks_status s = transfer_at<T>(c, n);
     if (s != LKS_OK) return s;
     const bool tm = timing_begin(c, n, 0);
-    if (sizeof(T) == 4 && c->fused3d) {
+    if (sizeof(T) == 4 && c->fused3d && !c->g.ks) {
         cudaError_t e = launch_fused_step3d(c->g, (const V4<float>*)src, (const V4<float>*)c->kus,
                                             (V4<float>*)dst, c->flags + 3, c->st);
         if (e != cudaSuccess) return fail(c, LKS_ERR_CUDA, "fused step: %s", cudaGetErrorString(e));
@@ -426,210 +475,449 @@ lks_status forward_step(lks_ctx* c, int n, const void* src, void* dst) {
 
 char* slot_ptr(lks_ctx* c, int slot) { return c->pool + (size_t)slot * c->snap_bytes; }
 
-// Tape slots are the first K+1 of the pool: slot t holds level seg*K + t.
-int tape_slot(const lks_ctx* c, int t) { return t; }
-
-lks_status copy_state(lks_ctx* c, void* dst, const void* src) {
-    CU(cudaMemcpyAsync(dst, src, (size_t)c->g.nodes * 4 * c->tsz, cudaMemcpyDeviceToDevice, c->st));
+lks_status copy_state(lks_ctx* c, void* dst, const void* src, cudaStream_t st) {
+    CU(cudaMemcpyAsync(dst, src, (size_t)c->g.nodes * 4 * c->tsz, cudaMemcpyDeviceToDevice, st));
     return LKS_OK;
 }
 
-template <class T>
-lks_status run_steps(lks_ctx* c, int from_level, int to_level, bool with_obj, int tape_seg) {
-    // Advance from from_level to to_level.  Without a tape the two working buffers alternate;
-    // with a tape (segment tape_seg, whose start level sits in tape slot 0) every level is
-    // written straight into its own tape slot and the working buffer keeps from_level.
-    for (int n = from_level + 1; n <= to_level; ++n) {
-        const void* src;
-        void* dst;
-        if (tape_seg >= 0) {
-            src = slot_ptr(c, tape_slot(c, n - 1 - tape_seg * c->K));
-            dst = slot_ptr(c, tape_slot(c, n - tape_seg * c->K));
-        } else {
-            src = c->s[c->work];
-            dst = c->s[1 - c->work];
-        }
-        lks_status s = forward_step<T>(c, n, src, dst);
-        if (s != LKS_OK) return s;
-        if (tape_seg < 0) c->work = 1 - c->work;
-        c->last = dst;
-        if (with_obj && n >= c->cfg.win_begin && n <= c->cfg.win_end) {
-            launch_objective<T>(c->g, (const V4<T>*)dst, c->jstep + n, c->st);
-            LAUNCHED();
-        }
-        if (with_obj) ++c->stats[0];
-        else ++c->stats[1];
-    }
-    c->work_level = (tape_seg >= 0) ? from_level : to_level;
-    return LKS_OK;
-}
-
-int seg_start(const lks_ctx* c, int a) { return a * c->K; }
-int seg_end(const lks_ctx* c, int a) { return std::min((a + 1) * c->K, c->n_fwd); }
-
-template <class T>
-lks_status restore_level(lks_ctx* c, int seg) {
-    const int lev = seg_start(c, seg);
-    if (c->work_level == lev) return LKS_OK;
-    const void* src = (seg == 0) ? c->s0 : (const void*)slot_ptr(c, c->slot_of[seg]);
-    if (seg != 0 && c->slot_of[seg] < 0) return fail(c, LKS_ERR_ARG, "schedule: no snapshot");
-    lks_status s = copy_state(c, c->s[c->work], src);
-    c->work_level = lev;
-    return s;
-}
-
-template <class T>
-lks_status exec_forward_action(lks_ctx* c, const Act& a, bool with_obj) {
-    switch (a.kind) {
-        case A_RESTORE:
-            return restore_level<T>(c, a.a);
-        case A_ADVANCE:
-            return run_steps<T>(c, seg_start(c, a.a), seg_start(c, a.b), with_obj, -1);
-        case A_STORE: {
-            if (c->free_slots.empty()) return fail(c, LKS_ERR_NOMEM, "schedule: out of slots");
-            int sl = c->free_slots.back();
-            c->free_slots.pop_back();
-            c->slot_of[a.a] = sl;
-            return copy_state(c, slot_ptr(c, sl), c->s[c->work]);
-        }
-        case A_FREE:
-            c->free_slots.push_back(c->slot_of[a.a]);
-            c->slot_of[a.a] = -1;
-            return LKS_OK;
-        case A_TAPE: {
-            lks_status s = copy_state(c, slot_ptr(c, tape_slot(c, 0)), c->s[c->work]);
-            if (s != LKS_OK) return s;
-            return run_steps<T>(c, seg_start(c, a.a), seg_end(c, a.a), with_obj, a.a);
-        }
-        default:
-            return fail(c, LKS_ERR_ARG, "schedule: unexpected action");
-    }
-}
-
+// One adjoint step n on the per-context kernels: lambda^n (lam[lam_par]) -> lambda^{n-1}.
 template <class T>
 lks_status adjoint_step(lks_ctx* c, int n, const void* sn, const void* sp) {
     const double h = 1.0 / (double)(c->cfg.win_end - c->cfg.win_begin + 1);
     const double hn = (n >= c->cfg.win_begin && n <= c->cfg.win_end) ? h : 0.0;
     lks_status s = transfer_at<T>(c, n);
     if (s != LKS_OK) return s;
-    V4<T>* lc = st4<T>(c->lam[0]);
-    V4<T>* ln = st4<T>(c->lam[1]);
+    V4<T>* lc = st4<T>(c->lam[c->lam_par]);
+    V4<T>* ln = st4<T>(c->lam[1 - c->lam_par]);
     const bool tm = timing_begin(c, n, 1);
     launch_adj_bcT<T>(c->g, lc, hn, c->st);
     LAUNCHED();
-    if (sizeof(T) == 4 && c->fused3d) {
+    if (sizeof(T) == 4 && c->fused3d && !c->g.ks) {
         cudaError_t e = launch_fused_adj3d(c->g, (const V4<float>*)lc, (V4<float>*)ln,
                                            (const V4<float>*)c->kus, (const V4<float>*)sn,
                                            (const V4<float>*)sp, (float*)c->e, c->face, hn,
                                            c->flags + 3, c->st);
         if (e != cudaSuccess) return fail(c, LKS_ERR_CUDA, "fused adjoint: %s", cudaGetErrorString(e));
         c->stats[4] += 2;
-        if (tm) timing_end(c, 1);
-        if (c->d.nd > 0 && c->g.boxN > 0) {
-            launch_sens<T>(c->d, c->g, c->ts, (const T*)c->e, (const T*)c->kprime, c->gacc, c->st);
-            LAUNCHED();
-        }
-        std::swap(c->lam[0], c->lam[1]);
-        return LKS_OK;
+    } else {
+        launch_adj_mu<T>(c->g, lc, (const V4<T>*)c->kus, (const V4<T>*)sn, st4<T>(c->mu),
+                         (T*)c->e, hn, c->st, (const V4<T>*)c->u3);
+        LAUNCHED();
+        launch_adj_moments<T>(c->g, st4<T>(c->mu), (const V4<T>*)sp, ln, (T*)c->phi, c->st,
+                              (V4<T>*)c->u3);
+        LAUNCHED();
+        launch_adj_divT<T>(c->g, (const T*)c->phi, ln, c->st);
+        LAUNCHED();
     }
-    launch_adj_mu<T>(c->g, lc, (const V4<T>*)c->kus, (const V4<T>*)sn, st4<T>(c->mu),
-                     (T*)c->e, hn, c->st, (const V4<T>*)c->u3);
-    LAUNCHED();
-    launch_adj_moments<T>(c->g, st4<T>(c->mu), (const V4<T>*)sp, ln, (T*)c->phi, c->st,
-                          (V4<T>*)c->u3);
-    LAUNCHED();
-    launch_adj_divT<T>(c->g, (const T*)c->phi, ln, c->st);
-    LAUNCHED();
     if (tm) timing_end(c, 1);
     if (c->d.nd > 0 && c->g.boxN > 0) {
         launch_sens<T>(c->d, c->g, c->ts, (const T*)c->e, (const T*)c->kprime, c->gacc, c->st);
         LAUNCHED();
     }
-    std::swap(c->lam[0], c->lam[1]);
+    c->lam_par ^= 1;
     return LKS_OK;
 }
 
+int seg_start(const lks_ctx* c, int a) { return a * c->K; }
+int seg_end(const lks_ctx* c, int a) { return std::min((a + 1) * c->K, c->n_fwd); }
+// ---------------------------------------------------------------- groups of contexts
+// A group runs one checkpoint schedule for contexts of identical step count and snapshot pool:
+// the single-context calls use a group of one, lks_batch_* a group over all its contexts.  On
+// the instance-table path (D2Q9 FP32) every phase of a step is one launch over the whole group,
+// and a run of steps can be captured once into a CUDA graph and replayed.
+
+struct GraphCache {
+    std::map<std::tuple<int, int, int, int, int, int>, cudaGraphExec_t> execs;
+    std::map<std::tuple<int, int, int, int, int, int>, int> nodes;
+    ~GraphCache() {
+        for (auto& kv : execs) cudaGraphExecDestroy(kv.second);
+    }
+    void clear() {
+        for (auto& kv : execs) cudaGraphExecDestroy(kv.second);
+        execs.clear();
+        nodes.clear();
+    }
+};
+
+struct Group {
+    lks_ctx* const* cs = nullptr;
+    int count = 0;
+    bool table = false;          // instance-table kernels
+    const Plan* plan = nullptr;
+    int* nbase = nullptr;
+    int tile_fwd = 0, tile_adj = 0;
+    GraphCache* graphs = nullptr;   // null: launch directly
+    cudaStream_t st = nullptr;
+    long long launches = 0;      // kernels launched (graph nodes included)
+};
+
+lks_status gfail(Group& G, lks_status s, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    for (int i = 0; i < G.count; ++i) G.cs[i]->err = buf;
+    return s;
+}
+
+#define GCU(call)                                                                         \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return gfail(G, LKS_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_));       \
+    } while (0)
+
+Group self_group(lks_ctx*& c) {
+    Group G;
+    G.cs = &c;
+    G.count = 1;
+    G.table = c->fused2d;
+    G.plan = &c->plan;
+    G.nbase = c->nbase;
+    G.tile_fwd = c->tile_fwd;
+    G.tile_adj = c->tile_adj;
+    G.st = c->st;
+    return G;
+}
+
+// Table-path launch sequences of one forward / adjoint step at offset k from *nbase.
+cudaError_t table_fwd_launches(const Group& G, int k, int src, int dst, bool with_obj,
+                               lks_ctx* timed, int n, int& nl) {
+    cudaError_t e;
+    if ((e = launch_t_design_pos(*G.plan, k, G.st)) != cudaSuccess) return e;
+    if ((e = launch_t_transfer2d(*G.plan, k, G.st)) != cudaSuccess) return e;
+    const bool tm = timed && timing_begin(timed, n, 0);
+    if ((e = launch_t_step2d(*G.plan, G.tile_fwd, src, dst, G.st)) != cudaSuccess) return e;
+    if (tm) timing_end(timed, 0);
+    nl += 3;
+    if (with_obj) {
+        if ((e = launch_t_objective(*G.plan, k, dst, G.st)) != cudaSuccess) return e;
+        ++nl;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t table_adj_launches(const Group& G, int k, int lam_in, int lam_out, int sn, int sp,
+                               lks_ctx* timed, int n, int& nl) {
+    cudaError_t e;
+    if ((e = launch_t_design_pos(*G.plan, k, G.st)) != cudaSuccess) return e;
+    if ((e = launch_t_transfer2d(*G.plan, k, G.st)) != cudaSuccess) return e;
+    const bool tm = timed && timing_begin(timed, n, 1);
+    if ((e = launch_t_bcT2d(*G.plan, k, lam_in, G.st)) != cudaSuccess) return e;
+    if ((e = launch_t_adj2d(*G.plan, G.tile_adj, k, lam_in, lam_out, sn, sp, G.st)) !=
+        cudaSuccess)
+        return e;
+    if (tm) timing_end(timed, 1);
+    if ((e = launch_t_sens(*G.plan, G.st)) != cudaSuccess) return e;
+    nl += 5;
+    return cudaSuccess;
+}
+
+// Run `len` table-path steps from base: fn(k, nl) issues step k (1..len) and counts launches.
+// With a graph cache the sequence is captured once per key and replayed.
+template <class Fn>
+lks_status table_run(Group& G, std::tuple<int, int, int, int, int, int> key, int base, int len,
+                     Fn fn) {
+    GCU(launch_set_int(G.nbase, base, G.st));
+    ++G.launches;
+    if (!G.graphs) {
+        int nl = 0;
+        for (int k = 1; k <= len; ++k) {
+            cudaError_t e = fn(k, nl, true);
+            if (e != cudaSuccess)
+                return gfail(G, LKS_ERR_CUDA, "table kernel launch: %s", cudaGetErrorString(e));
+        }
+        G.launches += nl;
+        return LKS_OK;
+    }
+    auto it = G.graphs->execs.find(key);
+    if (it == G.graphs->execs.end()) {
+        GCU(cudaStreamBeginCapture(G.st, cudaStreamCaptureModeThreadLocal));
+        int nl = 0;
+        cudaError_t e = cudaSuccess;
+        for (int k = 1; k <= len && e == cudaSuccess; ++k) e = fn(k, nl, false);
+        cudaGraph_t graph = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(G.st, &graph);
+        if (e != cudaSuccess || e2 != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return gfail(G, LKS_ERR_CUDA, "graph capture: %s",
+                         cudaGetErrorString(e != cudaSuccess ? e : e2));
+        }
+        cudaGraphExec_t exec = nullptr;
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return gfail(G, LKS_ERR_CUDA, "graph instantiate: %s",
+                                           cudaGetErrorString(e));
+        it = G.graphs->execs.emplace(key, exec).first;
+        G.graphs->nodes[key] = nl;
+    }
+    GCU(cudaGraphLaunch(it->second, G.st));
+    G.launches += G.graphs->nodes[key];
+    return LKS_OK;
+}
+
+// ---------------------------------------------------------------- schedule over a group
+
+// Advance every context of the group from from_level to to_level.  Without a tape the two
+// working buffers alternate; with a tape (segment tape_seg, whose start level sits in tape slot
+// 0) every level is written straight into its own tape slot and the working buffer keeps
+// from_level.
 template <class T>
-lks_status exec_adj(lks_ctx* c, int seg) {
-    const int a = seg_start(c, seg), b = seg_end(c, seg);
-    for (int n = b; n > a; --n) {
-        const void* sn = slot_ptr(c, tape_slot(c, n - a));
-        const void* sp = slot_ptr(c, tape_slot(c, n - 1 - a));
-        lks_status s = adjoint_step<T>(c, n, sn, sp);
+lks_status run_steps(Group& G, int from_level, int to_level, bool with_obj, int tape_seg) {
+    lks_ctx* c0 = G.cs[0];
+    const int len = to_level - from_level;
+    if (len > 0 && G.table) {
+        const int w0 = c0->work;
+        const int toff = tape_seg >= 0 ? from_level - tape_seg * c0->K : 0;
+        // the objective kernel only where some instance's window meets these steps
+        bool obj = false;
+        for (int i = 0; i < G.count && with_obj; ++i)
+            obj = obj || (G.cs[i]->cfg.win_begin <= to_level &&
+                          G.cs[i]->cfg.win_end > from_level);
+        auto fn = [&](int k, int& nl, bool direct) -> cudaError_t {
+            int src, dst;
+            if (tape_seg >= 0) {
+                src = BUF_POOL + toff + k - 1;
+                dst = BUF_POOL + toff + k;
+            } else {
+                const int w = (w0 + k - 1) & 1;
+                src = BUF_S0 + w;
+                dst = BUF_S0 + 1 - w;
+            }
+            return table_fwd_launches(G, k, src, dst, obj,
+                                      (direct && G.count == 1) ? c0 : nullptr, from_level + k, nl);
+        };
+        const auto key = std::make_tuple(tape_seg >= 0 ? 1 : 0, obj ? 1 : 0, len,
+                                         tape_seg >= 0 ? toff : w0, G.tile_fwd, 0);
+        lks_status s = table_run(G, key, from_level, len, fn);
         if (s != LKS_OK) return s;
+        for (int i = 0; i < G.count; ++i) {
+            lks_ctx* c = G.cs[i];
+            if (tape_seg >= 0) {
+                c->last = slot_ptr(c, toff + len);
+            } else {
+                c->work = (w0 + len) & 1;
+                c->last = c->s[c->work];
+            }
+            c->stats[with_obj ? 0 : 1] += len;
+        }
+    } else if (len > 0) {
+        lks_ctx* c = c0;
+        for (int n = from_level + 1; n <= to_level; ++n) {
+            const void* src;
+            void* dst;
+            if (tape_seg >= 0) {
+                src = slot_ptr(c, n - 1 - tape_seg * c->K);
+                dst = slot_ptr(c, n - tape_seg * c->K);
+            } else {
+                src = c->s[c->work];
+                dst = c->s[1 - c->work];
+            }
+            lks_status s = forward_step<T>(c, n, src, dst);
+            if (s != LKS_OK) return s;
+            if (tape_seg < 0) c->work = 1 - c->work;
+            c->last = dst;
+            if (with_obj && n >= c->cfg.win_begin && n <= c->cfg.win_end) {
+                launch_objective<T>(c->g, (const V4<T>*)dst, c->jstep + n, c->st);
+                LAUNCHED();
+            }
+            if (with_obj) ++c->stats[0];
+            else ++c->stats[1];
+        }
+    }
+    for (int i = 0; i < G.count; ++i)
+        G.cs[i]->work_level = (tape_seg >= 0) ? from_level : to_level;
+    return LKS_OK;
+}
+
+lks_status restore_level(Group& G, int seg) {
+    for (int i = 0; i < G.count; ++i) {
+        lks_ctx* c = G.cs[i];
+        const int lev = seg_start(c, seg);
+        if (c->work_level == lev) continue;
+        if (seg != 0 && c->slot_of[seg] < 0) return fail(c, LKS_ERR_ARG, "schedule: no snapshot");
+        const void* src = (seg == 0) ? c->s0 : (const void*)slot_ptr(c, c->slot_of[seg]);
+        lks_status s = copy_state(c, c->s[c->work], src, G.st);
+        if (s != LKS_OK) return s;
+        c->work_level = lev;
     }
     return LKS_OK;
 }
 
 template <class T>
-lks_status do_forward(lks_ctx* c, int N) {
-    c->n_fwd = N;
-    plan_tape(N, c->pool_slots, c->K, c->M, c->S);
-    c->acts.clear();
-    gen_schedule(0, c->M, c->S, c->acts);
-    c->slot_of.assign(c->M + 1, -1);
-    c->free_slots.clear();
-    for (int i = c->pool_slots - 1; i >= c->K + 1; --i) c->free_slots.push_back(i);
-    c->stats[0] = c->stats[1] = 0;
-    c->stats[2] = c->S;
-    c->stats[3] = c->K;
-    c->stats[4] = 0;
-    c->work = 0;
-    c->work_level = -1;
-    c->last = nullptr;
-    CU(cudaMemsetAsync(c->jstep, 0, (size_t)(c->cfg.max_steps + 2) * 8, c->st));
-    CU(cudaMemsetAsync(c->flags, 0, 64, c->st));
+lks_status exec_forward_action(Group& G, const Act& a, bool with_obj) {
+    lks_ctx* c0 = G.cs[0];
+    switch (a.kind) {
+        case A_RESTORE:
+            return restore_level(G, a.a);
+        case A_ADVANCE:
+            return run_steps<T>(G, seg_start(c0, a.a), seg_start(c0, a.b), with_obj, -1);
+        case A_STORE:
+            for (int i = 0; i < G.count; ++i) {
+                lks_ctx* c = G.cs[i];
+                if (c->free_slots.empty()) return fail(c, LKS_ERR_NOMEM, "schedule: out of slots");
+                const int sl = c->free_slots.back();
+                c->free_slots.pop_back();
+                c->slot_of[a.a] = sl;
+                lks_status s = copy_state(c, slot_ptr(c, sl), c->s[c->work], G.st);
+                if (s != LKS_OK) return s;
+            }
+            return LKS_OK;
+        case A_FREE:
+            for (int i = 0; i < G.count; ++i) {
+                lks_ctx* c = G.cs[i];
+                c->free_slots.push_back(c->slot_of[a.a]);
+                c->slot_of[a.a] = -1;
+            }
+            return LKS_OK;
+        case A_TAPE:
+            for (int i = 0; i < G.count; ++i) {
+                lks_ctx* c = G.cs[i];
+                lks_status s = copy_state(c, slot_ptr(c, 0), c->s[c->work], G.st);
+                if (s != LKS_OK) return s;
+            }
+            return run_steps<T>(G, seg_start(c0, a.a), seg_end(c0, a.a), with_obj, a.a);
+        default:
+            return gfail(G, LKS_ERR_ARG, "schedule: unexpected action");
+    }
+}
+
+template <class T>
+lks_status exec_adj(Group& G, int seg) {
+    lks_ctx* c0 = G.cs[0];
+    const int a = seg_start(c0, seg), b = seg_end(c0, seg), len = b - a;
+    if (len <= 0) return LKS_OK;
+    if (!G.table) {
+        for (int n = b; n > a; --n) {
+            lks_status s = adjoint_step<T>(c0, n, slot_ptr(c0, n - a), slot_ptr(c0, n - 1 - a));
+            if (s != LKS_OK) return s;
+        }
+        return LKS_OK;
+    }
+    const int par0 = c0->lam_par;
+    auto fn = [&](int k, int& nl, bool direct) -> cudaError_t {
+        const int kk = len - k + 1;                 // step n = a + kk, from b down to a + 1
+        const int par = par0 ^ ((k - 1) & 1);
+        return table_adj_launches(G, kk, BUF_LAM0 + par, BUF_LAM0 + 1 - par, BUF_POOL + kk,
+                                  BUF_POOL + kk - 1, (direct && G.count == 1) ? c0 : nullptr,
+                                  a + kk, nl);
+    };
+    const auto key = std::make_tuple(2, 0, len, par0, 0, G.tile_adj);
+    lks_status s = table_run(G, key, a, len, fn);
+    if (s != LKS_OK) return s;
+    for (int i = 0; i < G.count; ++i) G.cs[i]->lam_par = par0 ^ (len & 1);
+    return LKS_OK;
+}
+
+template <class T>
+lks_status do_forward(Group& G, int N) {
+    for (int i = 0; i < G.count; ++i) {
+        lks_ctx* c = G.cs[i];
+        c->n_fwd = N;
+        plan_tape(N, c->pool_slots, c->K, c->M, c->S);
+        c->acts.clear();
+        gen_schedule(0, c->M, c->S, c->acts);
+        c->slot_of.assign(c->M + 1, -1);
+        c->free_slots.clear();
+        for (int k = c->pool_slots - 1; k >= c->K + 1; --k) c->free_slots.push_back(k);
+        c->stats[0] = c->stats[1] = 0;
+        c->stats[2] = c->S;
+        c->stats[3] = c->K;
+        c->stats[4] = 0;
+        c->work = 0;
+        c->work_level = -1;
+        c->last = nullptr;
+        c->fwd_valid = false;
+        CU(cudaMemsetAsync(c->jstep, 0, (size_t)(c->cfg.max_steps + 2) * 8, G.st));
+        CU(cudaMemsetAsync(c->flags, 0, 64, G.st));
+    }
+    const std::vector<Act>& acts = G.cs[0]->acts;
     size_t i = 0;
-    for (; i < c->acts.size(); ++i) {
-        const Act& a = c->acts[i];
-        lks_status s = exec_forward_action<T>(c, a, true);
+    for (; i < acts.size(); ++i) {
+        lks_status s = exec_forward_action<T>(G, acts[i], true);
         if (s != LKS_OK) return s;
-        if (a.kind == A_TAPE) break;
+        if (acts[i].kind == A_TAPE) break;
     }
-    c->adj_begin = i + 1;
-    // J = h sum_n j_n in step order
-    const int w0 = c->cfg.win_begin, w1 = std::min(c->cfg.win_end, N);
-    std::vector<double> js(c->cfg.max_steps + 2, 0.0);
-    CU(cudaMemcpyAsync(js.data(), c->jstep, js.size() * 8, cudaMemcpyDeviceToHost, c->st));
-    launch_check_state<T>(c->g, (const V4<T>*)c->last, c->flags + 2, c->st);
-    LAUNCHED();
-    int fl[4];
-    CU(cudaMemcpyAsync(fl, c->flags, sizeof(fl), cudaMemcpyDeviceToHost, c->st));
-    CU(cudaStreamSynchronize(c->st));
-    if (fl[1]) return fail(c, LKS_ERR_ARG, "transfer tap list overflow");
-    if (fl[3] & 8) return fail(c, LKS_ERR_TIMEOUT, "a tensor-copy wait timed out in the fused step");
-    if (fl[3]) return fail(c, LKS_ERR_CUDA, "fused step reported error %d", fl[3]);
-    if (fl[2]) return fail(c, LKS_ERR_DIVERGED, "state diverged (non-finite or |u| >= 0.5)");
-    const double h = 1.0 / (double)(c->cfg.win_end - c->cfg.win_begin + 1);
-    double J = 0.0;
-    for (int n = w0; n <= w1; ++n) J += h * js[n];
-    c->J = J;
-    c->fwd_valid = true;
-    return LKS_OK;
+    std::vector<std::vector<double>> js(G.count);
+    std::vector<int> fl(4 * (size_t)G.count);
+    for (int k = 0; k < G.count; ++k) {
+        lks_ctx* c = G.cs[k];
+        c->adj_begin = i + 1;
+        js[k].assign(c->cfg.max_steps + 2, 0.0);
+        CU(cudaMemcpyAsync(js[k].data(), c->jstep, js[k].size() * 8, cudaMemcpyDeviceToHost, G.st));
+        launch_check_state<T>(c->g, (const V4<T>*)c->last, c->flags + 2, G.st);
+        LAUNCHED();
+        CU(cudaMemcpyAsync(c->s_end, c->last, c->snap_bytes, cudaMemcpyDeviceToDevice, G.st));
+        CU(cudaMemcpyAsync(fl.data() + 4 * k, c->flags, 16, cudaMemcpyDeviceToHost, G.st));
+    }
+    GCU(cudaStreamSynchronize(G.st));
+    lks_status worst = LKS_OK;
+    for (int k = 0; k < G.count; ++k) {
+        lks_ctx* c = G.cs[k];
+        const int* f = fl.data() + 4 * k;
+        lks_status s = LKS_OK;
+        if (f[1]) s = fail(c, LKS_ERR_ARG, "transfer tap list overflow");
+        else if (f[3] & 8) s = fail(c, LKS_ERR_TIMEOUT, "a tensor-copy wait timed out in the fused step");
+        else if (f[3]) s = fail(c, LKS_ERR_CUDA, "fused step reported error %d", f[3]);
+        else if (f[2]) s = fail(c, LKS_ERR_DIVERGED, "state diverged (non-finite or |u| >= 0.5)");
+        if (s != LKS_OK) {
+            if (worst == LKS_OK) worst = s;
+            continue;
+        }
+        const int w0 = c->cfg.win_begin, w1 = std::min(c->cfg.win_end, N);
+        const double h = 1.0 / (double)(c->cfg.win_end - c->cfg.win_begin + 1);
+        c->have_end = true;
+        double J = 0.0;
+        for (int n = w0; n <= w1; ++n) J += h * js[k][n];   // J = h sum_n j_n in step order
+        c->J = J;
+        c->fwd_valid = true;
+    }
+    return worst;
 }
 
 template <class T>
-lks_status do_adjoint(lks_ctx* c) {
-    CU(cudaMemsetAsync(c->flags, 0, 64, c->st));
-    CU(cudaMemsetAsync(c->lam[0], 0, c->snap_bytes, c->st));
-    if (c->u3) CU(cudaMemsetAsync(c->u3, 0, c->snap_bytes, c->st));
-    if (c->d.nd > 0) CU(cudaMemsetAsync(c->gacc, 0, (size_t)c->d.nd * 8, c->st));
-    for (size_t i = c->adj_begin - 1; i < c->acts.size(); ++i) {
-        const Act& a = c->acts[i];
-        if (a.kind == A_TAPE && i == c->adj_begin - 1) continue;  // recorded by the forward
-        lks_status s = (a.kind == A_ADJ) ? exec_adj<T>(c, a.a) : exec_forward_action<T>(c, a, false);
+lks_status do_adjoint(Group& G) {
+    for (int i = 0; i < G.count; ++i) {
+        lks_ctx* c = G.cs[i];
+        c->lam_par = 0;
+        CU(cudaMemsetAsync(c->flags, 0, 64, G.st));
+        if (c->adj_warm && c->have_lend)   // warm start: lambda^N from the last lambda^0
+            CU(cudaMemcpyAsync(c->lam[0], c->l_end, c->snap_bytes, cudaMemcpyDeviceToDevice, G.st));
+        else
+            CU(cudaMemsetAsync(c->lam[0], 0, c->snap_bytes, G.st));
+        if (c->u3) CU(cudaMemsetAsync(c->u3, 0, c->snap_bytes, G.st));
+        if (c->d.nd > 0) CU(cudaMemsetAsync(c->gacc, 0, (size_t)c->d.nd * 8, G.st));
+    }
+    lks_ctx* c0 = G.cs[0];
+    for (size_t i = c0->adj_begin - 1; i < c0->acts.size(); ++i) {
+        const Act& a = c0->acts[i];
+        if (a.kind == A_TAPE && i == c0->adj_begin - 1) continue;  // recorded by the forward
+        lks_status s = (a.kind == A_ADJ) ? exec_adj<T>(G, a.a) : exec_forward_action<T>(G, a, false);
         if (s != LKS_OK) return s;
     }
-    // the schedule may be replayed by another adjoint call of the same forward: the tape of
-    // the last segment has been overwritten, so a second adjoint needs a new forward
-    c->fwd_valid = false;
-    int fl[4];
-    CU(cudaMemcpyAsync(fl, c->flags, sizeof(fl), cudaMemcpyDeviceToHost, c->st));
-    CU(cudaStreamSynchronize(c->st));
-    if (fl[1]) return fail(c, LKS_ERR_ARG, "transfer tap list overflow");
-    if (fl[3] & 8) return fail(c, LKS_ERR_TIMEOUT, "a tensor-copy wait timed out in the fused step");
-    if (fl[3]) return fail(c, LKS_ERR_CUDA, "fused step reported error %d", fl[3]);
-    return LKS_OK;
+    // the tape of the last segment has been overwritten: a second adjoint needs a new forward
+    std::vector<int> fl(4 * (size_t)G.count);
+    for (int k = 0; k < G.count; ++k) {
+        lks_ctx* c = G.cs[k];
+        c->fwd_valid = false;
+        CU(cudaMemcpyAsync(c->l_end, c->lam[c->lam_par], c->snap_bytes, cudaMemcpyDeviceToDevice,
+                           G.st));
+        c->have_lend = true;
+        CU(cudaMemcpyAsync(fl.data() + 4 * k, c->flags, 16, cudaMemcpyDeviceToHost, G.st));
+    }
+    GCU(cudaStreamSynchronize(G.st));
+    lks_status worst = LKS_OK;
+    for (int k = 0; k < G.count; ++k) {
+        lks_ctx* c = G.cs[k];
+        const int* f = fl.data() + 4 * k;
+        lks_status s = LKS_OK;
+        if (f[1]) s = fail(c, LKS_ERR_ARG, "transfer tap list overflow");
+        else if (f[3] & 8) s = fail(c, LKS_ERR_TIMEOUT, "a tensor-copy wait timed out in the fused step");
+        else if (f[3]) s = fail(c, LKS_ERR_CUDA, "fused step reported error %d", f[3]);
+        if (s != LKS_OK && worst == LKS_OK) worst = s;
+    }
+    return worst;
 }
 
 template <class T>
@@ -638,6 +926,119 @@ lks_status reset_initial(lks_ctx* c) {
     LAUNCHED();
     launch_apply_bc<T>(c->g, st4<T>(c->s0), c->st);
     LAUNCHED();
+    return LKS_OK;
+}
+
+// Host record of a context's instance-table entry (valid once design and motion are set).
+Inst make_inst(const lks_ctx* c) {
+    Inst I;
+    std::memset(&I, 0, sizeof(I));
+    I.g = c->g;
+    I.d = c->d;
+    I.ts = c->ts;
+    I.motion = c->dmotion;
+    I.bufs = c->dbufs;
+    I.kref = (const float*)c->kref;
+    I.kprime = (const float*)c->kprime;
+    I.kus = (V4<float>*)c->kus;
+    I.e = (float*)c->e;
+    I.gacc = c->gacc;
+    I.jstep = c->jstep;
+    I.win_begin = c->cfg.win_begin;
+    I.win_end = c->cfg.win_end;
+    // the same FP64 expressions as the per-node source of the plain kernels, rounded once
+    const double h = 1.0 / (double)(c->cfg.win_end - c->cfg.win_begin + 1);
+    const Geom& g = c->g;
+    I.hwin = h;
+    I.src_r = g.okind == 0 ? (float)(-h / (3.0 * g.ocount)) : 0.f;
+    I.src_x = g.okind == 0 ? 0.f : (float)(-h * g.odir[0] / g.ocount);
+    I.src_y = g.okind == 0 ? 0.f : (float)(-h * g.odir[1] / g.ocount);
+    return I;
+}
+
+// Work units of one instance per unit kind (lks_table.h).
+void inst_units(const lks_ctx* c, int out[U_COUNT]) {
+    const Geom& g = c->g;
+    const bool body = c->d.nd > 0 && g.boxN > 0;
+    out[U_DCOL] = body ? (int)((c->d.ncol + kUnitThreads - 1) / kUnitThreads) : 0;
+    out[U_BOX] = body ? (int)((g.boxN + kUnitThreads - 1) / kUnitThreads) : 0;
+    out[U_SHELL] = (2 * (g.n[0] + g.n[1]) + kUnitThreads - 1) / kUnitThreads;
+    out[U_INST] = 1;
+    for (int k = 0; k < kTileCfgs; ++k)
+        out[U_TILE0 + k] = tile_count(g.n[0], tile_tx(k), g.periodic[0]) *
+                           tile_count(g.n[1], tile_ty(k), g.periodic[1]);
+}
+
+// Build a plan over contexts: the table and prefix arrays go to dinst / dpre (device, with
+// room for cs.size() entries), the host plan gets the totals and the persistent grids.
+cudaError_t build_plan(const std::vector<lks_ctx*>& cs, Inst* dinst, int* dpre, int* nbase,
+                       cudaStream_t st, Plan& p) {
+    const int B = (int)cs.size();
+    std::vector<Inst> tab(B);
+    std::vector<int> pre((size_t)U_COUNT * (B + 1), 0);
+    for (int i = 0; i < B; ++i) {
+        tab[i] = make_inst(cs[i]);
+        int u[U_COUNT];
+        inst_units(cs[i], u);
+        for (int k = 0; k < U_COUNT; ++k)
+            pre[(size_t)k * (B + 1) + i + 1] = pre[(size_t)k * (B + 1) + i] + u[k];
+    }
+    cudaError_t e = cudaMemcpyAsync(dinst, tab.data(), sizeof(Inst) * B, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(dpre, pre.data(), pre.size() * sizeof(int), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);   // host vectors go out of scope
+    if (e != cudaSuccess) return e;
+    std::memset(&p, 0, sizeof(p));
+    p.tab = dinst;
+    p.pre = dpre;
+    p.count = B;
+    p.nbase = nbase;
+    for (int k = 0; k < U_COUNT; ++k) p.total[k] = pre[(size_t)k * (B + 1) + B];
+    plan_grids(p);
+    return cudaGetLastError();
+}
+
+// kappa_ref and kappa' from the stored gamma, through the filter chain when it is on (the
+// [0,1] check of gamma sets flags[0]).
+lks_status design_prep(lks_ctx* c) {
+    const double* src = c->gamma;
+    if (c->fR > 0.0) {
+        launch_filter(c->d, c->fR, c->fbeta, c->feta, c->gamma, c->gbar, c->hp, c->fws, c->st);
+        LAUNCHED();
+        src = c->gbar;
+    }
+    if (c->prec == LKS_FP64)
+        launch_design_prep<double>(c->d, src, c->cfg.kappa_max, c->cfg.q, (double*)c->kref,
+                                   (double*)c->kref_t, (double*)c->kprime, c->flags, c->st);
+    else
+        launch_design_prep<float>(c->d, src, c->cfg.kappa_max, c->cfg.q, (float*)c->kref,
+                                  (float*)c->kref_t, (float*)c->kprime, c->flags, c->st);
+    LAUNCHED();
+    return LKS_OK;
+}
+
+// dJ/dgamma of the last adjoint: the accumulator, or its pull-back through the filter chain.
+const double* design_gradient(lks_ctx* c, cudaStream_t st) {
+    if (c->fR <= 0.0) return c->gacc;
+    launch_filter_T(c->d, c->fR, c->gacc, c->hp, c->fws, c->gout, st);
+    ++c->stats[4];
+    return c->gout;
+}
+
+// After a new motion table: rows with cos/sin evaluated on the host go to the device (the
+// instance-table kernels read them there), and a table context rebuilds its one-entry plan.
+lks_status finish_motion(lks_ctx* c) {
+    const int rows = c->cfg.max_steps + 1;
+    std::vector<Motion> mr(rows);
+    for (int n = 0; n < rows; ++n) mr[n] = motion_row(c, n);
+    CU(cudaMemcpyAsync(c->dmotion, mr.data(), sizeof(Motion) * rows, cudaMemcpyHostToDevice, c->st));
+    CU(cudaStreamSynchronize(c->st));
+    ++c->geo_gen;
+    if (c->fused2d) {
+        std::vector<lks_ctx*> one(1, c);
+        CU(build_plan(one, c->dinst, c->dpre, c->nbase, c->st, c->plan));
+    }
+    c->have_motion = true;
     return LKS_OK;
 }
 
@@ -743,6 +1144,7 @@ lks_status lks_create(const lks_config* cfg, void* workspace, size_t ws_bytes, l
     c->jstep = (double*)(w + L.off[L_JSTEP]);
     c->ts.col_base = (int*)(w + L.off[L_CBASE]);
     c->ts.col_frac = w + L.off[L_CFRAC];
+    c->ts.col_sc = (float4*)(w + L.off[L_CSC]);
     c->ts.zt_idx = (int*)(w + L.off[L_ZTI]);
     c->ts.zt_w = w + L.off[L_ZTW];
     c->ts.tap_cnt = (int*)(w + L.off[L_TCNT]);
@@ -771,8 +1173,34 @@ lks_status lks_create(const lks_config* cfg, void* workspace, size_t ws_bytes, l
     c->pool = w + L.off[L_POOL];
     c->pool_slots = L.pool_slots;
     c->snap_bytes = L.snap;
+    c->fused2d = (c->prec == LKS_FP32) && g.dim == 2 &&
+                 !(cfg->flags & (LKS_FLAG_PLAIN_KERNELS | LKS_FLAG_PAPER_ALKS));
+    c->dmotion = (Motion*)(w + L.off[L_MOTION]);
+    c->dbufs = (void**)(w + L.off[L_BUFS]);
+    c->dinst = (Inst*)(w + L.off[L_INST]);
+    c->dpre = (int*)(w + L.off[L_PRE]);
+    c->gbar = (double*)(w + L.off[L_GBAR]);
+    c->hp = (double*)(w + L.off[L_HP]);
+    c->fws = (double*)(w + L.off[L_FWS]);
+    c->gout = (double*)(w + L.off[L_GOUT]);
+    c->gtmp = (double*)(w + L.off[L_GTMP]);
+    c->scal = (double*)(w + L.off[L_SCAL]);
+    c->ks = w + L.off[L_KS];
+    c->s_end = w + L.off[L_SEND];
+    c->l_end = w + L.off[L_LEND];
+    c->nbase = c->flags + 8;
+    c->hbufs.assign(BUF_POOL + c->pool_slots, nullptr);
+    c->hbufs[BUF_S0] = c->s[0];
+    c->hbufs[BUF_S1] = c->s[1];
+    c->hbufs[BUF_INIT] = c->s0;
+    c->hbufs[BUF_LAM0] = c->lam[0];
+    c->hbufs[BUF_LAM1] = c->lam[1];
+    for (int k = 0; k < c->pool_slots; ++k) c->hbufs[BUF_POOL + k] = slot_ptr(c, k);
     lks_status s = LKS_OK;
-    if (cudaMemsetAsync(c->flags, 0, 64, c->st) != cudaSuccess) s = LKS_ERR_CUDA;
+    if (cudaMemcpy(c->dbufs, c->hbufs.data(), c->hbufs.size() * sizeof(void*),
+                   cudaMemcpyHostToDevice) != cudaSuccess)
+        s = LKS_ERR_CUDA;
+    if (s == LKS_OK && cudaMemsetAsync(c->flags, 0, 64, c->st) != cudaSuccess) s = LKS_ERR_CUDA;
     if (s == LKS_OK) s = c->prec == LKS_FP64 ? reset_initial<double>(c) : reset_initial<float>(c);
     if (s != LKS_OK) {
         lks_destroy(c);
@@ -798,13 +1226,8 @@ lks_status lks_set_design(lks_ctx* c, const double* gamma, int on_device) {
     CU(cudaMemcpyAsync(c->gamma, gamma, (size_t)c->d.nd * 8,
                        on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->st));
     CU(cudaMemsetAsync(c->flags, 0, 4, c->st));
-    if (c->prec == LKS_FP64)
-        launch_design_prep<double>(c->d, c->gamma, c->cfg.kappa_max, c->cfg.q, (double*)c->kref,
-                                   (double*)c->kref_t, (double*)c->kprime, c->flags, c->st);
-    else
-        launch_design_prep<float>(c->d, c->gamma, c->cfg.kappa_max, c->cfg.q, (float*)c->kref,
-                                  (float*)c->kref_t, (float*)c->kprime, c->flags, c->st);
-    LAUNCHED();
+    lks_status s = design_prep(c);
+    if (s != LKS_OK) return s;
     if (on_device) {
         int bad = 0;
         CU(cudaMemcpyAsync(&bad, c->flags, 4, cudaMemcpyDeviceToHost, c->st));
@@ -812,6 +1235,109 @@ lks_status lks_set_design(lks_ctx* c, const double* gamma, int on_device) {
         if (bad) return fail(c, LKS_ERR_ARG, "gamma outside [0,1]");
     }
     c->have_design = true;
+    return LKS_OK;
+}
+
+lks_status lks_set_filter(lks_ctx* c, double R, double beta, double eta) {
+    if (!c) return LKS_ERR_ARG;
+    if (!(R >= 0.0) || (R > 0.0 && (!(beta > 0.0) || !(eta > 0.0 && eta < 1.0))))
+        return fail(c, LKS_ERR_ARG, "filter needs R >= 0, and beta > 0, 0 < eta < 1 when R > 0");
+    c->fR = R;
+    c->fbeta = beta;
+    c->feta = eta;
+    c->fwd_valid = false;
+    if (c->have_design && c->d.nd > 0) {
+        lks_status s = design_prep(c);
+        if (s != LKS_OK) return s;
+    }
+    return LKS_OK;
+}
+
+lks_status lks_volume(lks_ctx* c, double vmax, double* G_out, double* dGdgamma, int on_device) {
+    if (!c || !G_out) return LKS_ERR_ARG;
+    if (!(vmax > 0.0)) return fail(c, LKS_ERR_ARG, "vmax must be positive");
+    if (!c->have_design || c->d.nd == 0) return fail(c, LKS_ERR_ORDER, "no design set");
+    const long long nd = c->d.nd;
+    launch_design_sum(nd, c->fR > 0.0 ? c->gbar : c->gamma, c->scal, c->st);
+    LAUNCHED();
+    double sum = 0.0;
+    CU(cudaMemcpyAsync(&sum, c->scal, 8, cudaMemcpyDeviceToHost, c->st));
+    const double dv = 1.0 / (vmax * (double)nd);
+    if (dGdgamma) {
+        launch_fill_f64(c->gtmp, nd, dv, c->st);
+        LAUNCHED();
+        const double* src = c->gtmp;
+        if (c->fR > 0.0) {
+            launch_filter_T(c->d, c->fR, c->gtmp, c->hp, c->fws, c->gout, c->st);
+            LAUNCHED();
+            src = c->gout;
+        }
+        CU(cudaMemcpyAsync(dGdgamma, src, (size_t)nd * 8,
+                           on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->st));
+    }
+    CU(cudaStreamSynchronize(c->st));
+    *G_out = sum * dv - 1.0;
+    return LKS_OK;
+}
+
+lks_status lks_set_static(lks_ctx* c, const double* kappa_s) {
+    if (!c) return LKS_ERR_ARG;
+    c->fwd_valid = false;
+    if (!kappa_s) {
+        c->g.ks = nullptr;
+    } else {
+        const size_t n = (size_t)c->g.nodes;
+        for (size_t m = 0; m < n; ++m)
+            if (!(kappa_s[m] >= 0.0) || !std::isfinite(kappa_s[m]))
+                return fail(c, LKS_ERR_ARG, "kappa_s[%zu] = %g is not a finite value >= 0", m,
+                            kappa_s[m]);
+        if (c->prec == LKS_FP64) {
+            CU(cudaMemcpy(c->ks, kappa_s, n * 8, cudaMemcpyHostToDevice));
+        } else {
+            std::vector<float> f(kappa_s, kappa_s + n);
+            CU(cudaMemcpy(c->ks, f.data(), n * 4, cudaMemcpyHostToDevice));
+        }
+        c->g.ks = c->ks;
+    }
+    if (c->fused2d && c->have_motion) {
+        std::vector<lks_ctx*> one(1, c);
+        CU(build_plan(one, c->dinst, c->dpre, c->nbase, c->st, c->plan));
+    }
+    ++c->geo_gen;
+    return LKS_OK;
+}
+
+lks_status lks_warm_start(lks_ctx* c) {
+    if (!c) return LKS_ERR_ARG;
+    if (!c->have_end) return fail(c, LKS_ERR_ORDER, "warm start needs a completed forward run");
+    CU(cudaMemcpyAsync(c->s0, c->s_end, c->snap_bytes, cudaMemcpyDeviceToDevice, c->st));
+    c->fwd_valid = false;
+    return LKS_OK;
+}
+
+lks_status lks_set_adjoint_start(lks_ctx* c, int warm) {
+    if (!c) return LKS_ERR_ARG;
+    c->adj_warm = warm != 0;
+    return LKS_OK;
+}
+
+lks_status lks_get_adjoint_state(const lks_ctx* cc, double* out) {
+    lks_ctx* c = const_cast<lks_ctx*>(cc);
+    if (!c || !out) return LKS_ERR_ARG;
+    if (!c->have_lend) return fail(c, LKS_ERR_ORDER, "no adjoint run yet");
+    double* tmp = nullptr;
+    const size_t bytes = (size_t)c->g.nodes * 4 * 8;
+    CU(cudaMalloc(&tmp, bytes));
+    if (c->prec == LKS_FP64)
+        launch_state_to_f64<double>(c->g, (const V4<double>*)c->l_end, tmp, c->st, false);
+    else
+        launch_state_to_f64<float>(c->g, (const V4<float>*)c->l_end, tmp, c->st, false);
+    cudaError_t e1 = cudaMemcpyAsync(out, tmp, bytes, cudaMemcpyDeviceToHost, c->st);
+    cudaError_t e2 = cudaStreamSynchronize(c->st);
+    cudaFree(tmp);
+    if (e1 != cudaSuccess || e2 != cudaSuccess)
+        return fail(c, LKS_ERR_CUDA, "get_adjoint_state: %s",
+                    cudaGetErrorString(e1 != cudaSuccess ? e1 : e2));
     return LKS_OK;
 }
 
@@ -825,8 +1351,7 @@ lks_status lks_set_motion(lks_ctx* c, const lks_motion* m) {
     Geom& g = c->g;
     if (c->d.nd == 0) {
         g.boxN = 0;
-        c->have_motion = true;
-        return LKS_OK;
+        return finish_motion(c);
     }
     // union over steps of the analysis nodes strictly within two cells of a moved design node
     double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
@@ -868,8 +1393,7 @@ lks_status lks_set_motion(lks_ctx* c, const lks_motion* m) {
         g.bn[a] = h - l + 1;
     }
     g.boxN = (long long)g.bn[0] * g.bn[1] * g.bn[2];
-    c->have_motion = true;
-    return LKS_OK;
+    return finish_motion(c);
 }
 
 lks_status lks_set_initial_state(lks_ctx* c, const double* state) {
@@ -897,7 +1421,9 @@ lks_status lks_forward(lks_ctx* c, int n_steps, double* J_out) {
     if (n_steps < 1 || n_steps > c->cfg.max_steps)
         return fail(c, LKS_ERR_ARG, "n_steps must be in [1, max_steps]");
     c->fwd_valid = false;
-    lks_status s = c->prec == LKS_FP64 ? do_forward<double>(c, n_steps) : do_forward<float>(c, n_steps);
+    Group G = self_group(c);
+    lks_status s = c->prec == LKS_FP64 ? do_forward<double>(G, n_steps) : do_forward<float>(G, n_steps);
+    c->stats[4] += G.launches;
     if (s != LKS_OK) return s;
     if (J_out) *J_out = c->J;
     return LKS_OK;
@@ -906,10 +1432,12 @@ lks_status lks_forward(lks_ctx* c, int n_steps, double* J_out) {
 lks_status lks_adjoint(lks_ctx* c, double* dJdgamma, int on_device) {
     if (!c) return LKS_ERR_ARG;
     if (!c->fwd_valid) return fail(c, LKS_ERR_ORDER, "adjoint needs a preceding forward run");
-    lks_status s = c->prec == LKS_FP64 ? do_adjoint<double>(c) : do_adjoint<float>(c);
+    Group G = self_group(c);
+    lks_status s = c->prec == LKS_FP64 ? do_adjoint<double>(G) : do_adjoint<float>(G);
+    c->stats[4] += G.launches;
     if (s != LKS_OK) return s;
     if (c->d.nd > 0 && dJdgamma) {
-        CU(cudaMemcpyAsync(dJdgamma, c->gacc, (size_t)c->d.nd * 8,
+        CU(cudaMemcpyAsync(dJdgamma, design_gradient(c, c->st), (size_t)c->d.nd * 8,
                            on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->st));
         CU(cudaStreamSynchronize(c->st));
     }
@@ -963,7 +1491,9 @@ lks_status lks_transfer(lks_ctx* c, int step, double* kappa_out, double* us_out)
     return LKS_OK;
 }
 
-int lks_uses_fused(const lks_ctx* c) { return c && c->fused3d ? 1 : 0; }
+int lks_uses_fused(const lks_ctx* c) {
+    return !c ? 0 : ((c->fused3d && !c->g.ks) ? 1 : (c->fused2d ? 2 : 0));
+}
 
 lks_status lks_get_stats(const lks_ctx* c, long long* st5) {
     if (!c || !st5) return LKS_ERR_ARG;
@@ -1016,6 +1546,302 @@ void lks_destroy(lks_ctx* c) {
         for (cudaEvent_t e : c->tev[w]) cudaEventDestroy(e);
     if (c->own_ws && c->ws) cudaFree(c->ws);
     delete c;
+}
+
+}  // extern "C"
+
+// ================================================================ batches of contexts
+// Many D2Q9 FP32 contexts (designs, finite-difference perturbations, grids of different sizes)
+// advanced in lock step: one checkpoint schedule, every phase of a step one persistent launch
+// over all instances, runs of steps captured into CUDA graphs on the batch's own stream, tile
+// shapes of the fused kernels picked by timing every candidate on the batch itself.
+
+struct lks_batch {
+    std::vector<lks_ctx*> cs;
+    cudaStream_t user_st = nullptr;   // the contexts' stream
+    cudaStream_t st = nullptr;        // own stream: graphs need a capturable stream
+    cudaEvent_t ev = nullptr;
+    char* dmem = nullptr;
+    Inst* dinst = nullptr;
+    int* dpre = nullptr;
+    int* nbase = nullptr;
+    Plan plan;
+    bool have_plan = false;
+    std::vector<int> gens;
+    GraphCache graphs;
+    bool use_graphs = true;
+    int tile_req[2] = {-1, -1};       // requested tile shapes, -1 = autotune
+    int tile[2] = {-1, -1};           // in use
+    float tune_ms[2][kTileCfgs];
+    long long launches = 0;
+    std::string err;
+};
+
+namespace {
+
+lks_status bfail(lks_batch* b, lks_status s, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    b->err = buf;
+    return s;
+}
+
+#define BCU(call)                                                                         \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return bfail(b, LKS_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_));       \
+    } while (0)
+
+// Copy the first failing context's message into the batch.
+lks_status bcollect(lks_batch* b, lks_status s) {
+    if (s == LKS_OK) return s;
+    for (size_t i = 0; i < b->cs.size(); ++i)
+        if (!b->cs[i]->err.empty()) {
+            b->err = "instance " + std::to_string(i) + ": " + b->cs[i]->err;
+            return s;
+        }
+    b->err = "batch run failed";
+    return s;
+}
+
+lks_status batch_prepare(lks_batch* b, int n_steps) {
+    for (size_t i = 0; i < b->cs.size(); ++i) {
+        lks_ctx* c = b->cs[i];
+        c->err.clear();
+        if (!c->have_design || !c->have_motion)
+            return bfail(b, LKS_ERR_ORDER, "instance %zu: set_design and set_motion must precede forward", i);
+        if (n_steps < 1 || n_steps > c->cfg.max_steps)
+            return bfail(b, LKS_ERR_ARG, "n_steps must be in [1, max_steps]");
+    }
+    bool stale = !b->have_plan;
+    for (size_t i = 0; i < b->cs.size(); ++i) stale = stale || b->gens[i] != b->cs[i]->geo_gen;
+    if (stale) {
+        b->graphs.clear();
+        BCU(build_plan(b->cs, b->dinst, b->dpre, b->nbase, b->st, b->plan));
+        for (size_t i = 0; i < b->cs.size(); ++i) b->gens[i] = b->cs[i]->geo_gen;
+        b->have_plan = true;
+        b->tile[0] = b->tile[1] = -1;
+    }
+    // autotune: time every tile shape of the fused step and adjoint kernels on this batch
+    if (b->tile[0] < 0 || b->tile[1] < 0) {
+        for (int w = 0; w < 2; ++w) {
+            if (b->tile_req[w] >= 0) {
+                b->tile[w] = b->tile_req[w];
+                continue;
+            }
+            BCU(launch_set_int(b->nbase, 0, b->st));
+            BCU(launch_t_design_pos(b->plan, 1, b->st));
+            BCU(launch_t_transfer2d(b->plan, 1, b->st));
+            for (lks_ctx* c : b->cs) {
+                BCU(cudaMemsetAsync(c->lam[0], 0, c->snap_bytes, b->st));
+                BCU(cudaMemsetAsync(c->lam[1], 0, c->snap_bytes, b->st));
+            }
+            cudaEvent_t e0, e1;
+            BCU(cudaEventCreate(&e0));
+            BCU(cudaEventCreate(&e1));
+            int best = 0;
+            for (int k = 0; k < kTileCfgs; ++k) {
+                auto run = [&]() -> cudaError_t {
+                    return w == 0 ? launch_t_step2d(b->plan, k, BUF_INIT, BUF_S1, b->st)
+                                  : launch_t_adj2d(b->plan, k, 1, BUF_LAM0, BUF_LAM1, BUF_INIT,
+                                                   BUF_INIT, b->st);
+                };
+                cudaError_t e = cudaSuccess;
+                for (int r = 0; r < 2 && e == cudaSuccess; ++r) e = run();
+                if (e == cudaSuccess) e = cudaEventRecord(e0, b->st);
+                for (int r = 0; r < 5 && e == cudaSuccess; ++r) e = run();
+                if (e == cudaSuccess) e = cudaEventRecord(e1, b->st);
+                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                float ms = 0.f;
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+                if (e != cudaSuccess) {
+                    cudaEventDestroy(e0);
+                    cudaEventDestroy(e1);
+                    return bfail(b, LKS_ERR_CUDA, "autotune: %s", cudaGetErrorString(e));
+                }
+                b->tune_ms[w][k] = ms / 5.f;
+                if (b->tune_ms[w][k] < b->tune_ms[w][best]) best = k;
+                b->launches += 7;
+            }
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            b->tile[w] = best;
+            b->launches += 3;
+        }
+        b->graphs.clear();
+    }
+    return LKS_OK;
+}
+
+Group batch_group(lks_batch* b) {
+    Group G;
+    G.cs = b->cs.data();
+    G.count = (int)b->cs.size();
+    G.table = true;
+    G.plan = &b->plan;
+    G.nbase = b->nbase;
+    G.tile_fwd = b->tile[0];
+    G.tile_adj = b->tile[1];
+    G.graphs = b->use_graphs ? &b->graphs : nullptr;
+    G.st = b->st;
+    return G;
+}
+
+}  // namespace
+
+extern "C" {
+
+lks_status lks_batch_create(lks_ctx* const* ctxs, int n, lks_batch** out) {
+    if (!out) return LKS_ERR_ARG;
+    *out = nullptr;
+    if (!ctxs || n < 1) return LKS_ERR_ARG;
+    for (int i = 0; i < n; ++i) {
+        lks_ctx* c = ctxs[i];
+        if (!c) return LKS_ERR_ARG;
+        if (!c->fused2d) {
+            fprintf(stderr, "lks_batch_create: instance %d is not a D2Q9 FP32 context on the "
+                            "fused kernels\n", i);
+            return LKS_ERR_ARG;
+        }
+        if (c->cfg.max_steps != ctxs[0]->cfg.max_steps || c->pool_slots != ctxs[0]->pool_slots ||
+            c->st != ctxs[0]->st) {
+            fprintf(stderr, "lks_batch_create: instances need equal max_steps, snapshot slots "
+                            "and stream (instance %d differs)\n", i);
+            return LKS_ERR_ARG;
+        }
+        for (int j = 0; j < i; ++j)
+            if (ctxs[j] == c) {
+                fprintf(stderr, "lks_batch_create: instance %d repeats instance %d\n", i, j);
+                return LKS_ERR_ARG;
+            }
+    }
+    lks_batch* b = new lks_batch();
+    b->cs.assign(ctxs, ctxs + n);
+    b->gens.assign(n, -1);
+    b->user_st = ctxs[0]->st;
+    const size_t inst_bytes = align256(sizeof(Inst) * n);
+    const size_t pre_bytes = align256(sizeof(int) * U_COUNT * (n + 1));
+    if (cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaMalloc((void**)&b->dmem, inst_bytes + pre_bytes + 256) != cudaSuccess) {
+        cudaGetLastError();
+        lks_batch_destroy(b);
+        return LKS_ERR_NOMEM;
+    }
+    b->dinst = (Inst*)b->dmem;
+    b->dpre = (int*)(b->dmem + inst_bytes);
+    b->nbase = (int*)(b->dmem + inst_bytes + pre_bytes);
+    *out = b;
+    return LKS_OK;
+}
+
+lks_status lks_batch_set_options(lks_batch* b, int use_graphs, int tile_fwd, int tile_adj) {
+    if (!b) return LKS_ERR_ARG;
+    if (tile_fwd < -1 || tile_fwd >= kTileCfgs || tile_adj < -1 || tile_adj >= kTileCfgs)
+        return bfail(b, LKS_ERR_ARG, "tile shape index out of range");
+    b->use_graphs = use_graphs != 0;
+    b->tile_req[0] = tile_fwd;
+    b->tile_req[1] = tile_adj;
+    b->tile[0] = b->tile[1] = -1;
+    b->graphs.clear();
+    return LKS_OK;
+}
+
+lks_status lks_batch_forward(lks_batch* b, int n_steps, double* J_out) {
+    if (!b) return LKS_ERR_ARG;
+    b->err.clear();
+    BCU(cudaEventRecord(b->ev, b->user_st));
+    BCU(cudaStreamWaitEvent(b->st, b->ev, 0));
+    b->launches = 0;
+    lks_status s = batch_prepare(b, n_steps);
+    if (s == LKS_OK) {
+        Group G = batch_group(b);
+        s = bcollect(b, do_forward<float>(G, n_steps));
+        b->launches += G.launches;
+        for (lks_ctx* c : b->cs) b->launches += c->stats[4];
+    }
+    BCU(cudaEventRecord(b->ev, b->st));
+    BCU(cudaStreamWaitEvent(b->user_st, b->ev, 0));
+    if (s != LKS_OK) return s;
+    if (J_out)
+        for (size_t i = 0; i < b->cs.size(); ++i) J_out[i] = b->cs[i]->J;
+    return LKS_OK;
+}
+
+lks_status lks_batch_adjoint(lks_batch* b, double* const* dJdgamma, int on_device) {
+    if (!b) return LKS_ERR_ARG;
+    b->err.clear();
+    for (size_t i = 0; i < b->cs.size(); ++i)
+        if (!b->cs[i]->fwd_valid)
+            return bfail(b, LKS_ERR_ORDER, "instance %zu: adjoint needs a preceding forward run", i);
+    BCU(cudaEventRecord(b->ev, b->user_st));
+    BCU(cudaStreamWaitEvent(b->st, b->ev, 0));
+    Group G = batch_group(b);
+    long long before = 0;
+    for (lks_ctx* c : b->cs) before += c->stats[4];
+    lks_status s = bcollect(b, do_adjoint<float>(G));
+    b->launches += G.launches;
+    for (lks_ctx* c : b->cs) b->launches += c->stats[4];
+    b->launches -= before;
+    if (s == LKS_OK && dJdgamma) {
+        for (size_t i = 0; i < b->cs.size(); ++i) {
+            lks_ctx* c = b->cs[i];
+            if (c->d.nd == 0 || !dJdgamma[i]) continue;
+            BCU(cudaMemcpyAsync(dJdgamma[i], design_gradient(c, b->st), (size_t)c->d.nd * 8,
+                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                b->st));
+        }
+        BCU(cudaStreamSynchronize(b->st));
+    }
+    BCU(cudaEventRecord(b->ev, b->st));
+    BCU(cudaStreamWaitEvent(b->user_st, b->ev, 0));
+    return s;
+}
+
+int lks_batch_tile_shapes(int* txty, int cap) {
+    if (cap < 0 || (!txty && cap > 0)) return -1;
+    for (int k = 0; k < kTileCfgs && k < cap; ++k) {
+        txty[2 * k] = tile_tx(k);
+        txty[2 * k + 1] = tile_ty(k);
+    }
+    return kTileCfgs;
+}
+
+lks_status lks_batch_tuning(const lks_batch* b, int* chosen2, float* ms) {
+    if (!b || !chosen2) return LKS_ERR_ARG;
+    chosen2[0] = b->tile[0];
+    chosen2[1] = b->tile[1];
+    if (ms)
+        for (int w = 0; w < 2; ++w)
+            for (int k = 0; k < kTileCfgs; ++k)
+                ms[w * kTileCfgs + k] = (b->tile_req[w] < 0 && b->tile[w] >= 0) ? b->tune_ms[w][k] : -1.f;
+    return LKS_OK;
+}
+
+lks_status lks_batch_stats(const lks_batch* b, long long* stats3) {
+    if (!b || !stats3) return LKS_ERR_ARG;
+    stats3[0] = b->launches;
+    stats3[1] = (long long)b->graphs.execs.size();
+    long long nodes = 0;
+    for (const auto& kv : b->graphs.nodes) nodes += kv.second;
+    stats3[2] = nodes;
+    return LKS_OK;
+}
+
+const char* lks_batch_last_error(const lks_batch* b) { return b ? b->err.c_str() : "null batch"; }
+
+void lks_batch_destroy(lks_batch* b) {
+    if (!b) return;
+    if (b->st) cudaStreamSynchronize(b->st);
+    b->graphs.clear();
+    if (b->dmem) cudaFree(b->dmem);
+    if (b->ev) cudaEventDestroy(b->ev);
+    if (b->st) cudaStreamDestroy(b->st);
+    delete b;
 }
 
 }  // extern "C"

@@ -1,0 +1,665 @@
+// D2Q9 FP32 kernels over instance tables (lks_table.h): every launch covers all instances of a
+// plan with a persistent grid that walks the concatenated work units.
+//
+//   k_t_design_pos  x_ref, y_ref of every design column (design_col_pos);
+//   k_t_transfer2d  kappa and u_S on every footprint-box node (transfer2d_node, Sec. 2.3);
+//   k_t_step2d      fused LKS step (Alg. 1; Sec. 2.2 f^eq with the viscosity term, Eqs. rho,
+//                   u, u_ex_2, bc_rho, bc_u) on TX x TY tiles: the state tile with a two-cell
+//                   halo goes to shared memory, f^eq of the tile and a one-cell rim is
+//                   evaluated once per node and direction, then gathered;
+//   k_t_objective   one block per instance inside the objective window (Sec. 2.5);
+//   k_t_bcT2d       transpose of the boundary copies (bcT_node);
+//   k_t_adj2d       fused exact adjoint step (structure of Alg. 2, Eqs. arho, au, as): lambda
+//                   to mu (Brinkman transpose and the kappa sensitivity density e), moments
+//                   of F~ on the tile and a one-cell rim, adjoint equilibrium and the full
+//                   transposed velocity gradient including the one-sided boundary rows;
+//   k_t_sens        dJ/dgamma gather per design column (sens_run, Sec. 2.4).
+#include <cuda_runtime.h>
+
+#include "lks_table.h"
+#include "lks_units.cuh"
+
+namespace lks {
+
+namespace {
+
+constexpr int NT = 256;
+
+// Instance of work unit u: the last i with pre[i] <= u (pre has count + 1 entries).
+__device__ __forceinline__ int find_inst(const int* __restrict__ pre, int count, int u) {
+    int lo = 0, hi = count - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(pre + mid) <= u) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ int wrap_any(int i, int n) {
+    i %= n;
+    return i < 0 ? i + n : i;
+}
+
+__device__ __forceinline__ int step_of(const Plan& p, int noff) { return __ldg(p.nbase) + noff; }
+
+// Stage instance i's record in shared memory when the block moves to it: kernels then read the
+// geometry from shared memory, which their global stores cannot alias, instead of reloading it
+// from global memory after every store.  Called by all threads; ends with a barrier when it
+// copies.
+__device__ __forceinline__ void stage_inst(const Plan& p, int i, int& cur, Inst& sI) {
+    if (i == cur) return;
+    __syncthreads();
+    const int* src = reinterpret_cast<const int*>(p.tab + i);
+    int* dst = reinterpret_cast<int*>(&sI);
+    for (int k = threadIdx.x; k < (int)(sizeof(Inst) / 4); k += blockDim.x) dst[k] = __ldg(src + k);
+    __syncthreads();
+    cur = i;
+}
+
+// ---------------------------------------------------------------- element-wise phases
+
+__global__ void __launch_bounds__(NT) k_t_design_pos(Plan p, int noff) {
+    const int* pre = p.pre + U_DCOL * (p.count + 1);
+    const int n = step_of(p, noff);
+    for (int u = blockIdx.x; u < p.total[U_DCOL]; u += gridDim.x) {
+        const int i = find_inst(pre, p.count, u);
+        const Inst& I = p.tab[i];
+        const long long k = (long long)(u - pre[i]) * kUnitThreads + threadIdx.x;
+        if (k < I.d.ncol) design_col_pos_sc(I.d, I.motion[n], I.ts, k);
+    }
+}
+
+__global__ void __launch_bounds__(NT) k_t_transfer2d(Plan p, int noff) {
+    const int* pre = p.pre + U_BOX * (p.count + 1);
+    const int n = step_of(p, noff);
+    for (int u = blockIdx.x; u < p.total[U_BOX]; u += gridDim.x) {
+        const int i = find_inst(pre, p.count, u);
+        const Inst& I = p.tab[i];
+        const long long bi = (long long)(u - pre[i]) * kUnitThreads + threadIdx.x;
+        if (bi < I.g.boxN) transfer2d_node(I.d, I.g, I.motion[n], I.ts, I.kref, I.kus, bi);
+    }
+}
+
+__global__ void __launch_bounds__(kObjThreads) k_t_objective(Plan p, int noff, int src) {
+    const int n = step_of(p, noff);
+    for (int i = blockIdx.x; i < p.count; i += gridDim.x) {
+        const Inst& I = p.tab[i];
+        if (n < I.win_begin || n > I.win_end) continue;   // uniform over the block
+        objective_block<float>(I.g, (const V4<float>*)I.bufs[src], I.jstep + n);
+    }
+}
+
+// Interior node next to the boundary for shell index t of a 2D grid: the layers x = 1,
+// x = n0-2, y = 1, y = n1-2 in that order, each node taken by the first layer holding it.
+__device__ __forceinline__ bool shell2d(const Geom& g, int t, int& x, int& y) {
+    const int n0 = g.n[0], n1 = g.n[1];
+    int layer;
+    if (t < n1) layer = 0;
+    else if (t < 2 * n1) { layer = 1; t -= n1; }
+    else if (t < 2 * n1 + n0) { layer = 2; t -= 2 * n1; }
+    else if (t < 2 * n1 + 2 * n0) { layer = 3; t -= 2 * n1 + n0; }
+    else return false;
+    const int a = layer / 2;
+    if (g.periodic[a]) return false;
+    if (a == 0) {
+        x = (layer & 1) ? n0 - 2 : 1;
+        y = t;
+    } else {
+        y = (layer & 1) ? n1 - 2 : 1;
+        x = t;
+        if (!g.periodic[0] && (x == 1 || x == n0 - 2)) return false;   // taken by an x layer
+    }
+    if (layer == 1 && x == 1) return false;   // n0 == 3: x = 1 is also the low layer
+    if (layer == 3 && y == 1) return false;
+    return !is_boundary(g, x, y, 0);
+}
+
+__global__ void __launch_bounds__(NT) k_t_bcT2d(Plan p, int noff, int lam) {
+    const int* pre = p.pre + U_SHELL * (p.count + 1);
+    const int n = step_of(p, noff);
+    for (int u = blockIdx.x; u < p.total[U_SHELL]; u += gridDim.x) {
+        const int i = find_inst(pre, p.count, u);
+        const Inst& I = p.tab[i];
+        const int t = (u - pre[i]) * kUnitThreads + threadIdx.x;
+        int x, y;
+        if (!shell2d(I.g, t, x, y)) continue;
+        const double h = (n >= I.win_begin && n <= I.win_end) ? I.hwin : 0.0;
+        bcT_node<float>(I.g, (V4<float>*)I.bufs[lam], h, x, y, 0);
+    }
+}
+
+__global__ void __launch_bounds__(NT) k_t_sens(Plan p) {
+    const int* pre = p.pre + U_DCOL * (p.count + 1);
+    for (int u = blockIdx.x; u < p.total[U_DCOL]; u += gridDim.x) {
+        const int i = find_inst(pre, p.count, u);
+        const Inst& I = p.tab[i];
+        const long long k = (long long)(u - pre[i]) * kUnitThreads + threadIdx.x;
+        if (k < I.d.ncol) sens2d_node(I.d, I.g, I.ts, I.e, I.kprime, I.gacc, k);
+    }
+}
+
+__global__ void k_set_int(int* dst, int v) { *dst = v; }
+
+// deriv_coef in single precision (same rows: central, periodic, one-sided on boundary nodes).
+__device__ __forceinline__ float deriv_coef_f(int i, int n, int periodic, int off) {
+    if (periodic || (i > 0 && i < n - 1)) return off == 1 ? 0.5f : (off == -1 ? -0.5f : 0.f);
+    if (i == 0) return off == 0 ? -1.5f : (off == 1 ? 2.f : (off == 2 ? -0.5f : 0.f));
+    return off == 0 ? 1.5f : (off == -1 ? -2.f : (off == -2 ? 0.5f : 0.f));
+}
+
+// ---------------------------------------------------------------- fused forward step
+
+// Tile position of unit `local` of an instance for tiles TX x TY.
+template <int TX, int TY>
+__device__ __forceinline__ void tile_xy(const Geom& g, int local, int& x0, int& y0) {
+    const int ntx = tile_count(g.n[0], TX, g.periodic[0]);
+    const int ky = local / ntx, kx = local - ky * ntx;
+    x0 = kx * TX - tile_origin(g.n[0], TX, g.periodic[0]);
+    y0 = ky * TY - tile_origin(g.n[1], TY, g.periodic[1]);
+}
+
+// Load a (TY+4) x (TX+4) tile of float4 node records starting at (x0-2, y0-2): periodic axes
+// wrap, positions outside a non-periodic axis read as zero.
+template <int TX, int TY>
+__device__ __forceinline__ void load_tile(const Geom& g, const float4* __restrict__ src, int x0,
+                                          int y0, float4* S) {
+    constexpr int HX = TX + 4, HY = TY + 4;
+    const int n0 = g.n[0], n1 = g.n[1];
+    const bool p0 = g.periodic[0], p1 = g.periodic[1];
+    for (int k = threadIdx.x; k < HX * HY; k += NT) {
+        const int ly = k / HX, lx = k - ly * HX;
+        int gx = x0 - 2 + lx, gy = y0 - 2 + ly;
+        if (p0) gx = wrap_any(gx, n0);
+        if (p1) gy = wrap_any(gy, n1);
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (gx >= 0 && gx < n0 && gy >= 0 && gy < n1) v = __ldg(src + (long long)gy * n0 + gx);
+        S[k] = v;
+    }
+}
+
+// First derivative of the velocity along one axis at a node whose record sits at S[s]
+// (neighbours at +-step): central, or the second-order one-sided difference on a
+// non-periodic boundary node (side -1: low face, +1: high face).
+__device__ __forceinline__ void dvel(const float4* S, int s, int step, int side, float& dux,
+                                     float& duy) {
+    if (side == 0) {
+        const float4 p = S[s + step], m = S[s - step];
+        dux = 0.5f * p.y - 0.5f * m.y;
+        duy = 0.5f * p.z - 0.5f * m.z;
+    } else if (side < 0) {
+        const float4 v = S[s], p1 = S[s + step], p2 = S[s + 2 * step];
+        dux = -1.5f * v.y + 2.f * p1.y - 0.5f * p2.y;
+        duy = -1.5f * v.z + 2.f * p1.z - 0.5f * p2.z;
+    } else {
+        const float4 v = S[s], m1 = S[s - step], m2 = S[s - 2 * step];
+        dux = 1.5f * v.y - 2.f * m1.y + 0.5f * m2.y;
+        duy = 1.5f * v.z - 2.f * m1.z + 0.5f * m2.z;
+    }
+}
+
+__device__ __forceinline__ int face_side(int c, int n, int periodic) {
+    if (periodic) return 0;
+    return c == 0 ? -1 : (c == n - 1 ? 1 : 0);
+}
+
+// A tile is interior when its two-cell halo lies inside the grid at least one node away from
+// every non-periodic boundary: then no index wraps, no node of the halo is a boundary node and
+// no boundary node is sourced from the tile, and the kernels take a path without those tests.
+template <int TX, int TY>
+__device__ __forceinline__ bool interior_tile(const Geom& g, int x0, int y0) {
+    return x0 - 3 >= 0 && x0 + TX + 2 <= g.n[0] - 1 && y0 - 3 >= 0 && y0 + TY + 2 <= g.n[1] - 1;
+}
+
+// f^eq of the eight moving directions at the node whose record is S[s], into F planes at k.
+template <int HX, int FN>
+__device__ __forceinline__ void feq8(const float4* S, int s, float* F, int k, float A,
+                                     float gxx, float gyx, float gxy, float gyy) {
+    constexpr float w1 = 1.f / 9.f, w2 = 1.f / 36.f;
+    const float4 v = S[s];
+    const float uu = v.y * v.y + v.z * v.z;
+    const float base = v.x - 1.5f * uu;
+    const float ax = A * (2.f * gxx), ay = A * (2.f * gyy);
+    const float sd = 2.f * gxx + 2.f * gyy, so = 2.f * (gxy + gyx);
+    const float ad = A * (sd + so), ae = A * (sd - so);
+    const float ux = v.y, uy = v.z;
+    const float cpp = ux + uy, cmp = uy - ux;
+    float* Fk = F + k;
+    Fk[0 * FN] = w1 * (base + 3.f * ux + 4.5f * ux * ux + ax);
+    Fk[1 * FN] = w1 * (base + 3.f * uy + 4.5f * uy * uy + ay);
+    Fk[2 * FN] = w1 * (base - 3.f * ux + 4.5f * ux * ux + ax);
+    Fk[3 * FN] = w1 * (base - 3.f * uy + 4.5f * uy * uy + ay);
+    Fk[4 * FN] = w2 * (base + 3.f * cpp + 4.5f * cpp * cpp + ad);
+    Fk[5 * FN] = w2 * (base + 3.f * cmp + 4.5f * cmp * cmp + ae);
+    Fk[6 * FN] = w2 * (base - 3.f * cpp + 4.5f * cpp * cpp + ad);
+    Fk[7 * FN] = w2 * (base - 3.f * cmp + 4.5f * cmp * cmp + ae);
+}
+
+// One tile of the forward step.  EDGE: the general path (wraps, grid edges, boundary nodes).
+template <int TX, int TY, bool EDGE>
+__device__ __forceinline__ void step_tile(const Inst& I, int x0, int y0, int src, int dst,
+                                          float4* S, float* F) {
+    constexpr int HX = TX + 4, FX = TX + 2, FY = TY + 2, FN = FX * FY;
+    constexpr float w0 = 4.f / 9.f;
+    const Geom& g = I.g;
+    const int n0 = g.n[0], n1 = g.n[1];
+    const float4* sp = (const float4*)I.bufs[src];
+    if (EDGE) {
+        load_tile<TX, TY>(g, sp, x0, y0, S);
+    } else {
+        const float4* base = sp + (long long)(y0 - 2) * n0 + (x0 - 2);
+        for (int k = threadIdx.x; k < HX * (TY + 4); k += NT) {
+            const int ly = k / HX, lx = k - ly * HX;
+            S[k] = __ldg(base + (long long)ly * n0 + lx);
+        }
+    }
+    __syncthreads();
+    const float A = (float)g.A, bfx = (float)g.body[0], bfy = (float)g.body[1];
+    // f^eq of every direction at the tile and its one-cell rim
+    for (int k = threadIdx.x; k < FN; k += NT) {
+        const int fy = k / FX, fx = k - fy * FX;
+        const int s = (fy + 1) * HX + fx + 1;
+        float gxx, gyx, gxy, gyy;   // g_ab = d u_a / d x_b
+        if (EDGE) {
+            int gx = x0 - 1 + fx, gy = y0 - 1 + fy;
+            if (g.periodic[0]) gx = wrap_any(gx, n0);
+            else if (gx < 0 || gx >= n0) continue;
+            if (g.periodic[1]) gy = wrap_any(gy, n1);
+            else if (gy < 0 || gy >= n1) continue;
+            dvel(S, s, 1, face_side(gx, n0, g.periodic[0]), gxx, gyx);
+            dvel(S, s, HX, face_side(gy, n1, g.periodic[1]), gxy, gyy);
+        } else {
+            dvel(S, s, 1, 0, gxx, gyx);
+            dvel(S, s, HX, 0, gxy, gyy);
+        }
+        feq8<HX, FN>(S, s, F, k, A, gxx, gyx, gxy, gyy);
+    }
+    __syncthreads();
+    // gather rho* = sum f_i(x - c_i), u* = sum c_i f_i(x - c_i); Brinkman update; BCs
+    V4<float>* out = (V4<float>*)I.bufs[dst];
+    for (int k = threadIdx.x; k < TX * TY; k += NT) {
+        const int ty = k / TX, tx = k - ty * TX;
+        const int x = x0 + tx, y = y0 + ty;
+        if (EDGE && (x < 0 || x >= n0 || y < 0 || y >= n1 || is_boundary(g, x, y, 0))) continue;
+        const int f = (ty + 1) * FX + tx + 1;
+        const float4 v = S[(ty + 2) * HX + tx + 2];
+        const float f0 = w0 * (v.x - 1.5f * (v.y * v.y + v.z * v.z));
+        const float f1 = F[0 * FN + f - 1];        // from x - (1, 0)
+        const float f2 = F[1 * FN + f - FX];       // from x - (0, 1)
+        const float f3 = F[2 * FN + f + 1];        // from x + (1, 0)
+        const float f4 = F[3 * FN + f + FX];       // from x + (0, 1)
+        const float f5 = F[4 * FN + f - FX - 1];   // from x - (1, 1)
+        const float f6 = F[5 * FN + f - FX + 1];   // from x - (-1, 1)
+        const float f7 = F[6 * FN + f + FX + 1];   // from x + (1, 1)
+        const float f8 = F[7 * FN + f + FX - 1];   // from x - (1, -1)
+        V4<float> o;
+        o.r = f0 + f1 + f2 + f3 + f4 + f5 + f6 + f7 + f8;
+        float usx = (f1 - f3) + (f5 - f6) + (f8 - f7);
+        float usy = (f2 - f4) + (f5 + f6) - (f7 + f8);
+        usx += bfx;
+        usy += bfy;
+        const long long m = (long long)y * n0 + x;
+        long long bi;
+        const float kst = g.ks ? ((const float*)g.ks)[m] : 0.f;
+        if (in_box(g, x, y, 0, bi)) {
+            const V4<float> ks = I.kus[bi];
+            const float inv = 1.f / (1.f + ks.r + kst);
+            o.x = (usx + ks.r * ks.x) * inv;
+            o.y = (usy + ks.r * ks.y) * inv;
+        } else if (kst != 0.f) {
+            const float inv = 1.f / (1.f + kst);
+            o.x = usx * inv;
+            o.y = usy * inv;
+        } else {
+            o.x = usx;
+            o.y = usy;
+        }
+        o.z = 0.f;
+        out[m] = o;
+        if (EDGE) write_bc_from(g, x, y, 0, o, out);
+    }
+    __syncthreads();
+}
+
+template <int TX, int TY>
+__global__ void __launch_bounds__(NT) k_t_step2d(Plan p, const int* __restrict__ pre, int total,
+                                                 int src, int dst) {
+    constexpr int HX = TX + 4, HY = TY + 4;
+    extern __shared__ float4 smem[];
+    float4* S = smem;                          // HY x HX state records
+    float* F = (float*)(smem + HX * HY);       // 8 planes of FY x FX: f_1..f_8
+    __shared__ Inst sI;
+    int cur = -1;
+    for (int u = blockIdx.x; u < total; u += gridDim.x) {
+        const int i = find_inst(pre, p.count, u);
+        stage_inst(p, i, cur, sI);
+        int x0, y0;
+        tile_xy<TX, TY>(sI.g, u - pre[i], x0, y0);
+        if (interior_tile<TX, TY>(sI.g, x0, y0))
+            step_tile<TX, TY, false>(sI, x0, y0, src, dst, S, F);
+        else
+            step_tile<TX, TY, true>(sI, x0, y0, src, dst, S, F);
+    }
+}
+
+// ---------------------------------------------------------------- fused adjoint step
+
+// Objective source of the adjoint step in single precision, fixed per tile.
+struct ObjSrc {
+    bool on;                  // inside the objective window
+    float r, x, y;            // d j / d (rho, ux, uy) at a target node, times h_n
+    bool cyl;
+};
+
+__device__ __forceinline__ ObjSrc obj_src(const Inst& I, int n) {
+    ObjSrc o;
+    o.on = n >= I.win_begin && n <= I.win_end;
+    o.r = I.src_r;
+    o.x = I.src_x;
+    o.y = I.src_y;
+    o.cyl = I.g.ocyl_r > 0.0;
+    return o;
+}
+
+__device__ __forceinline__ bool in_target2(const Geom& g, const ObjSrc& o, int x, int y) {
+    if (x < g.obox[0] || x > g.obox[1] || y < g.obox[2] || y > g.obox[3]) return false;
+    if (o.cyl) {   // the same FP64 test as the host's target list
+        const double dx = x - g.ocyl_c[0], dy = y - g.ocyl_c[1];
+        if (dx * dx + dy * dy > g.ocyl_r * g.ocyl_r) return false;
+    }
+    return true;
+}
+
+// One tile of the adjoint step.  EDGE: the general path (wraps, grid edges, boundary nodes,
+// one-sided boundary rows of the transposed gradient).
+template <int TX, int TY, bool EDGE>
+__device__ __forceinline__ void adj_tile(const Inst& I, int x0, int y0, const ObjSrc& os,
+                                         int lam_in, int lam_out, int sn, int sp, float4* M,
+                                         float* Q) {
+    constexpr int HX = TX + 4, HY = TY + 4, FX = TX + 2, FY = TY + 2, FN = FX * FY;
+    constexpr float w1 = 1.f / 9.f, w2 = 1.f / 36.f, w0 = 4.f / 9.f;
+    const Geom& g = I.g;
+    const int n0 = g.n[0], n1 = g.n[1];
+    const float4* lam = (const float4*)I.bufs[lam_in];
+    const V4<float>* su = (const V4<float>*)I.bufs[sn];
+    // 1. mu on the tile and a two-cell halo; e on the tile's own box nodes
+    for (int k = threadIdx.x; k < HX * HY; k += NT) {
+        const int ly = k / HX, lx = k - ly * HX;
+        int gx = x0 - 2 + lx, gy = y0 - 2 + ly;
+        if (EDGE) {
+            if (g.periodic[0]) gx = wrap_any(gx, n0);
+            if (g.periodic[1]) gy = wrap_any(gy, n1);
+        }
+        float4 m = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (!EDGE || (gx >= 0 && gx < n0 && gy >= 0 && gy < n1 && !is_boundary(g, gx, gy, 0))) {
+            const long long gm = (long long)gy * n0 + gx;
+            const float4 lv = __ldg(lam + gm);
+            float lr = lv.x, lux = lv.y, luy = lv.z;
+            if (os.on && in_target2(g, os, gx, gy)) {
+                lr += os.r;
+                lux += os.x;
+                luy += os.y;
+            }
+            long long bi;
+            const float kst = g.ks ? ((const float*)g.ks)[gm] : 0.f;
+            if (in_box(g, gx, gy, 0, bi)) {
+                const V4<float> ks = I.kus[bi];
+                const float inv = 1.f / (1.f + ks.r + kst);
+                lux *= inv;
+                luy *= inv;
+                const bool own = lx >= 2 && lx < TX + 2 && ly >= 2 && ly < TY + 2;
+                if (own) {
+                    const V4<float> un = su[gm];
+                    I.e[bi] = lux * (ks.x - un.x) + luy * (ks.y - un.y);
+                }
+            } else if (kst != 0.f) {
+                const float inv = 1.f / (1.f + kst);
+                lux *= inv;
+                luy *= inv;
+            }
+            m = make_float4(lr, lux, luy, 0.f);
+        }
+        M[k] = m;
+    }
+    __syncthreads();
+    // 2. moments of F~_i(y) = mu_rho(y + c_i) + c_i . mu_u(y + c_i) on the tile and rim
+    for (int k = threadIdx.x; k < FN; k += NT) {
+        const int fy = k / FX, fx = k - fy * FX;
+        const int s = (fy + 1) * HX + fx + 1;
+        const float4 c0 = M[s];
+        const float4 xp = M[s + 1], xm = M[s - 1], yp = M[s + HX], ym = M[s - HX];
+        const float4 pp = M[s + HX + 1], mp = M[s + HX - 1], mm = M[s - HX - 1],
+                     pm = M[s - HX + 1];
+        const float a1 = w1 * (xp.x + xp.y), a3 = w1 * (xm.x - xm.y);
+        const float a2 = w1 * (yp.x + yp.z), a4 = w1 * (ym.x - ym.z);
+        const float a5 = w2 * (pp.x + pp.y + pp.z), a6 = w2 * (mp.x - mp.y + mp.z);
+        const float a7 = w2 * (mm.x - mm.y - mm.z), a8 = w2 * (pm.x + pm.y - pm.z);
+        Q[k] = w0 * c0.x + a1 + a2 + a3 + a4 + a5 + a6 + a7 + a8;
+        Q[FN + k] = (a1 - a3) + (a5 - a6) + (a8 - a7);
+        Q[2 * FN + k] = (a2 - a4) + (a5 + a6) - (a7 + a8);
+        Q[3 * FN + k] = (a1 + a3) + (a5 + a6) + (a7 + a8);
+        Q[4 * FN + k] = (a5 - a6) + (a7 - a8);
+        Q[5 * FN + k] = (a2 + a4) + (a5 + a6) + (a7 + a8);
+    }
+    __syncthreads();
+    // 3. lambda^{n-1} = (R~, 3 U~ - 3 R~ u + 9 S~ u + D^T (2 A S~)) on the tile
+    const V4<float>* sprev = (const V4<float>*)I.bufs[sp];
+    V4<float>* out = (V4<float>*)I.bufs[lam_out];
+    const float twoA = (float)(2.0 * g.A);
+    for (int k = threadIdx.x; k < TX * TY; k += NT) {
+        const int ty = k / TX, tx = k - ty * TX;
+        const int x = x0 + tx, y = y0 + ty;
+        if (EDGE && (x < 0 || x >= n0 || y < 0 || y >= n1)) continue;
+        const int q = (ty + 1) * FX + tx + 1;
+        const V4<float> v = sprev[(long long)y * n0 + x];
+        const float R = Q[q], Ux = Q[FN + q], Uy = Q[2 * FN + q];
+        const float Sxx = Q[3 * FN + q], Sxy = Q[4 * FN + q], Syy = Q[5 * FN + q];
+        float lx = 3.f * Ux - 3.f * R * v.x;
+        float ly = 3.f * Uy - 3.f * R * v.y;
+        lx += 9.f * Sxx * v.x;
+        lx += 9.f * Sxy * v.y;
+        ly += 9.f * Sxy * v.x;
+        ly += 9.f * Syy * v.y;
+        // transposed gradient: rows y' = x - kk e_b whose stencil reaches x; phi_ab = 2 A S~_ab,
+        // b = x uses (Sxx, Sxy), b = y uses (Sxy, Syy)
+        float ax = 0.f, ay = 0.f;
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            const int c = b == 0 ? x : y, nn = b == 0 ? n0 : n1, per = g.periodic[b];
+            const int step = b == 0 ? 1 : FX;
+#pragma unroll
+            for (int kk = -2; kk <= 2; ++kk) {
+                float cf;
+                if (EDGE) {
+                    int yi = c - kk;
+                    if (per) yi = wrap_any(yi, nn);
+                    else if (yi < 0 || yi >= nn) continue;
+                    cf = deriv_coef_f(yi, nn, per, kk);
+                    if (cf == 0.f) continue;
+                } else {
+                    if (kk != 1 && kk != -1) continue;
+                    cf = kk == 1 ? 0.5f : -0.5f;
+                }
+                const int qq = q - kk * step;
+                // rows two nodes away are boundary rows, which the tile origin keeps inside
+                // the tile; the test only keeps a shared-memory read in bounds regardless
+                if (EDGE && (qq < 0 || qq >= FN)) continue;
+                const float pa = twoA * Q[(b == 0 ? 3 : 4) * FN + qq];
+                const float pb = twoA * Q[(b == 0 ? 4 : 5) * FN + qq];
+                ax += cf * pa;
+                ay += cf * pb;
+            }
+        }
+        V4<float> o;
+        o.r = R;
+        o.x = lx + ax;
+        o.y = ly + ay;
+        o.z = 0.f;
+        out[(long long)y * n0 + x] = o;
+    }
+    __syncthreads();
+}
+
+template <int TX, int TY>
+__global__ void __launch_bounds__(NT) k_t_adj2d(Plan p, const int* __restrict__ pre, int total,
+                                                int noff, int lam_in, int lam_out, int sn,
+                                                int sp) {
+    constexpr int HX = TX + 4, HY = TY + 4;
+    extern __shared__ float4 smem[];
+    float4* M = smem;                          // HY x HX: mu (rho, x, y, -)
+    float* Q = (float*)(smem + HX * HY);       // 6 planes of FY x FX: R, Ux, Uy, Sxx, Sxy, Syy
+    const int n = step_of(p, noff);
+    __shared__ Inst sI;
+    int cur = -1;
+    ObjSrc os;
+    for (int u = blockIdx.x; u < total; u += gridDim.x) {
+        const int i = find_inst(pre, p.count, u);
+        if (i != cur) {
+            stage_inst(p, i, cur, sI);
+            os = obj_src(sI, n);
+        }
+        int x0, y0;
+        tile_xy<TX, TY>(sI.g, u - pre[i], x0, y0);
+        if (interior_tile<TX, TY>(sI.g, x0, y0))
+            adj_tile<TX, TY, false>(sI, x0, y0, os, lam_in, lam_out, sn, sp, M, Q);
+        else
+            adj_tile<TX, TY, true>(sI, x0, y0, os, lam_in, lam_out, sn, sp, M, Q);
+    }
+}
+
+template <int C>
+struct Cfg {
+    static constexpr int TX = tile_tx(C), TY = tile_ty(C);
+    static constexpr size_t step_smem = (size_t)(TX + 4) * (TY + 4) * 16 + (size_t)8 * (TX + 2) * (TY + 2) * 4;
+    static constexpr size_t adj_smem = (size_t)(TX + 4) * (TY + 4) * 16 + (size_t)6 * (TX + 2) * (TY + 2) * 4;
+};
+
+template <int C>
+int occ_step() {
+    int b = 0;
+    cudaFuncSetAttribute(k_t_step2d<Cfg<C>::TX, Cfg<C>::TY>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg<C>::step_smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_t_step2d<Cfg<C>::TX, Cfg<C>::TY>, NT,
+                                                  Cfg<C>::step_smem);
+    return b;
+}
+template <int C>
+int occ_adj() {
+    int b = 0;
+    cudaFuncSetAttribute(k_t_adj2d<Cfg<C>::TX, Cfg<C>::TY>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg<C>::adj_smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_t_adj2d<Cfg<C>::TX, Cfg<C>::TY>, NT,
+                                                  Cfg<C>::adj_smem);
+    return b;
+}
+
+int sm_count() {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms > 0 ? sms : 1;
+}
+
+int cap_grid(long long units, int per_sm) {
+    const long long g = (long long)sm_count() * std::max(per_sm, 1);
+    return (int)std::max(1LL, std::min(units, g));
+}
+
+template <int C>
+cudaError_t step_cfg(const Plan& p, int src, int dst, cudaStream_t st) {
+    const int unit = U_TILE0 + C;
+    if (p.total[unit] == 0) return cudaSuccess;
+    k_t_step2d<Cfg<C>::TX, Cfg<C>::TY><<<p.grid[unit], NT, Cfg<C>::step_smem, st>>>(
+        p, p.pre + unit * (p.count + 1), p.total[unit], src, dst);
+    return cudaGetLastError();
+}
+
+template <int C>
+cudaError_t adj_cfg(const Plan& p, int noff, int li, int lo, int sn, int sp, cudaStream_t st) {
+    const int unit = U_TILE0 + C;
+    if (p.total[unit] == 0) return cudaSuccess;
+    k_t_adj2d<Cfg<C>::TX, Cfg<C>::TY><<<p.grid[U_COUNT + C], NT, Cfg<C>::adj_smem, st>>>(
+        p, p.pre + unit * (p.count + 1), p.total[unit], noff, li, lo, sn, sp);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+void plan_grids(Plan& p) {
+    int b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_t_transfer2d, NT, 0);
+    p.grid[U_BOX] = cap_grid(p.total[U_BOX], b);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_t_design_pos, NT, 0);
+    p.grid[U_DCOL] = cap_grid(p.total[U_DCOL], b);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_t_bcT2d, NT, 0);
+    p.grid[U_SHELL] = cap_grid(p.total[U_SHELL], b);
+    p.grid[U_INST] = std::max(1, p.count);
+    const int os[kTileCfgs] = {occ_step<0>(), occ_step<1>(), occ_step<2>(), occ_step<3>(),
+                               occ_step<4>()};
+    const int oa[kTileCfgs] = {occ_adj<0>(), occ_adj<1>(), occ_adj<2>(), occ_adj<3>(),
+                               occ_adj<4>()};
+    for (int c = 0; c < kTileCfgs; ++c) {
+        p.grid[U_TILE0 + c] = cap_grid(p.total[U_TILE0 + c], os[c]);
+        p.grid[U_COUNT + c] = cap_grid(p.total[U_TILE0 + c], oa[c]);
+    }
+    cudaGetLastError();
+}
+
+cudaError_t launch_t_design_pos(const Plan& p, int noff, cudaStream_t st) {
+    if (p.total[U_DCOL] == 0) return cudaSuccess;
+    k_t_design_pos<<<p.grid[U_DCOL], NT, 0, st>>>(p, noff);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_t_transfer2d(const Plan& p, int noff, cudaStream_t st) {
+    if (p.total[U_BOX] == 0) return cudaSuccess;
+    k_t_transfer2d<<<p.grid[U_BOX], NT, 0, st>>>(p, noff);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_t_step2d(const Plan& p, int cfg, int src, int dst, cudaStream_t st) {
+    switch (cfg) {
+        case 0: return step_cfg<0>(p, src, dst, st);
+        case 1: return step_cfg<1>(p, src, dst, st);
+        case 2: return step_cfg<2>(p, src, dst, st);
+        case 3: return step_cfg<3>(p, src, dst, st);
+        case 4: return step_cfg<4>(p, src, dst, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_t_objective(const Plan& p, int noff, int src, cudaStream_t st) {
+    k_t_objective<<<p.grid[U_INST], kObjThreads, 0, st>>>(p, noff, src);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_t_bcT2d(const Plan& p, int noff, int lam, cudaStream_t st) {
+    if (p.total[U_SHELL] == 0) return cudaSuccess;
+    k_t_bcT2d<<<p.grid[U_SHELL], NT, 0, st>>>(p, noff, lam);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_t_adj2d(const Plan& p, int cfg, int noff, int lam_in, int lam_out, int sn,
+                           int sp, cudaStream_t st) {
+    switch (cfg) {
+        case 0: return adj_cfg<0>(p, noff, lam_in, lam_out, sn, sp, st);
+        case 1: return adj_cfg<1>(p, noff, lam_in, lam_out, sn, sp, st);
+        case 2: return adj_cfg<2>(p, noff, lam_in, lam_out, sn, sp, st);
+        case 3: return adj_cfg<3>(p, noff, lam_in, lam_out, sn, sp, st);
+        case 4: return adj_cfg<4>(p, noff, lam_in, lam_out, sn, sp, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_t_sens(const Plan& p, cudaStream_t st) {
+    if (p.total[U_DCOL] == 0) return cudaSuccess;
+    k_t_sens<<<p.grid[U_DCOL], NT, 0, st>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_int(int* dst, int v, cudaStream_t st) {
+    k_set_int<<<1, 1, 0, st>>>(dst, v);
+    return cudaGetLastError();
+}
+
+}  // namespace lks

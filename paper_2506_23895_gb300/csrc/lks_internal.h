@@ -37,6 +37,7 @@ struct Geom {
     double ocyl_r, ocyl_c[2];
     double ocount;
     const int* otarget;   // node indices of the target region, ascending (device)
+    const void* ks;       // static Brinkman coefficient per node (T, device) or nullptr
 };
 
 // Design grid and per-step rigid motion.
@@ -57,6 +58,7 @@ struct Motion {
 struct TransferScratch {
     int* col_base;       // [ncol][2] floor of x_ref, y_ref per design column
     void* col_frac;      // [ncol][2] T: fractional part in [0,1)
+    float4* col_sc;      // [ncol] sin, cos of (pi f / 2) for f = x and y fractions (2D table path)
     int* zt_idx;         // [bn_z][4] design z index per analysis z of the box (-1: none)
     void* zt_w;          // [bn_z][4] T: kernel weight
     int* tap_cnt;        // [box columns]
@@ -124,11 +126,20 @@ void launch_transfer(const Design& d, const Geom& g, const Motion& m, TransferSc
 template <class T>
 void launch_sens(const Design& d, const Geom& g, TransferScratch ts, const T* e,
                  const T* kprime, double* gacc, cudaStream_t st);
+// Design chain (FP64): gb = H(F gamma), hp = H'(F gamma), wsum = filter normaliser; the
+// transposed chain out = F^T (hp * g) (hp = nullptr: F^T g); a fixed-order sum.
+void launch_filter(const Design& d, double R, double beta, double eta, const double* gamma,
+                   double* gb, double* hp, double* wsum, cudaStream_t st);
+void launch_filter_T(const Design& d, double R, const double* g, const double* hp,
+                     const double* wsum, double* out, cudaStream_t st);
+void launch_design_sum(long long nd, const double* a, double* out, cudaStream_t st);
+void launch_fill_f64(double* a, long long n, double v, cudaStream_t st);
 template <class T>
 void launch_box_to_grid(const Geom& g, const V4<T>* kus, double* kappa, double* us,
                         cudaStream_t st);
 template <class T>
-void launch_state_to_f64(const Geom& g, const V4<T>* s, double* out, cudaStream_t st);
+void launch_state_to_f64(const Geom& g, const V4<T>* s, double* out, cudaStream_t st,
+                         bool add_rho0 = true);
 template <class T>
 void launch_state_from_f64(const Geom& g, const double* in, V4<T>* s, cudaStream_t st);
 

@@ -137,12 +137,19 @@ __global__ void k_gather(Geom g, const T* __restrict__ F, const V4<T>* __restric
     V4<T> o;
     o.r = rs;
     long long bi;
+    // a static solid adds kappa_s (solid velocity 0) to the Brinkman denominator
+    const T kst = g.ks ? ((const T*)g.ks)[m] : (T)0;
     if (in_box(g, x, y, z, bi)) {
         const V4<T> ks = kus[bi];
-        const T k = ks.r, inv = (T)1 / ((T)1 + k);
+        const T k = ks.r, inv = (T)1 / ((T)1 + k + kst);
         o.x = (us[0] + (T)g.body[0] + k * ks.x) * inv;
         o.y = (us[1] + (T)g.body[1] + k * ks.y) * inv;
         o.z = (D == 3) ? (us[2] + (T)g.body[2] + k * ks.z) * inv : (T)0;
+    } else if (kst != (T)0) {
+        const T inv = (T)1 / ((T)1 + kst);
+        o.x = (us[0] + (T)g.body[0]) * inv;
+        o.y = (us[1] + (T)g.body[1]) * inv;
+        o.z = (D == 3) ? (us[2] + (T)g.body[2]) * inv : (T)0;
     } else {
         o.x = us[0] + (T)g.body[0];
         o.y = us[1] + (T)g.body[1];
@@ -204,8 +211,8 @@ __global__ void k_adj_bcT(Geom g, V4<T>* lam, double h) {
     bcT_node<T>(g, lam, h, x, y, z);
 }
 
-// mu = (lam_rho, lam_u / (1 + kappa)) on interior nodes, 0 on boundary nodes; in the
-// footprint box also e = mu_u . (u_S - u^n) = dJ/dkappa(x, t_n).
+// mu = (lam_rho, lam_u / (1 + kappa + kappa_s)) on interior nodes, 0 on boundary nodes; in
+// the footprint box also e = mu_u . (u_S - u^n) = dJ/dkappa(x, t_n).
 template <class T>
 __global__ void k_adj_mu(Geom g, const V4<T>* __restrict__ lam, const V4<T>* __restrict__ kus,
                          const V4<T>* __restrict__ sn, V4<T>* __restrict__ mu,
@@ -224,9 +231,14 @@ __global__ void k_adj_mu(Geom g, const V4<T>* __restrict__ lam, const V4<T>* __r
     obj_source(g, x, y, z, h, l);
     o.r = l.r;
     long long bi;
-    if (in_box(g, x, y, z, bi)) {
-        const V4<T> ks = kus[bi];
-        const T inv = (T)1 / ((T)1 + ks.r);
+    const T kst = g.ks ? ((const T*)g.ks)[m] : (T)0;
+    const bool box = in_box(g, x, y, z, bi);
+    if (box || kst != (T)0) {
+        V4<T> ks;
+        ks.r = ks.x = ks.y = ks.z = (T)0;
+        if (box) ks = kus[bi];
+        const T kt = ks.r + kst;   // moving and static Brinkman coefficients
+        const T inv = (T)1 / ((T)1 + kt);
         if (u3) {
             // printed ALKS (Eqs. au, au_ex): only the gathered first moment 3 U~ and the
             // objective source take the (1 + kappa)^-1 of the Brinkman term
@@ -235,7 +247,7 @@ __global__ void k_adj_mu(Geom g, const V4<T>* __restrict__ lam, const V4<T>* __r
             src.x = l.x - lam[m].x;
             src.y = l.y - lam[m].y;
             src.z = l.z - lam[m].z;
-            const T fac = ks.r * inv;
+            const T fac = kt * inv;
             o.x = l.x - (a3.x + src.x) * fac;
             o.y = l.y - (a3.y + src.y) * fac;
             o.z = l.z - (a3.z + src.z) * fac;
@@ -244,8 +256,10 @@ __global__ void k_adj_mu(Geom g, const V4<T>* __restrict__ lam, const V4<T>* __r
             o.y = l.y * inv;
             o.z = l.z * inv;
         }
-        const V4<T> v = sn[m];
-        e[bi] = o.x * (ks.x - v.x) + o.y * (ks.y - v.y) + o.z * (ks.z - v.z);
+        if (box) {
+            const V4<T> v = sn[m];
+            e[bi] = o.x * (ks.x - v.x) + o.y * (ks.y - v.y) + o.z * (ks.z - v.z);
+        }
     } else {
         o.x = l.x;
         o.y = l.y;
@@ -373,11 +387,12 @@ __global__ void k_check_state(Geom g, const V4<T>* __restrict__ s, int* flag) {
 }
 
 template <class T>
-__global__ void k_state_to_f64(Geom g, const V4<T>* __restrict__ s, double* __restrict__ out) {
+__global__ void k_state_to_f64(Geom g, const V4<T>* __restrict__ s, double* __restrict__ out,
+                               double r0) {
     long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (m >= g.nodes) return;
     const V4<T> v = s[m];
-    out[m] = g.rho0 + (double)v.r;
+    out[m] = r0 + (double)v.r;
     out[g.nodes + m] = (double)v.x;
     out[2 * g.nodes + m] = (double)v.y;
     out[3 * g.nodes + m] = (double)v.z;
@@ -464,8 +479,10 @@ void launch_check_state(const Geom& g, const V4<T>* s, int* flag, cudaStream_t s
 }
 
 template <class T>
-void launch_state_to_f64(const Geom& g, const V4<T>* s, double* out, cudaStream_t st) {
-    k_state_to_f64<T><<<grid_for(g.nodes), kThreads, 0, st>>>(g, s, out);
+void launch_state_to_f64(const Geom& g, const V4<T>* s, double* out, cudaStream_t st,
+                         bool add_rho0) {
+    k_state_to_f64<T><<<grid_for(g.nodes), kThreads, 0, st>>>(g, s, out,
+                                                               add_rho0 ? g.rho0 : 0.0);
 }
 
 template <class T>
@@ -487,7 +504,7 @@ void launch_state_from_f64(const Geom& g, const double* in, V4<T>* s, cudaStream
                                         cudaStream_t, V4<T>*);                               \
     template void launch_adj_divT<T>(const Geom&, const T*, V4<T>*, cudaStream_t);           \
     template void launch_check_state<T>(const Geom&, const V4<T>*, int*, cudaStream_t);      \
-    template void launch_state_to_f64<T>(const Geom&, const V4<T>*, double*, cudaStream_t);  \
+    template void launch_state_to_f64<T>(const Geom&, const V4<T>*, double*, cudaStream_t, bool);  \
     template void launch_state_from_f64<T>(const Geom&, const double*, V4<T>*, cudaStream_t);
 
 LKS_INST(float)

@@ -225,7 +225,102 @@ __global__ void k_box_to_grid(Geom g, const V4<T>* __restrict__ kus, double* kap
     us[2 * g.nodes + m] = c;
 }
 
+// ---------------------------------------------------------------- design chain
+// Density filter with linear weights w = max(0, R - |xi_i - xi_j|) over the design grid and the
+// tanh Heaviside projection (the projection filter the paper cites, Secs. 1 and 3.1), in FP64:
+// gb = H(F gamma), hp = H'(F gamma), wsum = sum_j w_ij.  One thread per design node, offsets
+// visited in (z, y, x) order.
+__global__ void k_filter(Design d, double R, int rr, double beta, double eta,
+                         const double* __restrict__ gamma, double* __restrict__ gb,
+                         double* __restrict__ hp, double* __restrict__ wsum) {
+    const long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (k >= d.nd) return;
+    const int x = (int)(k % d.L[0]), y = (int)((k / d.L[0]) % d.L[1]), z = (int)(k / d.ncol);
+    const int rz = d.L[2] > 1 ? rr : 0;
+    double acc = 0.0, W = 0.0;
+    for (int dz = -rz; dz <= rz; ++dz)
+        for (int dy = -rr; dy <= rr; ++dy)
+            for (int dx = -rr; dx <= rr; ++dx) {
+                const double w = R - sqrt((double)(dx * dx + dy * dy + dz * dz));
+                if (!(w > 0.0)) continue;
+                const int xx = x + dx, yy = y + dy, zz = z + dz;
+                if (xx < 0 || yy < 0 || zz < 0 || xx >= d.L[0] || yy >= d.L[1] || zz >= d.L[2])
+                    continue;
+                acc += w * gamma[((long long)zz * d.L[1] + yy) * d.L[0] + xx];
+                W += w;
+            }
+    const double gt = acc / W;
+    const double den = tanh(beta * eta) + tanh(beta * (1.0 - eta));
+    const double t = tanh(beta * (gt - eta));
+    gb[k] = (tanh(beta * eta) + t) / den;
+    hp[k] = beta * (1.0 - t * t) / den;
+    wsum[k] = W;
+}
+
+// Transposed chain: out_j = sum_i w_ij hp_i g_i / wsum_i (a gather over the same offsets).
+__global__ void k_filter_T(Design d, double R, int rr, const double* __restrict__ g,
+                           const double* __restrict__ hp, const double* __restrict__ wsum,
+                           double* __restrict__ out) {
+    const long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (k >= d.nd) return;
+    const int x = (int)(k % d.L[0]), y = (int)((k / d.L[0]) % d.L[1]), z = (int)(k / d.ncol);
+    const int rz = d.L[2] > 1 ? rr : 0;
+    double acc = 0.0;
+    for (int dz = -rz; dz <= rz; ++dz)
+        for (int dy = -rr; dy <= rr; ++dy)
+            for (int dx = -rr; dx <= rr; ++dx) {
+                const double w = R - sqrt((double)(dx * dx + dy * dy + dz * dz));
+                if (!(w > 0.0)) continue;
+                const int xx = x + dx, yy = y + dy, zz = z + dz;
+                if (xx < 0 || yy < 0 || zz < 0 || xx >= d.L[0] || yy >= d.L[1] || zz >= d.L[2])
+                    continue;
+                const long long i = ((long long)zz * d.L[1] + yy) * d.L[0] + xx;
+                acc += w * (hp ? hp[i] * g[i] : g[i]) / wsum[i];
+            }
+    out[k] = acc;
+}
+
+// sum of a design field in a fixed order (one block, FP64 tree), for the volume constraint.
+__global__ void k_design_sum(long long nd, const double* __restrict__ a, double* out) {
+    __shared__ double red[kThreads];
+    double acc = 0.0;
+    for (long long k = threadIdx.x; k < nd; k += kThreads) acc += a[k];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = kThreads / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = red[0];
+}
+
+__global__ void k_fill_f64(long long n, double v, double* a) {
+    const long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (k < n) a[k] = v;
+}
+
 }  // namespace
+
+void launch_fill_f64(double* a, long long n, double v, cudaStream_t st) {
+    if (n > 0) k_fill_f64<<<grid_for(n), kThreads, 0, st>>>(n, v, a);
+}
+
+void launch_filter(const Design& d, double R, double beta, double eta, const double* gamma,
+                   double* gb, double* hp, double* wsum, cudaStream_t st) {
+    if (d.nd == 0) return;
+    k_filter<<<grid_for(d.nd), kThreads, 0, st>>>(d, R, (int)ceil(R), beta, eta, gamma, gb, hp,
+                                                  wsum);
+}
+
+void launch_filter_T(const Design& d, double R, const double* g, const double* hp,
+                     const double* wsum, double* out, cudaStream_t st) {
+    if (d.nd == 0) return;
+    k_filter_T<<<grid_for(d.nd), kThreads, 0, st>>>(d, R, (int)ceil(R), g, hp, wsum, out);
+}
+
+void launch_design_sum(long long nd, const double* a, double* out, cudaStream_t st) {
+    k_design_sum<<<1, kThreads, 0, st>>>(nd, a, out);
+}
 
 template <class T>
 void launch_design_prep(const Design& d, const double* gamma, double kappa_max, double q,

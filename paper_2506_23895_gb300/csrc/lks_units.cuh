@@ -24,46 +24,97 @@ __device__ __forceinline__ void design_col_pos(const Design& d, const Motion& m,
     frac[2 * k + 1] = (T)(yr - by);
 }
 
-// ---------------------------------------------------------------- 2D transfer, one box node
+// ---------------------------------------------------------------- 2D transfer (table path)
+// Design column k for the D2Q9 instance-table kernels: integer base of x_ref, y_ref (FP64, as
+// design_col_pos) and, per axis, S = sin(pi f/2), C = cos(pi f/2) of the fraction f.  The four
+// taps of the cosine kernel then follow without further trigonometry: for an analysis node at
+// base + q, q = -1, 0, 1, 2, w = (1 - S)/4, (1 + C)/4, (1 + S)/4, (1 - C)/4 (w(r) =
+// (1 + cos(pi r/2))/4 at r = q - f).
+__device__ __forceinline__ void design_col_pos_sc(const Design& d, const Motion& m,
+                                                  const TransferScratch& ts, long long k) {
+    const int i = (int)((unsigned)k % (unsigned)d.L[0]), j = (int)((unsigned)k / (unsigned)d.L[0]);
+    const double dx = i - d.xiG[0], dy = j - d.xiG[1];
+    const double xr = m.c * dx - m.s * dy + m.xG[0];   // Eq. rigid_body_position
+    const double yr = m.s * dx + m.c * dy + m.xG[1];
+    const double bx = floor(xr), by = floor(yr);
+    reinterpret_cast<int2*>(ts.col_base)[k] = make_int2((int)bx, (int)by);
+    float4 sc;
+    sincospif(0.5f * (float)(xr - bx), &sc.x, &sc.y);
+    sincospif(0.5f * (float)(yr - by), &sc.z, &sc.w);
+    ts.col_sc[k] = sc;
+}
+
+__device__ __forceinline__ float tap_weight(int q1, float S, float C) {
+    // q1 = q + 1 in 0..3
+    const float t = q1 == 0 ? -S : (q1 == 1 ? C : (q1 == 2 ? S : -C));
+    return 0.25f * (1.f + t);
+}
+
 // kappa(x) = sum_xi W(x - x_ref(xi)) kappa_ref(xi) and u_S = omega R'(theta) m1 + u_G m0 with
-// m0 = sum W, m1 = sum W (xi - xi_G) (Eqs. brinkman_ref, velocity_ref; u_ref is affine in xi).
-// The design nodes whose support covers x are found through the inverse rigid map and summed
-// in design index order.
-template <class T>
+// m0 = sum W, m1 = sum W (xi - xi_G) at box node bi (Eqs. brinkman_ref, velocity_ref; u_ref is
+// affine in xi).  The design nodes whose taps cover x are found through the inverse rigid map
+// (a window widened against rounding) and summed in design index order.
 __device__ __forceinline__ void transfer2d_node(const Design& d, const Geom& g, const Motion& m,
                                                 const TransferScratch& ts,
-                                                const T* __restrict__ kref, V4<T>* kus,
-                                                long long bi) {
+                                                const float* __restrict__ kref,
+                                                V4<float>* kus, long long bi) {
     const int x = g.blo[0] + (int)((unsigned)bi % (unsigned)g.bn[0]);
     const int y = g.blo[1] + (int)((unsigned)bi / (unsigned)g.bn[0]);
-    const double px = x - m.xG[0], py = y - m.xG[1];
-    const double ic = m.c * px + m.s * py + d.xiG[0];
-    const double jc = -m.s * px + m.c * py + d.xiG[1];
-    const double R = 2.0 * (fabs(m.c) + fabs(m.s)) + 1e-6;
-    const int i0 = max(0, (int)ceil(ic - R)), i1 = min(d.L[0] - 1, (int)floor(ic + R));
-    const int j0 = max(0, (int)ceil(jc - R)), j1 = min(d.L[1] - 1, (int)floor(jc + R));
-    const T* frac = (const T*)ts.col_frac;
-    T kap = (T)0, m0 = (T)0, m1x = (T)0, m1y = (T)0;
+    const float c = (float)m.c, s = (float)m.s;
+    const float px = (float)(x - m.xG[0]), py = (float)(y - m.xG[1]);
+    const float ic = c * px + s * py + (float)d.xiG[0];
+    const float jc = -s * px + c * py + (float)d.xiG[1];
+    const float R = 2.f * (fabsf(c) + fabsf(s)) + 0.01f;
+    const int i0 = max(0, (int)ceilf(ic - R)), i1 = min(d.L[0] - 1, (int)floorf(ic + R));
+    const int j0 = max(0, (int)ceilf(jc - R)), j1 = min(d.L[1] - 1, (int)floorf(jc + R));
+    const int2* base = reinterpret_cast<const int2*>(ts.col_base);
+    const float gx0 = (float)d.xiG[0], gy0 = (float)d.xiG[1];
+    float kap = 0.f, m0 = 0.f, m1x = 0.f, m1y = 0.f;
     for (int j = j0; j <= j1; ++j)
         for (int i = i0; i <= i1; ++i) {
-            const long long k = (long long)j * d.L[0] + i;
-            const T rx = (T)(x - ts.col_base[2 * k]) - frac[2 * k];
-            const T ry = (T)(y - ts.col_base[2 * k + 1]) - frac[2 * k + 1];
-            if (!(fabs((double)rx) < 2.0 && fabs((double)ry) < 2.0)) continue;
-            const T W = peskin(rx) * peskin(ry);
-            if (W == (T)0) continue;
-            kap += W * kref[k];
+            const int k = j * d.L[0] + i;
+            const int2 b = __ldg(base + k);
+            const int qx = x - b.x + 1, qy = y - b.y + 1;
+            if ((unsigned)qx > 3u || (unsigned)qy > 3u) continue;
+            const float4 sc = __ldg(ts.col_sc + k);
+            const float W = tap_weight(qx, sc.x, sc.y) * tap_weight(qy, sc.z, sc.w);
+            kap += W * __ldg(kref + k);
             m0 += W;
-            m1x += W * (T)(i - d.xiG[0]);
-            m1y += W * (T)(j - d.xiG[1]);
+            m1x += W * ((float)i - gx0);
+            m1y += W * ((float)j - gy0);
         }
-    const T om = (T)m.om, c = (T)m.c, s = (T)m.s;
-    V4<T> o;
+    const float om = (float)m.om;
+    V4<float> o;
     o.r = kap;
-    o.x = (-s * m1x - c * m1y) * om + (T)m.uG[0] * m0;
-    o.y = (c * m1x - s * m1y) * om + (T)m.uG[1] * m0;
-    o.z = (T)0;
+    o.x = (-s * m1x - c * m1y) * om + (float)m.uG[0] * m0;
+    o.y = (c * m1x - s * m1y) * om + (float)m.uG[1] * m0;
+    o.z = 0.f;
     kus[bi] = o;
+}
+
+// Sensitivity gather for design node k on the table path: sum over its 4 x 4 taps of
+// W e(x) with the same tap weights as transfer2d_node, times kappa', added to dJ/dgamma (FP64).
+__device__ __forceinline__ void sens2d_node(const Design& d, const Geom& g,
+                                            const TransferScratch& ts, const float* __restrict__ e,
+                                            const float* __restrict__ kprime,
+                                            double* __restrict__ gacc, long long k) {
+    const int2 b = reinterpret_cast<const int2*>(ts.col_base)[k];
+    const float4 sc = ts.col_sc[k];
+    const int ex0 = b.x - 1 - g.blo[0], ey0 = b.y - 1 - g.blo[1];
+    float acc = 0.f;
+#pragma unroll
+    for (int ty = 0; ty < 4; ++ty) {
+        const int ey = ey0 + ty;
+        if (ey < 0 || ey >= g.bn[1]) continue;
+        const float wy = tap_weight(ty, sc.z, sc.w);
+#pragma unroll
+        for (int tx = 0; tx < 4; ++tx) {
+            const int ex = ex0 + tx;
+            if (ex < 0 || ex >= g.bn[0]) continue;
+            acc += (tap_weight(tx, sc.x, sc.y) * wy) * e[(long long)ey * g.bn[0] + ex];
+        }
+    }
+    gacc[k] += (double)kprime[k] * (double)acc;
 }
 
 // ---------------------------------------------------------------- sensitivity gather (Sec. 2.4)
@@ -169,12 +220,6 @@ __device__ __forceinline__ void obj_source(const Geom& g, int x, int y, int z, d
         l.y += (T)(-h * g.odir[1] / g.ocount);
         l.z += (T)(-h * g.odir[2] / g.ocount);
     }
-}
-
-// Window weight h_n of step n: 1/(window length) inside the window, else 0.
-__host__ __device__ __forceinline__ double window_weight(int n, int wb, int we) {
-    const double h = 1.0 / (double)(we - wb + 1);
-    return (n >= wb && n <= we) ? h : 0.0;
 }
 
 // ---------------------------------------------------------------- boundary transpose

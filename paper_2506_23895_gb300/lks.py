@@ -23,7 +23,11 @@ STATUS = {0: "LKS_OK", 1: "LKS_ERR_ARG", 2: "LKS_ERR_ORDER", 3: "LKS_ERR_NOMEM",
 EXPORTS = ("lks_workspace_bytes", "lks_create", "lks_set_design", "lks_set_motion",
            "lks_set_initial_state", "lks_forward", "lks_adjoint", "lks_get_state",
            "lks_transfer", "lks_uses_fused", "lks_get_stats", "lks_set_timing", "lks_read_timing",
-           "lks_checkpoint_schedule", "lks_step_noalloc", "lks_last_error", "lks_destroy")
+           "lks_checkpoint_schedule", "lks_step_noalloc", "lks_last_error", "lks_destroy",
+           "lks_batch_create", "lks_batch_set_options", "lks_batch_forward", "lks_batch_adjoint",
+           "lks_batch_tile_shapes", "lks_batch_tuning", "lks_batch_stats",
+           "lks_batch_last_error", "lks_batch_destroy", "lks_set_filter", "lks_volume",
+           "lks_set_static", "lks_warm_start", "lks_set_adjoint_start", "lks_get_adjoint_state")
 
 
 class LksError(RuntimeError):
@@ -97,6 +101,33 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.lks_last_error.restype = ctypes.c_char_p
     lib.lks_destroy.argtypes = [P]
     lib.lks_destroy.restype = None
+    lib.lks_set_filter.argtypes = [P, ctypes.c_double, ctypes.c_double, ctypes.c_double]
+    lib.lks_set_filter.restype = ctypes.c_int
+    lib.lks_volume.argtypes = [P, ctypes.c_double, D, P, ctypes.c_int]
+    lib.lks_volume.restype = ctypes.c_int
+    lib.lks_set_static.argtypes = [P, D]
+    lib.lks_warm_start.argtypes = [P]
+    lib.lks_set_adjoint_start.argtypes = [P, ctypes.c_int]
+    lib.lks_get_adjoint_state.argtypes = [P, D]
+    for name in ("lks_set_static", "lks_warm_start", "lks_set_adjoint_start",
+                 "lks_get_adjoint_state"):
+        getattr(lib, name).restype = ctypes.c_int
+    lib.lks_batch_create.argtypes = [ctypes.POINTER(P), ctypes.c_int, ctypes.POINTER(P)]
+    lib.lks_batch_set_options.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    lib.lks_batch_forward.argtypes = [P, ctypes.c_int, D]
+    lib.lks_batch_adjoint.argtypes = [P, ctypes.POINTER(P), ctypes.c_int]
+    lib.lks_batch_tile_shapes.argtypes = [ctypes.POINTER(ctypes.c_int), ctypes.c_int]
+    lib.lks_batch_tile_shapes.restype = ctypes.c_int
+    lib.lks_batch_tuning.argtypes = [P, ctypes.POINTER(ctypes.c_int),
+                                     ctypes.POINTER(ctypes.c_float)]
+    lib.lks_batch_stats.argtypes = [P, ctypes.POINTER(ctypes.c_longlong)]
+    lib.lks_batch_last_error.argtypes = [P]
+    lib.lks_batch_last_error.restype = ctypes.c_char_p
+    lib.lks_batch_destroy.argtypes = [P]
+    lib.lks_batch_destroy.restype = None
+    for name in ("lks_batch_create", "lks_batch_set_options", "lks_batch_forward",
+                 "lks_batch_adjoint", "lks_batch_tuning", "lks_batch_stats"):
+        getattr(lib, name).restype = ctypes.c_int
     for name in ("lks_create", "lks_set_design", "lks_set_motion", "lks_set_initial_state",
                  "lks_forward", "lks_adjoint", "lks_get_state", "lks_transfer", "lks_get_stats",
                  "lks_set_timing", "lks_read_timing"):
@@ -200,6 +231,39 @@ class Solver:
             g = np.ascontiguousarray(np.asarray(gamma, dtype=np.float64))
             self._check(self.lib.lks_set_design(self.ctx, g.ctypes.data_as(ctypes.c_void_p), 0))
 
+    def set_filter(self, R: float, beta: float = 1.0, eta: float = 0.5) -> None:
+        """Density filter + Heaviside projection in front of the solver (R = 0: off)."""
+        self._check(self.lib.lks_set_filter(self.ctx, R, beta, eta))
+
+    def volume(self, vmax: float):
+        """(G, dG/dgamma) of the volume constraint on the current design."""
+        G = ctypes.c_double(0.0)
+        dG = np.zeros(self.design_shape, dtype=np.float64)
+        self._check(self.lib.lks_volume(self.ctx, vmax, ctypes.byref(G),
+                                        dG.ctypes.data_as(ctypes.c_void_p), 0))
+        return G.value, dG
+
+    def set_static(self, kappa_s=None) -> None:
+        """Static solid field (nz, ny, nx) of Brinkman coefficients, or None to remove it."""
+        if kappa_s is None:
+            self._check(self.lib.lks_set_static(self.ctx, None))
+        else:
+            k = np.ascontiguousarray(np.asarray(kappa_s, dtype=np.float64))
+            assert k.size == self.state_shape[1] * self.state_shape[2] * self.state_shape[3]
+            self._check(self.lib.lks_set_static(self.ctx, _dptr(k)))
+
+    def warm_start(self) -> None:
+        """Initial state := final state of the last forward run."""
+        self._check(self.lib.lks_warm_start(self.ctx))
+
+    def set_adjoint_start(self, warm: bool) -> None:
+        self._check(self.lib.lks_set_adjoint_start(self.ctx, int(warm)))
+
+    def get_adjoint_state(self) -> np.ndarray:
+        s = np.zeros(self.state_shape, dtype=np.float64)
+        self._check(self.lib.lks_get_adjoint_state(self.ctx, _dptr(s)))
+        return s
+
     def set_motion(self, rows) -> None:
         r = np.ascontiguousarray(np.asarray(rows, dtype=np.float64).reshape(-1, 8))
         m = LksMotion(r.shape[0], _dptr(r))
@@ -252,6 +316,11 @@ class Solver:
     def fused(self) -> bool:
         return bool(self.lib.lks_uses_fused(self.ctx))
 
+    @property
+    def kernels(self) -> str:
+        """'fused3d', 'fused2d' or 'plain': which kernels run this context's steps."""
+        return {1: "fused3d", 2: "fused2d"}.get(self.lib.lks_uses_fused(self.ctx), "plain")
+
     def set_timing(self, stride: int) -> None:
         self._check(self.lib.lks_set_timing(self.ctx, stride))
 
@@ -271,6 +340,92 @@ class Solver:
             self.lib.lks_destroy(self.ctx)
             self.ctx = None
             self.workspace = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def state_bytes(problem, precision: int = FP32) -> int:
+    """Device bytes of one stored state of a problem (one snapshot slot)."""
+    nodes = problem.n[0] * problem.n[1] * problem.n[2]
+    return (nodes * 4 * (8 if precision == FP64 else 4) + 255) // 256 * 256
+
+
+def tile_shapes():
+    """Candidate (tx, ty) tile shapes of the fused 2D kernels."""
+    lib = load()
+    n = lib.lks_batch_tile_shapes(None, 0)
+    a = (ctypes.c_int * (2 * n))()
+    lib.lks_batch_tile_shapes(a, n)
+    return [(a[2 * k], a[2 * k + 1]) for k in range(n)]
+
+
+class Batch:
+    """Many D2Q9 FP32 problems advanced in lock step (lks_batch_*): one launch per phase over
+    all members, runs of steps replayed from CUDA graphs, autotuned tile shapes.
+
+    The members are Solvers built with equal max_steps and `slots` snapshot slots each."""
+
+    def __init__(self, problems, slots: int, stream=None, max_steps: Optional[int] = None):
+        self.lib = load()
+        self.solvers = [Solver(p, FP32, max_steps=max_steps,
+                               ckpt_bytes=slots * state_bytes(p, FP32), stream=stream)
+                        for p in problems]
+        arr = (ctypes.c_void_p * len(self.solvers))(*[s.ctx.value for s in self.solvers])
+        self.b = ctypes.c_void_p()
+        st = self.lib.lks_batch_create(arr, len(self.solvers), ctypes.byref(self.b))
+        if st != 0:
+            raise LksError(st, "lks_batch_create failed")
+
+    def _check(self, st):
+        if st != 0:
+            raise LksError(st, self.lib.lks_batch_last_error(self.b).decode())
+
+    def set_options(self, graphs: bool = True, tile_fwd: int = -1, tile_adj: int = -1) -> None:
+        self._check(self.lib.lks_batch_set_options(self.b, int(graphs), tile_fwd, tile_adj))
+
+    def forward(self, n_steps: Optional[int] = None) -> np.ndarray:
+        n = self.solvers[0].problem.n_steps if n_steps is None else n_steps
+        J = np.zeros(len(self.solvers), dtype=np.float64)
+        for s in self.solvers:
+            s.adjoint_ready = False
+        self._check(self.lib.lks_batch_forward(self.b, n, _dptr(J)))
+        return J
+
+    def adjoint(self, outs=None):
+        """Per member dJ/dgamma: into `outs` (contiguous float64 torch CUDA tensors) or new
+        numpy arrays."""
+        B = len(self.solvers)
+        if outs is not None:
+            ptrs = (ctypes.c_void_p * B)(*[o.data_ptr() for o in outs])
+            self._check(self.lib.lks_batch_adjoint(self.b, ptrs, 1))
+            return outs
+        gs = [np.zeros(s.design_shape, dtype=np.float64) for s in self.solvers]
+        ptrs = (ctypes.c_void_p * B)(*[g.ctypes.data for g in gs])
+        self._check(self.lib.lks_batch_adjoint(self.b, ptrs, 0))
+        return gs
+
+    def tuning(self):
+        n = len(tile_shapes())
+        ch = (ctypes.c_int * 2)()
+        ms = (ctypes.c_float * (2 * n))()
+        self._check(self.lib.lks_batch_tuning(self.b, ch, ms))
+        return {"step": ch[0], "adjoint": ch[1], "step_ms": list(ms[:n]), "adjoint_ms": list(ms[n:])}
+
+    def stats(self):
+        a = (ctypes.c_longlong * 3)()
+        self._check(self.lib.lks_batch_stats(self.b, a))
+        return {"launches": a[0], "graphs": a[1], "graph_nodes": a[2]}
+
+    def close(self) -> None:
+        if getattr(self, "b", None):
+            self.lib.lks_batch_destroy(self.b)
+            self.b = None
+        for s in getattr(self, "solvers", []):
+            s.close()
 
     def __del__(self):
         try:

@@ -200,14 +200,23 @@ def test_fused_fp32_step_matches_plain_fp32_and_oracle(L, name):
     assert rel_l2(gf, go) < 1e-4
 
 
-def test_fp64_and_2d_use_plain_kernels(L):
+def test_kernel_choice_per_context(L):
     w = CASES["small3d_J2"]()
     s = L.Solver(w.problem, L.FP64)
-    assert not s.fused
+    assert s.kernels == "plain"
+    s.close()
+    s = L.Solver(w.problem, L.FP32)
+    assert s.kernels == "fused3d"
     s.close()
     w2 = CASES["small2d_J1"]()
     s = L.Solver(w2.problem, L.FP32)
-    assert not s.fused
+    assert s.kernels == "fused2d"
+    s.close()
+    s = L.Solver(w2.problem, L.FP64)
+    assert s.kernels == "plain"
+    s.close()
+    s = L.Solver(w2.problem, L.FP32, flags=L.FLAG_PAPER_ALKS)
+    assert s.kernels == "plain"
     s.close()
 
 
