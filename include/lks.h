@@ -246,9 +246,10 @@ typedef struct lks_batch lks_batch;
  * at every call.  LKS_ERR_NOMEM if that fails. */
 lks_status lks_batch_create(lks_ctx* const* ctxs, int n, lks_batch** out);
 
-/* use_graphs: 1 (default) capture and replay runs of steps, 0 launch directly.  tile_fwd,
- * tile_adj: index into lks_batch_tile_shapes for the fused step / adjoint kernel, or -1
- * (default) to autotune at the next forward.  LKS_ERR_ARG on an index out of range. */
+/* use_graphs: 1 (default) capture and replay runs of steps, 0 launch directly.  tile_fwd:
+ * configuration of the fused step kernel (0..4 tiles, 5..8 row-marching strips; see
+ * lks_batch_tile_shapes); tile_adj: configuration of the fused adjoint kernel (0..4 tiles);
+ * -1 (default) autotunes at the next forward.  LKS_ERR_ARG on an index out of range. */
 lks_status lks_batch_set_options(lks_batch* b, int use_graphs, int tile_fwd, int tile_adj);
 
 /* lks_forward for every member: J_out (host, n doubles, may be NULL) receives each member's
@@ -261,12 +262,13 @@ lks_status lks_batch_forward(lks_batch* b, int n_steps, double* J_out);
  * forward on every member. */
 lks_status lks_batch_adjoint(lks_batch* b, double* const* dJdgamma, int on_device);
 
-/* The candidate tile shapes as (tx, ty) pairs; returns their number (writes <= cap pairs) or
- * -1 on bad arguments.  Host only. */
+/* The work-unit extent (tx, ty) of every step configuration (the adjoint uses the first
+ * five); returns their number (writes <= cap pairs) or -1 on bad arguments.  Host only. */
 int lks_batch_tile_shapes(int* txty, int cap);
 
-/* chosen2: tile shape indices in use for [step, adjoint] (-1 before the first forward);
- * ms (may be NULL): 2 x shapes autotune timings in ms per launch, -1 where not timed. */
+/* chosen2: configuration indices in use for [step, adjoint] (-1 before the first forward);
+ * ms (may be NULL): 2 x (number of step configurations) autotune timings in ms per launch,
+ * step then adjoint, -1 where not timed. */
 lks_status lks_batch_tuning(const lks_batch* b, int* chosen2, float* ms);
 
 /* [0] kernels launched by the last forward or adjoint call (graph nodes included), [1] graphs

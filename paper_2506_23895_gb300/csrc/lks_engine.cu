@@ -427,7 +427,22 @@ Motion motion_row(const lks_ctx* c, int n) {
     for (int a = 0; a < 3; ++a) {
         m.xG[a] = r[2 + a];
         m.uG[a] = r[5 + a];
+        m.ugf[a] = (float)m.uG[a];
     }
+    m.ch = (float)m.c;
+    m.cl = (float)(m.c - (double)m.ch);
+    m.sh = (float)m.s;
+    m.sl = (float)(m.s - (double)m.sh);
+    for (int a = 0; a < 2; ++a) {
+        const double fl = std::floor(m.xG[a]);
+        m.xgi[a] = (int)fl;
+        m.xgh[a] = (float)(m.xG[a] - fl);
+        m.xgl[a] = (float)((m.xG[a] - fl) - (double)m.xgh[a]);
+        m.xgf[a] = (float)m.xG[a];
+    }
+    m.cf = (float)m.c;
+    m.sf = (float)m.s;
+    m.omf = (float)m.om;
     return m;
 }
 
@@ -950,6 +965,9 @@ Inst make_inst(const lks_ctx* c) {
     const double h = 1.0 / (double)(c->cfg.win_end - c->cfg.win_begin + 1);
     const Geom& g = c->g;
     I.hwin = h;
+    I.Af = (float)g.A;
+    I.bf[0] = (float)g.body[0];
+    I.bf[1] = (float)g.body[1];
     I.src_r = g.okind == 0 ? (float)(-h / (3.0 * g.ocount)) : 0.f;
     I.src_x = g.okind == 0 ? 0.f : (float)(-h * g.odir[0] / g.ocount);
     I.src_y = g.okind == 0 ? 0.f : (float)(-h * g.odir[1] / g.ocount);
@@ -1100,7 +1118,10 @@ lks_status lks_create(const lks_config* cfg, void* workspace, size_t ws_bytes, l
     d.L[0] = cfg->lx;
     d.L[1] = cfg->lx > 0 ? cfg->ly : 0;
     d.L[2] = cfg->lx > 0 ? (cfg->dim == 3 ? cfg->lz : 1) : 0;
-    for (int a = 0; a < 3; ++a) d.xiG[a] = cfg->xi_G[a];
+    for (int a = 0; a < 3; ++a) {
+        d.xiG[a] = cfg->xi_G[a];
+        d.xiGf[a] = (float)cfg->xi_G[a];
+    }
     d.nd = (long long)d.L[0] * d.L[1] * d.L[2];
     d.ncol = (long long)d.L[0] * d.L[1];
 
@@ -1644,7 +1665,9 @@ lks_status batch_prepare(lks_batch* b, int n_steps) {
             BCU(cudaEventCreate(&e0));
             BCU(cudaEventCreate(&e1));
             int best = 0;
-            for (int k = 0; k < kTileCfgs; ++k) {
+            const int ncfg = w == 0 ? kTileCfgs : kAdjCfgs;
+            for (int k = 0; k < kTileCfgs; ++k) b->tune_ms[w][k] = -1.f;
+            for (int k = 0; k < ncfg; ++k) {
                 auto run = [&]() -> cudaError_t {
                     return w == 0 ? launch_t_step2d(b->plan, k, BUF_INIT, BUF_S1, b->st)
                                   : launch_t_adj2d(b->plan, k, 1, BUF_LAM0, BUF_LAM1, BUF_INIT,
@@ -1741,7 +1764,7 @@ lks_status lks_batch_create(lks_ctx* const* ctxs, int n, lks_batch** out) {
 
 lks_status lks_batch_set_options(lks_batch* b, int use_graphs, int tile_fwd, int tile_adj) {
     if (!b) return LKS_ERR_ARG;
-    if (tile_fwd < -1 || tile_fwd >= kTileCfgs || tile_adj < -1 || tile_adj >= kTileCfgs)
+    if (tile_fwd < -1 || tile_fwd >= kTileCfgs || tile_adj < -1 || tile_adj >= kAdjCfgs)
         return bfail(b, LKS_ERR_ARG, "tile shape index out of range");
     b->use_graphs = use_graphs != 0;
     b->tile_req[0] = tile_fwd;
@@ -1818,7 +1841,8 @@ lks_status lks_batch_tuning(const lks_batch* b, int* chosen2, float* ms) {
     if (ms)
         for (int w = 0; w < 2; ++w)
             for (int k = 0; k < kTileCfgs; ++k)
-                ms[w * kTileCfgs + k] = (b->tile_req[w] < 0 && b->tile[w] >= 0) ? b->tune_ms[w][k] : -1.f;
+                ms[w * kTileCfgs + k] =
+                    (b->tile_req[w] < 0 && b->tile[w] >= 0) ? b->tune_ms[w][k] : -1.f;
     return LKS_OK;
 }
 

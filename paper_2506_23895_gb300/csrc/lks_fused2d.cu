@@ -178,24 +178,40 @@ __device__ __forceinline__ void load_tile(const Geom& g, const float4* __restric
     }
 }
 
-// First derivative of the velocity along one axis at a node whose record sits at S[s]
-// (neighbours at +-step): central, or the second-order one-sided difference on a
+// The arithmetic of the helpers below is written with explicitly rounded operations
+// (__fmaf_rn, __fmul_rn, __fadd_rn, __fsub_rn), which the compiler neither contracts nor
+// reorders: the tile and the row-marching forward kernels then compute bitwise the same state.
+#define FMA_ __fmaf_rn
+#define MUL_ __fmul_rn
+#define ADD_ __fadd_rn
+#define SUB_ __fsub_rn
+
+// First derivative of the velocity along one axis from a node's record v and its neighbours at
+// +-1 (p1, m1) and +-2 (p2, m2): central, or the second-order one-sided difference on a
 // non-periodic boundary node (side -1: low face, +1: high face).
+__device__ __forceinline__ void dvel_v(int side, const float4& v, const float4& p1,
+                                       const float4& m1, const float4& p2, const float4& m2,
+                                       float& dux, float& duy) {
+    if (side == 0) {
+        dux = FMA_(0.5f, p1.y, MUL_(-0.5f, m1.y));
+        duy = FMA_(0.5f, p1.z, MUL_(-0.5f, m1.z));
+    } else if (side < 0) {
+        dux = FMA_(-1.5f, v.y, FMA_(2.f, p1.y, MUL_(-0.5f, p2.y)));
+        duy = FMA_(-1.5f, v.z, FMA_(2.f, p1.z, MUL_(-0.5f, p2.z)));
+    } else {
+        dux = FMA_(1.5f, v.y, FMA_(-2.f, m1.y, MUL_(0.5f, m2.y)));
+        duy = FMA_(1.5f, v.z, FMA_(-2.f, m1.z, MUL_(0.5f, m2.z)));
+    }
+}
+
+// The same at the node whose record sits at S[s] (neighbours at +-step); reads only the
+// values the side uses.
 __device__ __forceinline__ void dvel(const float4* S, int s, int step, int side, float& dux,
                                      float& duy) {
-    if (side == 0) {
-        const float4 p = S[s + step], m = S[s - step];
-        dux = 0.5f * p.y - 0.5f * m.y;
-        duy = 0.5f * p.z - 0.5f * m.z;
-    } else if (side < 0) {
-        const float4 v = S[s], p1 = S[s + step], p2 = S[s + 2 * step];
-        dux = -1.5f * v.y + 2.f * p1.y - 0.5f * p2.y;
-        duy = -1.5f * v.z + 2.f * p1.z - 0.5f * p2.z;
-    } else {
-        const float4 v = S[s], m1 = S[s - step], m2 = S[s - 2 * step];
-        dux = 1.5f * v.y - 2.f * m1.y + 0.5f * m2.y;
-        duy = 1.5f * v.z - 2.f * m1.z + 0.5f * m2.z;
-    }
+    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (side == 0) dvel_v(0, z, S[s + step], S[s - step], z, z, dux, duy);
+    else if (side < 0) dvel_v(-1, S[s], S[s + step], z, S[s + 2 * step], z, dux, duy);
+    else dvel_v(1, S[s], z, S[s - step], z, S[s - 2 * step], dux, duy);
 }
 
 __device__ __forceinline__ int face_side(int c, int n, int periodic) {
@@ -211,28 +227,70 @@ __device__ __forceinline__ bool interior_tile(const Geom& g, int x0, int y0) {
     return x0 - 3 >= 0 && x0 + TX + 2 <= g.n[0] - 1 && y0 - 3 >= 0 && y0 + TY + 2 <= g.n[1] - 1;
 }
 
-// f^eq of the eight moving directions at the node whose record is S[s], into F planes at k.
-template <int HX, int FN>
-__device__ __forceinline__ void feq8(const float4* S, int s, float* F, int k, float A,
-                                     float gxx, float gyx, float gxy, float gyy) {
+// f^eq of the eight moving directions (D2Q9 order 1..8) at a node with record v and velocity
+// gradient g_ab = d u_a / d x_b: w_i (rho - rho0 - 1.5 u^2 + 4.5 (c.u)^2 + A c.S.c + 3 c.u),
+// opposite directions sharing their symmetric part.
+__device__ __forceinline__ void feq8_v(const float4& v, float A, float gxx, float gyx, float gxy,
+                                       float gyy, float f[8]) {
     constexpr float w1 = 1.f / 9.f, w2 = 1.f / 36.f;
-    const float4 v = S[s];
-    const float uu = v.y * v.y + v.z * v.z;
-    const float base = v.x - 1.5f * uu;
-    const float ax = A * (2.f * gxx), ay = A * (2.f * gyy);
-    const float sd = 2.f * gxx + 2.f * gyy, so = 2.f * (gxy + gyx);
-    const float ad = A * (sd + so), ae = A * (sd - so);
     const float ux = v.y, uy = v.z;
-    const float cpp = ux + uy, cmp = uy - ux;
-    float* Fk = F + k;
-    Fk[0 * FN] = w1 * (base + 3.f * ux + 4.5f * ux * ux + ax);
-    Fk[1 * FN] = w1 * (base + 3.f * uy + 4.5f * uy * uy + ay);
-    Fk[2 * FN] = w1 * (base - 3.f * ux + 4.5f * ux * ux + ax);
-    Fk[3 * FN] = w1 * (base - 3.f * uy + 4.5f * uy * uy + ay);
-    Fk[4 * FN] = w2 * (base + 3.f * cpp + 4.5f * cpp * cpp + ad);
-    Fk[5 * FN] = w2 * (base + 3.f * cmp + 4.5f * cmp * cmp + ae);
-    Fk[6 * FN] = w2 * (base - 3.f * cpp + 4.5f * cpp * cpp + ad);
-    Fk[7 * FN] = w2 * (base - 3.f * cmp + 4.5f * cmp * cmp + ae);
+    const float base = FMA_(-1.5f, FMA_(ux, ux, MUL_(uy, uy)), v.x);
+    const float ax = MUL_(A, MUL_(2.f, gxx)), ay = MUL_(A, MUL_(2.f, gyy));
+    const float sd = ADD_(MUL_(2.f, gxx), MUL_(2.f, gyy)), so = MUL_(2.f, ADD_(gxy, gyx));
+    const float ad = MUL_(A, ADD_(sd, so)), ae = MUL_(A, SUB_(sd, so));
+    const float cpp = ADD_(ux, uy), cmp = SUB_(uy, ux);
+    const float sx = ADD_(FMA_(MUL_(4.5f, ux), ux, base), ax);
+    const float sy = ADD_(FMA_(MUL_(4.5f, uy), uy, base), ay);
+    const float spp = ADD_(FMA_(MUL_(4.5f, cpp), cpp, base), ad);
+    const float smp = ADD_(FMA_(MUL_(4.5f, cmp), cmp, base), ae);
+    f[0] = MUL_(w1, FMA_(3.f, ux, sx));
+    f[1] = MUL_(w1, FMA_(3.f, uy, sy));
+    f[2] = MUL_(w1, FMA_(-3.f, ux, sx));
+    f[3] = MUL_(w1, FMA_(-3.f, uy, sy));
+    f[4] = MUL_(w2, FMA_(3.f, cpp, spp));
+    f[5] = MUL_(w2, FMA_(3.f, cmp, smp));
+    f[6] = MUL_(w2, FMA_(-3.f, cpp, spp));
+    f[7] = MUL_(w2, FMA_(-3.f, cmp, smp));
+}
+
+// Rest direction: f_0 = w0 (rho - rho0 - 1.5 u^2).
+__device__ __forceinline__ float feq0_v(const float4& v) {
+    constexpr float w0 = 4.f / 9.f;
+    return MUL_(w0, FMA_(-1.5f, FMA_(v.y, v.y, MUL_(v.z, v.z)), v.x));
+}
+
+// Output node from its nine gathered values: rho* = sum f_i, u* = sum c_i f_i (Eqs. rho, u),
+// the body force and the Brinkman update (Eq. u_ex_2) with kappa, u_S (ks, zero outside the
+// footprint box) and a static solid's kappa_s.
+__device__ __forceinline__ V4<float> gather_out(float f0, float f1, float f2, float f3, float f4,
+                                                float f5, float f6, float f7, float f8,
+                                                const float4& ks, float kst, float bfx,
+                                                float bfy) {
+    V4<float> o;
+    o.r = ADD_(ADD_(ADD_(ADD_(f0, f1), ADD_(f2, f3)), ADD_(ADD_(f4, f5), ADD_(f6, f7))), f8);
+    const float usx = ADD_(ADD_(ADD_(SUB_(f1, f3), SUB_(f5, f6)), SUB_(f8, f7)), bfx);
+    const float usy = ADD_(SUB_(ADD_(SUB_(f2, f4), ADD_(f5, f6)), ADD_(f7, f8)), bfy);
+    if (ks.x != 0.f || ks.y != 0.f || ks.z != 0.f) {
+        const float inv = __fdiv_rn(1.f, ADD_(ADD_(1.f, ks.x), kst));
+        o.x = MUL_(FMA_(ks.x, ks.y, usx), inv);
+        o.y = MUL_(FMA_(ks.x, ks.z, usy), inv);
+    } else if (kst != 0.f) {
+        const float inv = __fdiv_rn(1.f, ADD_(1.f, kst));
+        o.x = MUL_(usx, inv);
+        o.y = MUL_(usy, inv);
+    } else {
+        o.x = usx;
+        o.y = usy;
+    }
+    o.z = 0.f;
+    return o;
+}
+
+// kappa, u_S at node (x, y) of the footprint box, else zero.
+__device__ __forceinline__ float4 kus_at(const Inst& I, int x, int y) {
+    long long bi;
+    return in_box(I.g, x, y, 0, bi) ? __ldg((const float4*)I.kus + bi)
+                                    : make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
 // One tile of the forward step.  EDGE: the general path (wraps, grid edges, boundary nodes).
@@ -240,7 +298,6 @@ template <int TX, int TY, bool EDGE>
 __device__ __forceinline__ void step_tile(const Inst& I, int x0, int y0, int src, int dst,
                                           float4* S, float* F) {
     constexpr int HX = TX + 4, FX = TX + 2, FY = TY + 2, FN = FX * FY;
-    constexpr float w0 = 4.f / 9.f;
     const Geom& g = I.g;
     const int n0 = g.n[0], n1 = g.n[1];
     const float4* sp = (const float4*)I.bufs[src];
@@ -254,7 +311,7 @@ __device__ __forceinline__ void step_tile(const Inst& I, int x0, int y0, int src
         }
     }
     __syncthreads();
-    const float A = (float)g.A, bfx = (float)g.body[0], bfy = (float)g.body[1];
+    const float A = I.Af, bfx = I.bf[0], bfy = I.bf[1];
     // f^eq of every direction at the tile and its one-cell rim
     for (int k = threadIdx.x; k < FN; k += NT) {
         const int fy = k / FX, fx = k - fy * FX;
@@ -272,7 +329,10 @@ __device__ __forceinline__ void step_tile(const Inst& I, int x0, int y0, int src
             dvel(S, s, 1, 0, gxx, gyx);
             dvel(S, s, HX, 0, gxy, gyy);
         }
-        feq8<HX, FN>(S, s, F, k, A, gxx, gyx, gxy, gyy);
+        float fv[8];
+        feq8_v(S[s], A, gxx, gyx, gxy, gyy, fv);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) F[q * FN + k] = fv[q];
     }
     __syncthreads();
     // gather rho* = sum f_i(x - c_i), u* = sum c_i f_i(x - c_i); Brinkman update; BCs
@@ -282,8 +342,7 @@ __device__ __forceinline__ void step_tile(const Inst& I, int x0, int y0, int src
         const int x = x0 + tx, y = y0 + ty;
         if (EDGE && (x < 0 || x >= n0 || y < 0 || y >= n1 || is_boundary(g, x, y, 0))) continue;
         const int f = (ty + 1) * FX + tx + 1;
-        const float4 v = S[(ty + 2) * HX + tx + 2];
-        const float f0 = w0 * (v.x - 1.5f * (v.y * v.y + v.z * v.z));
+        const float f0 = feq0_v(S[(ty + 2) * HX + tx + 2]);
         const float f1 = F[0 * FN + f - 1];        // from x - (1, 0)
         const float f2 = F[1 * FN + f - FX];       // from x - (0, 1)
         const float f3 = F[2 * FN + f + 1];        // from x + (1, 0)
@@ -292,29 +351,10 @@ __device__ __forceinline__ void step_tile(const Inst& I, int x0, int y0, int src
         const float f6 = F[5 * FN + f - FX + 1];   // from x - (-1, 1)
         const float f7 = F[6 * FN + f + FX + 1];   // from x + (1, 1)
         const float f8 = F[7 * FN + f + FX - 1];   // from x - (1, -1)
-        V4<float> o;
-        o.r = f0 + f1 + f2 + f3 + f4 + f5 + f6 + f7 + f8;
-        float usx = (f1 - f3) + (f5 - f6) + (f8 - f7);
-        float usy = (f2 - f4) + (f5 + f6) - (f7 + f8);
-        usx += bfx;
-        usy += bfy;
         const long long m = (long long)y * n0 + x;
-        long long bi;
         const float kst = g.ks ? ((const float*)g.ks)[m] : 0.f;
-        if (in_box(g, x, y, 0, bi)) {
-            const V4<float> ks = I.kus[bi];
-            const float inv = 1.f / (1.f + ks.r + kst);
-            o.x = (usx + ks.r * ks.x) * inv;
-            o.y = (usy + ks.r * ks.y) * inv;
-        } else if (kst != 0.f) {
-            const float inv = 1.f / (1.f + kst);
-            o.x = usx * inv;
-            o.y = usy * inv;
-        } else {
-            o.x = usx;
-            o.y = usy;
-        }
-        o.z = 0.f;
+        const V4<float> o =
+            gather_out(f0, f1, f2, f3, f4, f5, f6, f7, f8, kus_at(I, x, y), kst, bfx, bfy);
         out[m] = o;
         if (EDGE) write_bc_from(g, x, y, 0, o, out);
     }
@@ -339,6 +379,145 @@ __global__ void __launch_bounds__(NT) k_t_step2d(Plan p, const int* __restrict__
             step_tile<TX, TY, false>(sI, x0, y0, src, dst, S, F);
         else
             step_tile<TX, TY, true>(sI, x0, y0, src, dst, S, F);
+    }
+}
+
+// cp.async: 16-byte copies global -> shared (src_bytes 0 fills zeros), commit, wait.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, int src_bytes) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src),
+                 "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait1() {
+    asm volatile("cp.async.wait_group 1;" ::: "memory");
+}
+
+// ---------------------------------------------------------------- row-marching forward step
+// A block owns a strip of SW = NTH - 2 output columns and a chunk of YC output rows and marches
+// up the rows.  State rows stream through a six-row cp.async ring two rows ahead of use; per
+// F-row f every thread evaluates f^eq at column x0 - 1 + t (the strip and one rim column on
+// each side: 2 / SW extra work where a tile recomputes its whole rim), the six directions that
+// leave the column go through shared memory, and each output node collects its nine values
+// over three consecutive F-rows in registers.  With the helpers above the values are those of
+// the tile kernel, bit for bit.
+template <int NTH, int YC>
+__global__ void __launch_bounds__(NTH) k_t_step2d_rows(Plan p, const int* __restrict__ pre,
+                                                        int total, int src, int dst) {
+    constexpr int SW = NTH - 2, RW = NTH + 2, NR = 6;
+    __shared__ float4 R[NR][RW];     // state rows, columns x0 - 2 .. x0 + SW + 1
+    __shared__ float Fs[6][NTH];     // f_1, f_3, f_5, f_6, f_7, f_8 of the current F-row
+    __shared__ Inst sI;
+    int cur = -1;
+    const int t = threadIdx.x;
+    for (int u = blockIdx.x; u < total; u += gridDim.x) {
+        const int i = find_inst(pre, p.count, u);
+        stage_inst(p, i, cur, sI);
+        const Geom& g = sI.g;
+        const int n0 = g.n[0], n1 = g.n[1], p0 = g.periodic[0], p1 = g.periodic[1];
+        const int ns = tile_count(n0, SW, p0);
+        const int loc = u - pre[i];
+        const int kc = loc / ns, kx = loc - kc * ns;
+        const int x0 = kx * SW - tile_origin(n0, SW, p0);
+        const int y0 = kc * YC - tile_origin(n1, YC, p1), y1 = y0 + YC;
+        const float4* sp = (const float4*)sI.bufs[src];
+        V4<float>* out = (V4<float>*)sI.bufs[dst];
+        const float A = sI.Af, bfx = sI.bf[0], bfy = sI.bf[1];
+        auto slot = [](int r) { return ((r % NR) + NR) % NR; };
+        auto issue_row = [&](int r) {   // state row r (unwrapped index) into its ring slot
+            float4* row = R[slot(r)];
+            int gy = r;
+            bool rin = true;
+            if (p1) gy = wrap_any(gy, n1);
+            else rin = gy >= 0 && gy < n1;
+            for (int k = t; k < RW; k += NTH) {
+                int gx = x0 - 2 + k;
+                bool in = rin;
+                if (p0) gx = wrap_any(gx, n0);
+                else in = in && gx >= 0 && gx < n0;
+                cp_async16(row + k, in ? sp + (long long)gy * n0 + gx : sp, in ? 16 : 0);
+            }
+        };
+        __syncthreads();   // the ring and Fs of the previous unit are no longer read
+        for (int r = y0 - 3; r <= y0 + 1; ++r) issue_row(r);
+        cp_async_commit();
+        // this thread's f^eq column and, for 1 <= t <= SW, output column
+        const int xr = x0 - 1 + t;
+        int xc = xr;
+        bool cin = true;
+        if (p0) xc = wrap_any(xc, n0);
+        else cin = xc >= 0 && xc < n0;
+        const int sx = face_side(xc, n0, p0);
+        const bool ocol = t >= 1 && t <= SW &&
+                          (p0 ? (xr >= 0 && xr < n0) : (xr >= 1 && xr <= n0 - 2));
+        float a2 = 0.f, a5 = 0.f, a6 = 0.f;   // f2, f5, f6 collected for the next row
+        float b2 = 0.f, b5 = 0.f, b6 = 0.f;   // the same for the row after that
+        float c0 = 0.f, c1 = 0.f, c3 = 0.f;   // f0, f1, f3 collected for the next row
+        for (int f = y0 - 1; f <= y1; ++f) {
+            if (f + 3 <= y1 + 2) issue_row(f + 3);
+            cp_async_commit();
+            cp_async_wait1();
+            __syncthreads();
+            float fv[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            float f0 = 0.f;
+            int fy = f;
+            bool rin = true;
+            if (p1) fy = wrap_any(fy, n1);
+            else rin = fy >= 0 && fy < n1;
+            if (cin && rin) {   // f^eq at (xc, f)
+                const float4* r0 = R[slot(f)];
+                const float4* rp = R[slot(f + 1)];
+                const float4* rm = R[slot(f - 1)];
+                const int c = t + 1;
+                const float4 v = r0[c], z = make_float4(0.f, 0.f, 0.f, 0.f);
+                float gxx, gyx, gxy, gyy;
+                if (sx == 0) dvel_v(0, z, r0[c + 1], r0[c - 1], z, z, gxx, gyx);
+                else if (sx < 0) dvel_v(-1, v, r0[c + 1], z, r0[c + 2], z, gxx, gyx);
+                else dvel_v(1, v, z, r0[c - 1], z, r0[c - 2], gxx, gyx);
+                const int sy = face_side(fy, n1, p1);
+                if (sy == 0) dvel_v(0, z, rp[c], rm[c], z, z, gxy, gyy);
+                else if (sy < 0) dvel_v(-1, v, rp[c], z, R[slot(f + 2)][c], z, gxy, gyy);
+                else dvel_v(1, v, z, rm[c], z, R[slot(f - 2)][c], gxy, gyy);
+                feq8_v(v, A, gxx, gyx, gxy, gyy, fv);
+                f0 = feq0_v(v);
+            }
+            Fs[0][t] = fv[0];   // f_1
+            Fs[1][t] = fv[2];   // f_3
+            Fs[2][t] = fv[4];   // f_5
+            Fs[3][t] = fv[5];   // f_6
+            Fs[4][t] = fv[6];   // f_7
+            Fs[5][t] = fv[7];   // f_8
+            __syncthreads();
+            if (t >= 1 && t <= SW) {
+                // values the nodes (x, f - 1), (x, f), (x, f + 1) receive from F-row f
+                const float g4 = fv[3], g7 = Fs[4][t + 1], g8 = Fs[5][t - 1];
+                const float g1 = Fs[0][t - 1], g3 = Fs[1][t + 1];
+                const float g2 = fv[1], g5 = Fs[2][t - 1], g6 = Fs[3][t + 1];
+                const int y = f - 1;   // output row completed by this F-row
+                bool orow = y >= y0 && y < y1;
+                orow = orow && (p1 ? (y >= 0 && y < n1) : (y >= 1 && y <= n1 - 2));
+                if (ocol && orow) {
+                    const long long m = (long long)y * n0 + xc;
+                    const float kst = g.ks ? ((const float*)g.ks)[m] : 0.f;
+                    const V4<float> o = gather_out(c0, c1, b2, c3, g4, b5, b6, g7, g8,
+                                                   kus_at(sI, xc, y), kst, bfx, bfy);
+                    out[m] = o;
+                    write_bc_from(g, xc, y, 0, o, out);
+                }
+                b2 = a2;
+                b5 = a5;
+                b6 = a6;
+                a2 = g2;
+                a5 = g5;
+                a6 = g6;
+                c0 = f0;
+                c1 = g1;
+                c3 = g3;
+            }
+        }
     }
 }
 
@@ -527,6 +706,29 @@ __global__ void __launch_bounds__(NT) k_t_adj2d(Plan p, const int* __restrict__ 
     }
 }
 
+// Row-marching step configurations 5..8: threads per strip and rows per chunk.
+template <int C>
+struct RowCfg {
+    static constexpr int NTH = tile_tx(C) + 2, YC = tile_ty(C);
+};
+
+template <int C>
+int occ_rows() {
+    int b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &b, k_t_step2d_rows<RowCfg<C>::NTH, RowCfg<C>::YC>, RowCfg<C>::NTH, 0);
+    return b;
+}
+
+template <int C>
+cudaError_t rows_cfg(const Plan& p, int src, int dst, cudaStream_t st) {
+    const int unit = U_TILE0 + C;
+    if (p.total[unit] == 0) return cudaSuccess;
+    k_t_step2d_rows<RowCfg<C>::NTH, RowCfg<C>::YC><<<p.grid[unit], RowCfg<C>::NTH, 0, st>>>(
+        p, p.pre + unit * (p.count + 1), p.total[unit], src, dst);
+    return cudaGetLastError();
+}
+
 template <int C>
 struct Cfg {
     static constexpr int TX = tile_tx(C), TY = tile_ty(C);
@@ -595,13 +797,12 @@ void plan_grids(Plan& p) {
     p.grid[U_SHELL] = cap_grid(p.total[U_SHELL], b);
     p.grid[U_INST] = std::max(1, p.count);
     const int os[kTileCfgs] = {occ_step<0>(), occ_step<1>(), occ_step<2>(), occ_step<3>(),
-                               occ_step<4>()};
-    const int oa[kTileCfgs] = {occ_adj<0>(), occ_adj<1>(), occ_adj<2>(), occ_adj<3>(),
-                               occ_adj<4>()};
-    for (int c = 0; c < kTileCfgs; ++c) {
-        p.grid[U_TILE0 + c] = cap_grid(p.total[U_TILE0 + c], os[c]);
-        p.grid[U_COUNT + c] = cap_grid(p.total[U_TILE0 + c], oa[c]);
-    }
+                               occ_step<4>(), occ_rows<5>(),  occ_rows<6>(),  occ_rows<7>(),
+                               occ_rows<8>()};
+    const int oa[kAdjCfgs] = {occ_adj<0>(), occ_adj<1>(), occ_adj<2>(), occ_adj<3>(),
+                              occ_adj<4>()};
+    for (int c = 0; c < kTileCfgs; ++c) p.grid[U_TILE0 + c] = cap_grid(p.total[U_TILE0 + c], os[c]);
+    for (int c = 0; c < kAdjCfgs; ++c) p.grid[U_COUNT + c] = cap_grid(p.total[U_TILE0 + c], oa[c]);
     cudaGetLastError();
 }
 
@@ -624,6 +825,10 @@ cudaError_t launch_t_step2d(const Plan& p, int cfg, int src, int dst, cudaStream
         case 2: return step_cfg<2>(p, src, dst, st);
         case 3: return step_cfg<3>(p, src, dst, st);
         case 4: return step_cfg<4>(p, src, dst, st);
+        case 5: return rows_cfg<5>(p, src, dst, st);
+        case 6: return rows_cfg<6>(p, src, dst, st);
+        case 7: return rows_cfg<7>(p, src, dst, st);
+        case 8: return rows_cfg<8>(p, src, dst, st);
         default: return cudaErrorInvalidValue;
     }
 }

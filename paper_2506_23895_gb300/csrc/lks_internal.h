@@ -44,6 +44,7 @@ struct Geom {
 struct Design {
     int L[3];
     double xiG[3];
+    float xiGf[3];      // the same in single precision
     long long nd;       // design nodes
     long long ncol;     // design columns lx*ly
 };
@@ -51,6 +52,12 @@ struct Design {
 struct Motion {
     double c, s, om;    // cos(theta), sin(theta), omega
     double xG[3], uG[3];
+    // single-precision forms for FP32 kernels: cos and sin as float pairs (hi + lo), x_G split
+    // into an integer and a float-pair fraction, and plain floats
+    float ch, cl, sh, sl;
+    int xgi[2];
+    float xgh[2], xgl[2];
+    float cf, sf, omf, xgf[2], ugf[3];
 };
 
 // Per-step scratch produced by the design-position kernel and consumed by the transfer,

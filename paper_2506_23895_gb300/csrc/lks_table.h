@@ -26,17 +26,24 @@ struct Inst {
     double* gacc;             // dJ/dgamma accumulator
     double* jstep;            // objective per step
     int win_begin, win_end;
+    float Af, bf[2];          // A and the body force in single precision
     double hwin;              // 1 / (window length): the window weight h_n inside the window
     float src_r, src_x, src_y;   // h_n d j / d (rho, ux, uy) at a target node, inside the window
 };
 
-// Tile shapes of the fused kernels (256 threads each); chosen per run by the autotuner.
-constexpr int kTileCfgs = 5;
+// Configurations of the fused kernels, chosen per run by the autotuner.  Step: five tile
+// shapes of 256 threads (0..4) and four row-marching strips (5..8: strips of 62, 126, 126 and
+// 254 columns marching over chunks of 64, 64, 128 and 64 rows).  Adjoint: the five tile shapes
+// (0..4).  tile_tx / tile_ty give the extent of one work unit.
+constexpr int kTileCfgs = 9;
+constexpr int kAdjCfgs = 5;
 __host__ __device__ constexpr int tile_tx(int k) {
-    return k == 0 ? 32 : (k == 1 ? 16 : (k == 2 ? 32 : (k == 3 ? 64 : 64)));
+    return k == 0 ? 32 : (k == 1 ? 16 : (k == 2 ? 32 : (k <= 4 ? 64 :
+           (k == 5 ? 62 : (k == 8 ? 254 : 126)))));
 }
 __host__ __device__ constexpr int tile_ty(int k) {
-    return k == 0 ? 8 : (k == 1 ? 16 : (k == 2 ? 16 : (k == 3 ? 8 : 16)));
+    return k == 0 ? 8 : (k == 1 ? 16 : (k == 2 ? 16 : (k == 3 ? 8 : (k == 4 ? 16 :
+           (k == 7 ? 128 : 64)))));
 }
 
 // Work-unit kinds: design columns and box nodes in blocks of kUnitThreads, boundary-shell
@@ -49,7 +56,7 @@ struct Plan {
     const int* pre;           // device, [U_COUNT][count + 1]
     int count;
     int total[U_COUNT];
-    int grid[U_COUNT + kTileCfgs];   // persistent grid per kernel (set on the host)
+    int grid[U_COUNT + kAdjCfgs];    // persistent grid per kernel (set on the host)
     const int* nbase;         // device: step index base added to each launch's offset
 };
 

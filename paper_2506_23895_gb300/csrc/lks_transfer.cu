@@ -126,7 +126,7 @@ __global__ void k_tap_lists(Design d, Geom g, Motion m, TransferScratch ts) {
             const long long k = (long long)j * d.L[0] + i;
             const T rx = (T)(x - ts.col_base[2 * k]) - frac[2 * k];
             const T ry = (T)(y - ts.col_base[2 * k + 1]) - frac[2 * k + 1];
-            if (!(fabs((double)rx) < 2.0 && fabs((double)ry) < 2.0)) continue;
+            if (!(fabs(rx) < (T)2 && fabs(ry) < (T)2)) continue;   // exact in T
             const T W = peskin(rx) * peskin(ry);
             if (W == (T)0) continue;
             if (cnt == kMaxTaps) {
@@ -184,12 +184,16 @@ __global__ void k_fill(Design d, Geom g, Motion m, TransferScratch ts, const T* 
         kap += zw[t] * k2[col * d.L[2] + zeta];
     }
     const T* cm = (const T*)ts.col_m + 3 * col;
-    const T om = (T)m.om, c = (T)m.c, s = (T)m.s;
+    // single-precision motion fields for T = float (the same roundings as converting here)
+    const bool f32 = sizeof(T) == 4;
+    const T om = f32 ? (T)m.omf : (T)m.om, c = f32 ? (T)m.cf : (T)m.c, s = f32 ? (T)m.sf : (T)m.s;
+    const T ug0 = f32 ? (T)m.ugf[0] : (T)m.uG[0], ug1 = f32 ? (T)m.ugf[1] : (T)m.uG[1];
+    const T ug2 = f32 ? (T)m.ugf[2] : (T)m.uG[2];
     V4<T> o;
     o.r = kap;
-    o.x = mz * ((-s * cm[1] - c * cm[2]) * om + (T)m.uG[0] * cm[0]);
-    o.y = mz * ((c * cm[1] - s * cm[2]) * om + (T)m.uG[1] * cm[0]);
-    o.z = (g.dim == 3) ? mz * ((T)m.uG[2] * cm[0]) : (T)0;
+    o.x = mz * ((-s * cm[1] - c * cm[2]) * om + ug0 * cm[0]);
+    o.y = mz * ((c * cm[1] - s * cm[2]) * om + ug1 * cm[0]);
+    o.z = (g.dim == 3) ? mz * (ug2 * cm[0]) : (T)0;
     kus[bi] = o;
 }
 

@@ -30,17 +30,43 @@ __device__ __forceinline__ void design_col_pos(const Design& d, const Motion& m,
 // taps of the cosine kernel then follow without further trigonometry: for an analysis node at
 // base + q, q = -1, 0, 1, 2, w = (1 - S)/4, (1 + C)/4, (1 + S)/4, (1 - C)/4 (w(r) =
 // (1 + cos(pi r/2))/4 at r = q - f).
+// x_ref = x_G + a da - b db of one axis in single precision without losing the fraction:
+// Dekker's exact product split (with fma) and Knuth's two-sum carry the rounding errors, so
+// base + frac equals x_ref to about 1e-12 although every operation is FP32 (GB300's FP64 rate is
+// a small fraction of its FP32 rate).  Returns the integer base; frac in [0, 1).
+__device__ __forceinline__ int ref_coord(float ah, float al, float da, float bh, float bl,
+                                         float db, int gi, float gh, float gl, float& frac) {
+    const float p = ah * da, pe = fmaf(ah, da, -p);     // a_hi da = p + pe exactly
+    const float q = bh * db, qe = fmaf(bh, db, -q);     // b_hi db = q + qe exactly
+    const float r = p - q, rb = r - p;
+    const float re = (p - (r - rb)) + (-q - rb);        // p - q = r + re exactly
+    const float t = r + gh, tb = t - r;
+    const float te = (r - (t - tb)) + (gh - tb);        // r + gh = t + te exactly
+    const float lo = ((te + re) + (pe - qe)) + (fmaf(al, da, -bl * db) + gl);
+    float fl = floorf(t);
+    float f = (t - fl) + lo;                            // t - floor(t) is exact
+    if (f < 0.f) {
+        f += 1.f;
+        fl -= 1.f;
+    } else if (f >= 1.f) {
+        f -= 1.f;
+        fl += 1.f;
+    }
+    frac = f;
+    return gi + (int)fl;
+}
+
 __device__ __forceinline__ void design_col_pos_sc(const Design& d, const Motion& m,
                                                   const TransferScratch& ts, long long k) {
     const int i = (int)((unsigned)k % (unsigned)d.L[0]), j = (int)((unsigned)k / (unsigned)d.L[0]);
-    const double dx = i - d.xiG[0], dy = j - d.xiG[1];
-    const double xr = m.c * dx - m.s * dy + m.xG[0];   // Eq. rigid_body_position
-    const double yr = m.s * dx + m.c * dy + m.xG[1];
-    const double bx = floor(xr), by = floor(yr);
-    reinterpret_cast<int2*>(ts.col_base)[k] = make_int2((int)bx, (int)by);
+    const float dx = (float)i - d.xiGf[0], dy = (float)j - d.xiGf[1];
+    float fx, fy;   // Eq. rigid_body_position: x_ref = c dx - s dy + x_G, y_ref = s dx + c dy + y_G
+    const int bx = ref_coord(m.ch, m.cl, dx, m.sh, m.sl, dy, m.xgi[0], m.xgh[0], m.xgl[0], fx);
+    const int by = ref_coord(m.sh, m.sl, dx, -m.ch, -m.cl, dy, m.xgi[1], m.xgh[1], m.xgl[1], fy);
+    reinterpret_cast<int2*>(ts.col_base)[k] = make_int2(bx, by);
     float4 sc;
-    sincospif(0.5f * (float)(xr - bx), &sc.x, &sc.y);
-    sincospif(0.5f * (float)(yr - by), &sc.z, &sc.w);
+    sincospif(0.5f * fx, &sc.x, &sc.y);
+    sincospif(0.5f * fy, &sc.z, &sc.w);
     ts.col_sc[k] = sc;
 }
 
@@ -60,15 +86,15 @@ __device__ __forceinline__ void transfer2d_node(const Design& d, const Geom& g, 
                                                 V4<float>* kus, long long bi) {
     const int x = g.blo[0] + (int)((unsigned)bi % (unsigned)g.bn[0]);
     const int y = g.blo[1] + (int)((unsigned)bi / (unsigned)g.bn[0]);
-    const float c = (float)m.c, s = (float)m.s;
-    const float px = (float)(x - m.xG[0]), py = (float)(y - m.xG[1]);
-    const float ic = c * px + s * py + (float)d.xiG[0];
-    const float jc = -s * px + c * py + (float)d.xiG[1];
+    const float c = m.cf, s = m.sf;
+    const float px = (float)x - m.xgf[0], py = (float)y - m.xgf[1];
+    const float ic = c * px + s * py + d.xiGf[0];
+    const float jc = -s * px + c * py + d.xiGf[1];
     const float R = 2.f * (fabsf(c) + fabsf(s)) + 0.01f;
     const int i0 = max(0, (int)ceilf(ic - R)), i1 = min(d.L[0] - 1, (int)floorf(ic + R));
     const int j0 = max(0, (int)ceilf(jc - R)), j1 = min(d.L[1] - 1, (int)floorf(jc + R));
     const int2* base = reinterpret_cast<const int2*>(ts.col_base);
-    const float gx0 = (float)d.xiG[0], gy0 = (float)d.xiG[1];
+    const float gx0 = d.xiGf[0], gy0 = d.xiGf[1];
     float kap = 0.f, m0 = 0.f, m1x = 0.f, m1y = 0.f;
     for (int j = j0; j <= j1; ++j)
         for (int i = i0; i <= i1; ++i) {
@@ -83,11 +109,11 @@ __device__ __forceinline__ void transfer2d_node(const Design& d, const Geom& g, 
             m1x += W * ((float)i - gx0);
             m1y += W * ((float)j - gy0);
         }
-    const float om = (float)m.om;
+    const float om = m.omf;
     V4<float> o;
     o.r = kap;
-    o.x = (-s * m1x - c * m1y) * om + (float)m.uG[0] * m0;
-    o.y = (c * m1x - s * m1y) * om + (float)m.uG[1] * m0;
+    o.x = (-s * m1x - c * m1y) * om + m.ugf[0] * m0;
+    o.y = (c * m1x - s * m1y) * om + m.ugf[1] * m0;
     o.z = 0.f;
     kus[bi] = o;
 }

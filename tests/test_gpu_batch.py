@@ -122,11 +122,13 @@ def test_batch_members_bitwise_equal_single_runs(L, graphs):
 
 
 def test_batch_every_tile_shape_gives_identical_results(L):
+    """Every step configuration (tiles, row-marching strips) and every adjoint tile shape gives
+    bitwise the same results."""
     ws = members(n=4, steps=24, side=(24, 90))
     ref = None
     for k in range(len(L.tile_shapes())):
-        J, gs, info = run_batch(L, ws, 6, tiles=(k, k))
-        assert info["tuning"]["step"] == k and info["tuning"]["adjoint"] == k
+        J, gs, info = run_batch(L, ws, 6, tiles=(k, k % 5))
+        assert info["tuning"]["step"] == k and info["tuning"]["adjoint"] == k % 5
         if ref is None:
             ref = (J, gs)
         else:
@@ -140,7 +142,7 @@ def test_batch_matches_oracle_and_autotunes(L):
     J, gs, info = run_batch(L, ws, 5)
     t = info["tuning"]
     assert 0 <= t["step"] < len(L.tile_shapes()) and 0 <= t["adjoint"] < len(L.tile_shapes())
-    assert min(t["step_ms"]) > 0 and min(t["adjoint_ms"]) > 0
+    assert min(t["step_ms"]) > 0 and min(t["adjoint_ms"][:5]) > 0
     for i, w in enumerate(ws):
         Jo, go = oracle.gradient(w.problem, w.gamma, w.motion)
         assert abs(J[i] - Jo) <= 1e-5 * abs(Jo)
