@@ -52,6 +52,7 @@ class OrcProblem(ctypes.Structure):
         ("obj_dir", ctypes.c_double * 3),
         ("obj_cyl_r", ctypes.c_double), ("obj_cyl_c", ctypes.c_double * 2),
         ("win_begin", ctypes.c_int), ("win_end", ctypes.c_int),
+        ("rot_axis", ctypes.c_double * 3),
     ]
 
 
@@ -96,6 +97,9 @@ def to_struct(p) -> OrcProblem:
     s.obj_cyl_r = p.obj_cyl_r
     s.obj_cyl_c[0], s.obj_cyl_c[1] = p.obj_cyl_c
     s.win_begin, s.win_end = p.win
+    ax = getattr(p, "rot_axis", (0.0, 0.0, 1.0))
+    for a in range(3):
+        s.rot_axis[a] = ax[a]
     return s
 
 

@@ -83,6 +83,7 @@ typedef struct {
     double obj_dir[3];
     double obj_cyl_r, obj_cyl_c[2];
     int win_begin, win_end;
+    double rot_axis[3]; /* 3D rotation axis (unit vector); (0, 0, 1) or all zero: the z axis */
 } orc_problem;
 
 }  // extern "C"
@@ -205,8 +206,16 @@ double kappa_ref_prime(const orc_problem& p, double gamma) {
     return p.kappa_max * p.q * (1.0 + p.q) / (d * d);
 }
 
+// True when a 3D problem rotates about an axis other than z.
+bool general_axis(const orc_problem& p) {
+    const double* a = p.rot_axis;
+    return p.dim == 3 && !(a[0] == 0.0 && a[1] == 0.0 && (a[2] == 0.0 || a[2] == 1.0));
+}
+
 // Position and velocity of design node xi (Eqs. rigid_body_position / rigid_body_velocity).
-// In 3D the rotation is about the z axis, as in the 3D rotor of Sec. 3.3.
+// In 2D the rotation is in the plane; in 3D about the z axis (the 3D rotor of Sec. 3.3) or,
+// for a general unit axis a, by Rodrigues' formula R = cos(th) I + sin(th) [a]x +
+// (1 - cos(th)) a a^T, whose time derivative gives u_ref = omega a x (R (xi - xi_G)) + u_G.
 void rigid_point(const orc_problem& p, const double* mrow, const int xi[3], double xr[3],
                  double ur[3]) {
     double th = mrow[0], om = mrow[1];
@@ -214,6 +223,21 @@ void rigid_point(const orc_problem& p, const double* mrow, const int xi[3], doub
     const double* uG = mrow + 5;
     double dx = xi[0] - p.xi_G[0], dy = xi[1] - p.xi_G[1], dz = xi[2] - p.xi_G[2];
     double c = std::cos(th), s = std::sin(th);
+    if (general_axis(p)) {
+        const double* a = p.rot_axis;
+        const double d[3] = {dx, dy, dz};
+        const double ad = a[0] * dx + a[1] * dy + a[2] * dz;
+        const double axd[3] = {a[1] * dz - a[2] * dy, a[2] * dx - a[0] * dz, a[0] * dy - a[1] * dx};
+        double rd[3];
+        for (int k = 0; k < 3; ++k) rd[k] = c * d[k] + s * axd[k] + (1.0 - c) * a[k] * ad;
+        const double w[3] = {a[1] * rd[2] - a[2] * rd[1], a[2] * rd[0] - a[0] * rd[2],
+                             a[0] * rd[1] - a[1] * rd[0]};
+        for (int k = 0; k < 3; ++k) {
+            xr[k] = rd[k] + xG[k];
+            ur[k] = om * w[k] + uG[k];
+        }
+        return;
+    }
     xr[0] = c * dx - s * dy + xG[0];
     xr[1] = s * dx + c * dy + xG[1];
     ur[0] = (-s * dx - c * dy) * om + uG[0];

@@ -51,6 +51,7 @@ class Problem:
     u_init: Tuple[float, float, float] = (0.0, 0.0, 0.0)
     body_force: Tuple[float, float, float] = (0.0, 0.0, 0.0)
     xi_G: Tuple[float, float, float] = (0.0, 0.0, 0.0)   # rotation centre in design coords
+    rot_axis: Tuple[float, float, float] = (0.0, 0.0, 1.0)   # 3D rotation axis (unit vector)
     obj_kind: int = OBJ_PRESSURE
     obj_box: Tuple[int, int, int, int, int, int] = (0, 0, 0, 0, 0, 0)  # inclusive x0,x1,y0,y1,z0,z1
     obj_dir: Tuple[float, float, float] = (0.0, 0.0, 1.0)
@@ -299,10 +300,18 @@ def small_channel2d(nx: int = 24, ny: int = 20, LD: int = 8, n_steps: int = 40,
     return Workload(p, g, m)
 
 
+def unit(v: Sequence[float]) -> Tuple[float, float, float]:
+    """v / |v| as a tuple (a rotation axis)."""
+    n = math.sqrt(sum(float(a) * float(a) for a in v))
+    return (float(v[0]) / n, float(v[1]) / n, float(v[2]) / n)
+
+
 def small_duct3d(nx: int = 16, ny: int = 15, nz: int = 16, LD: int = 5, n_steps: int = 24,
                  omega: float = 0.03, trans_amp: float = 1.0, seed: int = 12,
-                 obj_kind: int = OBJ_VELOCITY, A: float = 0.45) -> Workload:
-    """A few-thousand-node 3D duct with a design grid rotating about z and translating in y."""
+                 obj_kind: int = OBJ_VELOCITY, A: float = 0.45,
+                 rot_axis: Tuple[float, float, float] = (0.0, 0.0, 1.0)) -> Workload:
+    """A few-thousand-node 3D duct with a design grid rotating about rot_axis (default z) and
+    translating in y."""
     cx, cy, cz = (nx - 1) / 2.0, (ny - 1) / 2.0, (nz - 1) / 2.0
     if obj_kind == OBJ_VELOCITY:
         box = (int(cx) - 2, int(cx) + 2, int(cy) - 2, int(cy) + 2, nz - 4, nz - 3)
@@ -316,7 +325,8 @@ def small_duct3d(nx: int = 16, ny: int = 15, nz: int = 16, LD: int = 5, n_steps:
         u_init=(0.0, 0.0, 0.04), xi_G=((LD - 1) / 2.0,) * 3,
         obj_kind=obj_kind, obj_box=box, obj_dir=(0.0, 0.0, 1.0),
         obj_cyl_r=2.5 if obj_kind == OBJ_VELOCITY else 0.0, obj_cyl_c=(cx, cy),
-        win=(max(1, n_steps // 2), n_steps), n_steps=n_steps, name="small3d")
+        win=(max(1, n_steps // 2), n_steps), n_steps=n_steps, name="small3d",
+        rot_axis=tuple(rot_axis))
     m = motion_table(n_steps, (cx, cy, cz + 0.25), omega=omega, trans_amp=trans_amp,
                      trans_period=max(40.0, n_steps / 1.5), trans_axis=1, theta0=0.2)
     g = make_gamma((LD, LD, LD), 1.0, seed)
