@@ -87,6 +87,10 @@ typedef struct {
                                 fits in 8 GB, else the minimum of a two-level scheme */
     void* stream;            /* cudaStream_t for all work; NULL = legacy default stream */
     int flags;               /* LKS_FLAG_* bits; 0 normally */
+    double rot_axis[3];      /* 3D rotation axis of the design grid, a unit vector; all zero or
+                                (0, 0, 1) is the z axis (the paper's 3D rotor, Sec. 3.3).  Any
+                                other axis uses a cell-list transfer (R(theta) by Rodrigues'
+                                formula).  Ignored in 2D. */
 } lks_config;
 
 /* Run every step on the plain per-node kernels even where the fused FP32 3D step applies. */

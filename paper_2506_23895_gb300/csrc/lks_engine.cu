@@ -134,6 +134,9 @@ struct lks_ctx {
     Plan plan;
     int geo_gen = 0;             // bumped when the footprint box changes
     int tile_fwd = 0, tile_adj = 0;   // tile shapes of the fused 2D kernels
+    bool gaxis = false;          // 3D rotation about an axis other than z
+    double axis[3] = {0.0, 0.0, 1.0};
+    AxisScratch as;
     // design chain: density filter radius (0 = off), projection steepness and threshold
     double fR = 0.0, fbeta = 1.0, feta = 0.5;
     double* gbar = nullptr;      // projected field the solver sees
@@ -180,6 +183,12 @@ lks_status fail(lks_ctx* c, lks_status s, const char* fmt, ...) {
             return fail(c, LKS_ERR_CUDA, "kernel launch: %s", cudaGetErrorString(e_));    \
         ++c->stats[4];                                                                    \
     } while (0)
+
+// True when a 3D configuration rotates about an axis other than z.
+bool general_axis(const lks_config* cfg) {
+    const double* a = cfg->rot_axis;
+    return cfg->dim == 3 && !(a[0] == 0.0 && a[1] == 0.0 && (a[2] == 0.0 || a[2] == 1.0));
+}
 
 bool validate(const lks_config* cfg, std::string& why) {
     if (!cfg) {
@@ -240,6 +249,14 @@ bool validate(const lks_config* cfg, std::string& why) {
         why = "objective window must satisfy 1 <= win_begin <= win_end";
         return false;
     }
+    if (general_axis(cfg)) {
+        const double* a = cfg->rot_axis;
+        const double n2 = a[0] * a[0] + a[1] * a[1] + a[2] * a[2];
+        if (!(std::fabs(n2 - 1.0) < 1e-9)) {
+            why = "rot_axis must be a unit vector";
+            return false;
+        }
+    }
     if (cfg->obj_kind != LKS_OBJ_PRESSURE && cfg->obj_kind != LKS_OBJ_VELOCITY) {
         why = "unknown objective kind";
         return false;
@@ -283,7 +300,7 @@ double count_target(const lks_config* c) {
 }
 
 struct Layout {
-    size_t off[48];
+    size_t off[64];
     size_t total;
     int pool_slots;
     size_t snap;
@@ -293,10 +310,11 @@ enum {
     L_S0, L_S1, L_SINIT, L_L0, L_L1, L_F, L_MU, L_PHI, L_KUS, L_E, L_GAMMA, L_KREF, L_KPRIME,
     L_GACC, L_JSTEP, L_CBASE, L_CFRAC, L_ZTI, L_ZTW, L_TCNT, L_TIDX, L_TW, L_CM, L_DZB, L_DZF,
     L_FLAGS, L_KREFT, L_K2, L_FACE, L_TGT, L_U3, L_MOTION, L_BUFS, L_INST, L_PRE, L_GBAR,
-    L_HP, L_FWS, L_GOUT, L_GTMP, L_SCAL, L_CSC, L_KS, L_SEND, L_LEND, L_POOL,
+    L_HP, L_FWS, L_GOUT, L_GTMP, L_SCAL, L_CSC, L_KS, L_SEND, L_LEND, L_GBASE, L_GFRAC,
+    L_GCNT, L_GIDX, L_POOL,
     L_COUNT
 };
-static_assert(L_COUNT <= 48, "Layout::off holds 48 regions");
+static_assert(L_COUNT <= 64, "Layout::off holds 64 regions");
 
 Layout make_layout(const lks_config* cfg) {
     Layout L;
@@ -356,6 +374,13 @@ Layout make_layout(const lks_config* cfg) {
     sz[L_CSC] = (size_t)std::max(ncol, 1LL) * 16;
     sz[L_KS] = (size_t)nodes * T;
     sz[L_SEND] = sz[L_LEND] = state;
+    {   // general-axis transfer: per design node and per box cell (worst case: every node)
+        const bool ga = general_axis(cfg) && nd > 0;
+        sz[L_GBASE] = ga ? (size_t)nd * 16 : 0;
+        sz[L_GFRAC] = ga ? (size_t)nd * 4 * T : 0;
+        sz[L_GCNT] = ga ? (size_t)nodes * 4 : 0;
+        sz[L_GIDX] = ga ? (size_t)nodes * kCellMax * 4 : 0;
+    }
     sz[L_TGT] = (size_t)std::max(1.0, count_target(cfg)) * 4;
     sz[L_U3] = (cfg->flags & LKS_FLAG_PAPER_ALKS) ? state : 0;
     sz[L_KREFT] = (size_t)std::max(nd, 1LL) * T;
@@ -443,6 +468,27 @@ Motion motion_row(const lks_ctx* c, int n) {
     m.cf = (float)m.c;
     m.sf = (float)m.s;
     m.omf = (float)m.om;
+    // R(theta) about the unit axis a by Rodrigues' formula (the z axis gives the plane rotation)
+    const double* a = c->axis;
+    const double cc = m.c, ss = m.s, oc = 1.0 - cc;
+    if (!c->gaxis) {
+        const double Rz[9] = {cc, -ss, 0.0, ss, cc, 0.0, 0.0, 0.0, 1.0};
+        for (int k = 0; k < 9; ++k) m.R[k] = Rz[k];
+        m.ax[0] = 0.0;
+        m.ax[1] = 0.0;
+        m.ax[2] = 1.0;
+    } else {
+        m.R[0] = cc + oc * a[0] * a[0];
+        m.R[1] = oc * a[0] * a[1] - ss * a[2];
+        m.R[2] = oc * a[0] * a[2] + ss * a[1];
+        m.R[3] = oc * a[1] * a[0] + ss * a[2];
+        m.R[4] = cc + oc * a[1] * a[1];
+        m.R[5] = oc * a[1] * a[2] - ss * a[0];
+        m.R[6] = oc * a[2] * a[0] - ss * a[1];
+        m.R[7] = oc * a[2] * a[1] + ss * a[0];
+        m.R[8] = cc + oc * a[2] * a[2];
+        for (int k = 0; k < 3; ++k) m.ax[k] = a[k];
+    }
     return m;
 }
 
@@ -459,6 +505,12 @@ lks_status transfer_at(lks_ctx* c, int n) {
         return LKS_OK;
     }
     const Motion m = motion_row(c, n);
+    if (c->gaxis) {
+        launch_transfer_axis<T>(c->d, c->g, m, c->as, (const T*)c->kref, st4<T>(c->kus), c->st);
+        LAUNCHED();
+        c->stats[4] += 2;
+        return LKS_OK;
+    }
     launch_design_pos<T>(c->d, c->g, m, c->ts, c->st);
     LAUNCHED();
     launch_transfer<T>(c->d, c->g, m, c->ts, (const T*)c->kref_t, (T*)c->k2, st4<T>(c->kus),
@@ -526,7 +578,12 @@ lks_status adjoint_step(lks_ctx* c, int n, const void* sn, const void* sp) {
     }
     if (tm) timing_end(c, 1);
     if (c->d.nd > 0 && c->g.boxN > 0) {
-        launch_sens<T>(c->d, c->g, c->ts, (const T*)c->e, (const T*)c->kprime, c->gacc, c->st);
+        if (c->gaxis)
+            launch_sens_axis<T>(c->d, c->g, c->as, (const T*)c->e, (const T*)c->kprime, c->gacc,
+                                c->st);
+        else
+            launch_sens<T>(c->d, c->g, c->ts, (const T*)c->e, (const T*)c->kprime, c->gacc,
+                           c->st);
         LAUNCHED();
     }
     c->lam_par ^= 1;
@@ -1207,6 +1264,13 @@ lks_status lks_create(const lks_config* cfg, void* workspace, size_t ws_bytes, l
     c->gtmp = (double*)(w + L.off[L_GTMP]);
     c->scal = (double*)(w + L.off[L_SCAL]);
     c->ks = w + L.off[L_KS];
+    c->gaxis = general_axis(cfg) && c->d.nd > 0;
+    if (general_axis(cfg))
+        for (int a = 0; a < 3; ++a) c->axis[a] = cfg->rot_axis[a];
+    c->as.base = (int4*)(w + L.off[L_GBASE]);
+    c->as.frac = w + L.off[L_GFRAC];
+    c->as.cnt = (int*)(w + L.off[L_GCNT]);
+    c->as.idx = (int*)(w + L.off[L_GIDX]);
     c->s_end = w + L.off[L_SEND];
     c->l_end = w + L.off[L_LEND];
     c->nbase = c->flags + 8;
@@ -1379,6 +1443,20 @@ lks_status lks_set_motion(lks_ctx* c, const lks_motion* m) {
     const double cx[2] = {0.0, (double)(c->d.L[0] - 1)}, cy[2] = {0.0, (double)(c->d.L[1] - 1)};
     for (int n = 1; n <= c->cfg.max_steps; ++n) {
         const Motion mo = motion_row(c, n);
+        if (c->gaxis) {   // images of the design box's eight corners bound its image
+            for (int cidx = 0; cidx < 8; ++cidx) {
+                double dv[3];
+                for (int a = 0; a < 3; ++a)
+                    dv[a] = ((cidx >> a) & 1 ? (double)(c->d.L[a] - 1) : 0.0) - c->d.xiG[a];
+                for (int a = 0; a < 3; ++a) {
+                    const double xr = mo.R[3 * a] * dv[0] + mo.R[3 * a + 1] * dv[1] +
+                                      mo.R[3 * a + 2] * dv[2] + mo.xG[a];
+                    lo[a] = std::min(lo[a], xr);
+                    hi[a] = std::max(hi[a], xr);
+                }
+            }
+            continue;
+        }
         for (int a = 0; a < 2; ++a)
             for (int b = 0; b < 2; ++b) {
                 const double dx = cx[a] - c->d.xiG[0], dy = cy[b] - c->d.xiG[1];

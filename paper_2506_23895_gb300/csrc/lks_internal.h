@@ -58,6 +58,8 @@ struct Motion {
     int xgi[2];
     float xgh[2], xgl[2];
     float cf, sf, omf, xgf[2], ugf[3];
+    // rotation matrix R(theta) (row-major) about the unit axis ax (3D general-axis transfer)
+    double R[9], ax[3];
 };
 
 // Per-step scratch produced by the design-position kernel and consumed by the transfer,
@@ -78,6 +80,16 @@ struct TransferScratch {
 };
 
 constexpr int kMaxTaps = 32;
+
+// Scratch of the general-axis transfer: per design node the integer base of x_ref (int4) and
+// its fraction (V4<T>); per footprint-box cell the design nodes whose base is that cell.
+constexpr int kCellMax = 8;   // a unit cube holds at most 8 points at mutual distance >= 1
+struct AxisScratch {
+    int4* base;
+    void* frac;
+    int* cnt;    // [box cells]
+    int* idx;    // [box cells][kCellMax], ascending design index
+};
 
 // ---- kernel launchers (templated on T = float / double, explicitly instantiated) ----
 template <class T>
@@ -141,6 +153,13 @@ void launch_filter_T(const Design& d, double R, const double* g, const double* h
                      const double* wsum, double* out, cudaStream_t st);
 void launch_design_sum(long long nd, const double* a, double* out, cudaStream_t st);
 void launch_fill_f64(double* a, long long n, double v, cudaStream_t st);
+// General-axis transfer (kappa, u_S on the box) and its sensitivity gather.
+template <class T>
+void launch_transfer_axis(const Design& d, const Geom& g, const Motion& m, AxisScratch as,
+                          const T* kref, V4<T>* kus, cudaStream_t st);
+template <class T>
+void launch_sens_axis(const Design& d, const Geom& g, AxisScratch as, const T* e,
+                      const T* kprime, double* gacc, cudaStream_t st);
 template <class T>
 void launch_box_to_grid(const Geom& g, const V4<T>* kus, double* kappa, double* us,
                         cudaStream_t st);

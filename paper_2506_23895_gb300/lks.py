@@ -55,6 +55,7 @@ class LksConfig(ctypes.Structure):
         ("ckpt_bytes", ctypes.c_size_t),
         ("stream", ctypes.c_void_p),
         ("flags", ctypes.c_int),
+        ("rot_axis", ctypes.c_double * 3),
     ]
 
 
@@ -165,6 +166,9 @@ def make_config(problem, precision: int = FP32, max_steps: Optional[int] = None,
     c.ckpt_bytes = ckpt_bytes
     c.stream = stream
     c.flags = flags
+    ax = getattr(p, "rot_axis", (0.0, 0.0, 1.0))
+    for a in range(3):
+        c.rot_axis[a] = ax[a]
     return c
 
 
