@@ -330,6 +330,10 @@ def run_batch_line(args, lks, W, ws, rank, local, dev):
     return 0
 
 
+# kernel of each fused 3D forward-step variant (lks_step_variant)
+STEP3D_KERNELS = {0: "k_fused_step3d", 1: "k_zstep3d<8>"}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -433,7 +437,9 @@ def run_ours(args):
                         "avg_launch_ms": adj_step_ms, "samples": tm["adj_n"]},
            "roofline_forward": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
                                 "frac": ach / peak, "traffic": ncu_traffic("forward_step"),
-                                "kernel": "forward stencil step: k_fused_step3d",
+                                "kernel": "forward stencil step: " + STEP3D_KERNELS.get(
+                                    solver.step_variant(), "?"),
+                                "variant": solver.step_variant(),
                                 "peak_kind": f"{peak_kind} hbm_gbs (copy)",
                                 "algorithmic_bytes_per_launch": bytes_fwd,
                                 "avg_launch_ms": fwd_step_ms, "samples": tm["fwd_n"]},

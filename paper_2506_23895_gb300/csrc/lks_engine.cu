@@ -135,6 +135,8 @@ struct lks_ctx {
     int geo_gen = 0;             // bumped when the footprint box changes
     int tile_fwd = 0, tile_adj = 0;   // tile shapes of the fused 2D kernels
     bool gaxis = false;          // 3D rotation about an axis other than z
+    int step3d_req = -1;         // fused 3D step variant requested (-1: time them once)
+    int step3d_var = -1;         // variant in use (-1: not chosen yet)
     double axis[3] = {0.0, 0.0, 1.0};
     AxisScratch as;
     // design chain: density filter radius (0 = off), projection steepness and threshold
@@ -519,6 +521,50 @@ lks_status transfer_at(lks_ctx* c, int n) {
     return LKS_OK;
 }
 
+// Variant of the fused 3D step for this context: the requested one, else each variant timed on
+// the step src -> dst (three launches after one warm-up, CUDA events) and the fastest kept.
+// Every variant writes the same dst, so the timing launches leave the step done.
+lks_status choose_step3d(lks_ctx* c, const void* src, void* dst) {
+    if (c->step3d_req >= 0) {
+        c->step3d_var = c->step3d_req;
+        return LKS_OK;
+    }
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    CU(cudaStreamIsCapturing(c->st, &cap));
+    if (cap != cudaStreamCaptureStatusNone) {
+        c->step3d_var = 1;
+        return LKS_OK;
+    }
+    cudaEvent_t e0, e1;
+    CU(cudaEventCreate(&e0));
+    CU(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int bv = 1;
+    cudaError_t err = cudaSuccess;
+    for (int v = 0; v < kStep3dVariants && err == cudaSuccess; ++v) {
+        for (int r = 0; r < 4 && err == cudaSuccess; ++r) {
+            if (r == 1) err = cudaEventRecord(e0, c->st);
+            if (err == cudaSuccess)
+                err = launch_fused_step3d(c->g, (const V4<float>*)src, (const V4<float>*)c->kus,
+                                          (V4<float>*)dst, c->flags + 3, c->st, v);
+        }
+        if (err == cudaSuccess) err = cudaEventRecord(e1, c->st);
+        if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+        if (err == cudaSuccess && ms < best) {
+            best = ms;
+            bv = v;
+        }
+        c->stats[4] += 4;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (err != cudaSuccess) return fail(c, LKS_ERR_CUDA, "step variant timing: %s", cudaGetErrorString(err));
+    c->step3d_var = bv;
+    return LKS_OK;
+}
+
 // One forward step n: src -> dst (3D / FP64 / plain paths).
 template <class T>
 lks_status forward_step(lks_ctx* c, int n, const void* src, void* dst) {
@@ -526,8 +572,12 @@ lks_status forward_step(lks_ctx* c, int n, const void* src, void* dst) {
     if (s != LKS_OK) return s;
     const bool tm = timing_begin(c, n, 0);
     if (sizeof(T) == 4 && c->fused3d && !c->g.ks) {
+        if (c->step3d_var < 0) {
+            s = choose_step3d(c, src, dst);
+            if (s != LKS_OK) return s;
+        }
         cudaError_t e = launch_fused_step3d(c->g, (const V4<float>*)src, (const V4<float>*)c->kus,
-                                            (V4<float>*)dst, c->flags + 3, c->st);
+                                            (V4<float>*)dst, c->flags + 3, c->st, c->step3d_var);
         if (e != cudaSuccess) return fail(c, LKS_ERR_CUDA, "fused step: %s", cudaGetErrorString(e));
         ++c->stats[4];
     } else {
@@ -1592,6 +1642,18 @@ lks_status lks_transfer(lks_ctx* c, int step, double* kappa_out, double* us_out)
 
 int lks_uses_fused(const lks_ctx* c) {
     return !c ? 0 : ((c->fused3d && !c->g.ks) ? 1 : (c->fused2d ? 2 : 0));
+}
+
+lks_status lks_step_variant(lks_ctx* c, int request, int* chosen) {
+    if (!c || request < -2 || request >= kStep3dVariants)
+        return c ? fail(c, LKS_ERR_ARG, "step variant must be in [-2, %d]", kStep3dVariants - 1)
+                 : LKS_ERR_ARG;
+    if (request >= -1) {
+        c->step3d_req = request;
+        c->step3d_var = -1;
+    }
+    if (chosen) *chosen = c->step3d_var;
+    return LKS_OK;
 }
 
 lks_status lks_get_stats(const lks_ctx* c, long long* st5) {

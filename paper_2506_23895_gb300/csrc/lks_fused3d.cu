@@ -371,6 +371,352 @@ __global__ void __launch_bounds__(NTHR, 4)
     }
 }
 
+// ---------------------------------------------------------------- register z-march variant
+// The same step with fewer instructions and one block barrier per plane:
+//   * every thread keeps its column's u at plane p-1 and the full node at p in registers, so an
+//     f^eq evaluation reads the four in-plane neighbours and the next plane's centre only;
+//   * every thread waits on the ring's mbarriers itself (no serialising single-thread wait);
+//   * the cross-column f^eq values alternate between two shared-memory buffers, so one barrier
+//     per plane orders both their writes and their reads;
+//   * tiles of 32 x 8 columns; tiles away from the x and y faces take a path without face
+//     tests, and the rim f^eq work fills whole warps.
+// The arithmetic is that of feq_node and the gather above, operation for operation.
+template <int TY_>
+struct ZCfg {
+    static constexpr int TX = 32, TY = TY_;
+    static constexpr int HX = TX + 4, HY = TY + 4, FX = TX + 2, FY = TY + 2;
+    static constexpr int NTHR = TX * TY, NHALO = FX * FY - TX * TY, FS = FX * FY;
+    static constexpr int NSLOT = 5;
+    static constexpr int MINB = 3;     // resident blocks per SM
+    static constexpr unsigned PLANE_BYTES = HX * HY * 16;
+    static constexpr size_t OFF_F = (size_t)NSLOT * PLANE_BYTES;
+    static constexpr size_t OFF_BAR = OFF_F + (size_t)2 * NCROSS * FS * 4;
+    static constexpr size_t SMEM = OFF_BAR + NSLOT * 8;
+};
+
+// f^eq of one node from registers (centre c, u at p-1 and p+1) and its in-plane neighbours in
+// the ring plane (c0 points at the node).  Same operations as feq_node.
+template <int HXs, int FSs, bool EDGE>
+__device__ __forceinline__ void feq_reg(const FusedArgs& a, const float4* __restrict__ c0,
+                                        const float4& c, const float3& um, const float3& up,
+                                        float* __restrict__ sFn, int xm, int ym, int zm,
+                                        const float4& zfar, float& f_rest, float& f_pz,
+                                        float& f_mz) {
+    float Dxx, Dyx, Dzx, Dxy, Dyy, Dzy, Dxz, Dyz, Dzz;
+    if (EDGE) {
+        const float4 cm4 = make_float4(0.f, um.x, um.y, um.z);
+        const float4 cp4 = make_float4(0.f, up.x, up.y, up.z);
+        deriv2(xm, c, c0[-1], c0[1], xm == 2 ? c0[-2] : c, xm == 1 ? c0[2] : c, Dxx, Dyx, Dzx);
+        deriv2(ym, c, c0[-HXs], c0[HXs], ym == 2 ? c0[-2 * HXs] : c, ym == 1 ? c0[2 * HXs] : c,
+               Dxy, Dyy, Dzy);
+        deriv2(zm, c, cm4, cp4, zfar, zfar, Dxz, Dyz, Dzz);
+    } else {
+        const float4 e = c0[1], w = c0[-1], n = c0[HXs], s = c0[-HXs];
+        Dxx = e.y - w.y;
+        Dyx = e.z - w.z;
+        Dzx = e.w - w.w;
+        Dxy = n.y - s.y;
+        Dyy = n.z - s.z;
+        Dzy = n.w - s.w;
+        Dxz = up.x - um.x;
+        Dyz = up.y - um.y;
+        Dzz = up.z - um.z;
+    }
+    const float A = a.A, hA = 0.5f * a.A;
+    const float ASxx = A * Dxx, ASyy = A * Dyy, ASzz = A * Dzz;
+    const float ASxy = hA * (Dxy + Dyx);
+    const float ASxz = hA * (Dxz + Dzx);
+    const float ASyz = hA * (Dyz + Dzy);
+    const float ux = c.y, uy = c.z, uz = c.w;
+    const float P = c.x - 1.5f * (ux * ux + uy * uy + uz * uz);
+    f_rest = a.w0 * P;
+    const float w1 = a.w1, w13 = 3.f * a.w1;
+    {
+        const float b = w1 * (P + 4.5f * ux * ux + ASxx);
+        sFn[0 * FSs] = b + w13 * ux;
+        sFn[1 * FSs] = b - w13 * ux;
+    }
+    {
+        const float b = w1 * (P + 4.5f * uy * uy + ASyy);
+        sFn[2 * FSs] = b + w13 * uy;
+        sFn[3 * FSs] = b - w13 * uy;
+    }
+    {
+        const float b = w1 * (P + 4.5f * uz * uz + ASzz);
+        f_pz = b + w13 * uz;
+        f_mz = b - w13 * uz;
+    }
+    const float w2 = a.w2, w23 = 3.f * a.w2, w245 = 4.5f * a.w2, w2x2 = 2.f * a.w2;
+    const float T0 = w2 * (P + ASxx + ASyy + ASzz);
+    const float s1 = ux + uy, d1 = ux - uy;
+    const float q1 = ASxz + ASyz, q2 = ASyz - ASxz;
+    {
+        const float cu = s1 + uz;
+        const float sym = T0 + w245 * cu * cu + w2x2 * (ASxy + q1);
+        sFn[4 * FSs] = sym + w23 * cu;
+        sFn[11 * FSs] = sym - w23 * cu;
+    }
+    {
+        const float cu = uz - d1;
+        const float sym = T0 + w245 * cu * cu + w2x2 * (q2 - ASxy);
+        sFn[5 * FSs] = sym + w23 * cu;
+        sFn[10 * FSs] = sym - w23 * cu;
+    }
+    {
+        const float cu = uz + d1;
+        const float sym = T0 + w245 * cu * cu - w2x2 * (ASxy + q2);
+        sFn[6 * FSs] = sym + w23 * cu;
+        sFn[9 * FSs] = sym - w23 * cu;
+    }
+    {
+        const float cu = uz - s1;
+        const float sym = T0 + w245 * cu * cu + w2x2 * (ASxy - q1);
+        sFn[7 * FSs] = sym + w23 * cu;
+        sFn[8 * FSs] = sym - w23 * cu;
+    }
+}
+
+template <int TY_, bool IN>
+__device__ __forceinline__ void zbody(const CUtensorMap& tmap, const FusedArgs& a,
+                                      unsigned char* smem, int hfx, int hfy, int q0, int q1,
+                                      int nplanes) {
+    using C = ZCfg<TY_>;
+    constexpr int TX = C::TX, TY = C::TY, HX = C::HX, HY = C::HY, FX = C::FX;
+    constexpr int FS = C::FS, NSLOT = C::NSLOT;
+    float4* raw = reinterpret_cast<float4*>(smem);
+    float* sFbase = reinterpret_cast<float*>(smem + C::OFF_F);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::OFF_BAR);
+    const Geom& g = a.g;
+    const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+    const int tid = threadIdx.x;
+    const int tx = tid % TX, ty = tid / TX;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int gx = x0 + tx, gy = y0 + ty;
+    const int hgx = x0 - 1 + hfx, hgy = y0 - 1 + hfy;
+    const bool edge = !IN && ((x0 - 1 <= 0) || (x0 + TX >= nx - 1) || (y0 - 1 <= 0) ||
+                              (y0 + TY >= ny - 1));
+    const int pxm = axis_mode(gx, nx), pym = axis_mode(gy, ny);
+    const int rxm = axis_mode(hgx, nx), rym = axis_mode(hgy, ny);
+    const int hp = (ty + 2) * HX + (tx + 2);
+    const int hr = (hfy + 1) * HX + (hfx + 1);
+    const int fop = (ty + 1) * FX + (tx + 1);
+    const int forr = hfy * FX + hfx;
+    constexpr int RIMW = (C::NHALO + 31) / 32 * 32;
+    const bool has_rim = tid < RIMW;   // whole warps
+    const bool out_col = IN || (gx >= 1 && gx <= nx - 2 && gy >= 1 && gy <= ny - 2);
+    const bool bc_col = !IN && (gx == 1 || gx == nx - 2 || gy == 1 || gy == ny - 2);
+    const int bxx = gx - g.blo[0], byy = gy - g.blo[1];
+    const bool box_col = g.boxN > 0 && bxx >= 0 && byy >= 0 && bxx < g.bn[0] && byy < g.bn[1];
+    const long long box_plane = (long long)g.bn[0] * g.bn[1];
+    const float4* kus_col = a.kus + ((long long)byy * g.bn[0] + bxx) - (long long)g.blo[2] * box_plane;
+    const long long zstride = (long long)nx * ny;
+    const bool in_xy = IN || (gx < nx && gy < ny);
+    const bool rim_in_xy = IN || (hgx >= 0 && hgx < nx && hgy >= 0 && hgy < ny);
+    float4* out_col_ptr = a.out + ((long long)gy * nx + gx);
+    const int zlo = max(q0, 1), zhi = nz - 2;
+    const float bfx = (float)g.body[0], bfy = (float)g.body[1], bfz = (float)g.body[2];
+
+    bool ok = true;
+    // prologue: planes q0-2 (load 0) and q0-1 (load 1) into registers
+    float3 um, rum;
+    float4 c0, rc0;
+    {
+        bool good = mbar_wait(smem_addr(&bars[0]), 0);
+        good = mbar_wait(smem_addr(&bars[1]), 0) && good;
+        const float4* r0 = raw;
+        const float4* r1 = raw + (size_t)HX * HY;
+        const float4 v = r0[hp];
+        um = make_float3(v.y, v.z, v.w);
+        c0 = r1[hp];
+        const float4 rv = r0[hr];
+        rum = make_float3(rv.y, rv.z, rv.w);
+        rc0 = r1[hr];
+        ok = !__syncthreads_or(!good);
+    }
+    float acc0[4] = {0.f, 0.f, 0.f, 0.f};
+    float acc1[4] = {0.f, 0.f, 0.f, 0.f};
+    int s0 = 1;                    // slot of plane p
+    int wslot = 2, wpar = 0;       // slot / parity of plane p + 1
+    int islot = 0, ik = NSLOT;     // next refill: slot and load index
+
+    for (int p = q0 - 1; ok && p <= q1; ++p) {
+        const bool good = mbar_wait(smem_addr(&bars[wslot]), wpar);
+        const float4* r0 = raw + (size_t)s0 * HX * HY;
+        const float4* rp = raw + (size_t)wslot * HX * HY;
+        float* sF = sFbase + (size_t)((p - q0 + 1) & 1) * NCROSS * FS;
+        float* sFp = sF + fop;
+        const float4 cpn = rp[hp];
+        const float3 up = make_float3(cpn.y, cpn.z, cpn.w);
+        float4 rcpn = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (has_rim) rcpn = rp[hr];
+        const float3 rup = make_float3(rcpn.y, rcpn.z, rcpn.w);
+        float f_rest, f_pz, f_mz;
+        const int zm = (p == 0) ? 1 : (p == nz - 1 ? 2 : 0);
+        if (!edge && zm == 0) {
+            const float4 z0 = make_float4(0.f, 0.f, 0.f, 0.f);
+            feq_reg<HX, FS, false>(a, r0 + hp, c0, um, up, sFp, 0, 0, 0, z0, f_rest, f_pz, f_mz);
+            if (has_rim) {
+                float d0, d1, d2;
+                feq_reg<HX, FS, false>(a, r0 + hr, rc0, rum, rup, sF + forr, 0, 0, 0, z0, d0, d1,
+                                       d2);
+            }
+        } else {
+            const int z2 = (zm == 1) ? 2 : nz - 3;
+            float4 zf = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (zm != 0 && in_xy) zf = a.src[((long long)z2 * ny + gy) * nx + gx];
+            feq_reg<HX, FS, true>(a, r0 + hp, c0, um, up, sFp, pxm, pym, zm, zf, f_rest, f_pz,
+                                  f_mz);
+            if (has_rim) {
+                float4 zr = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (zm != 0 && rim_in_xy) zr = a.src[((long long)z2 * ny + hgy) * nx + hgx];
+                float d0, d1, d2;
+                feq_reg<HX, FS, true>(a, r0 + hr, rc0, rum, rup, sF + forr, rxm, rym, zm, zr, d0,
+                                      d1, d2);
+            }
+        }
+        um = make_float3(c0.y, c0.z, c0.w);
+        c0 = cpn;
+        rum = make_float3(rc0.y, rc0.z, rc0.w);
+        rc0 = rcpn;
+        if (__syncthreads_or(!good)) {
+            ok = false;
+            break;
+        }
+        // every thread is past its reads of plane p - 1: its slot takes load k(p) - 1 + NSLOT
+        if (tid == 0 && ik < nplanes) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            tma_load_box(smem_addr(raw + (size_t)islot * HX * HY), &tmap, x0 - 2, y0 - 2,
+                         q0 - 2 + ik, smem_addr(&bars[islot]), C::PLANE_BYTES);
+        }
+        ++ik;
+        if (++islot == NSLOT) islot = 0;
+        s0 = wslot;
+        if (++wslot == NSLOT) {
+            wslot = 0;
+            wpar ^= 1;
+        }
+        const float fpx = sFp[0 * FS - 1], fmx = sFp[1 * FS + 1];
+        const float fpy = sFp[2 * FS - FX], fmy = sFp[3 * FS + FX];
+        const float cpp_p = sFp[4 * FS - 1 - FX], cmp_p = sFp[5 * FS + 1 - FX];
+        const float cpm_p = sFp[6 * FS - 1 + FX], cmm_p = sFp[7 * FS + 1 + FX];
+        const float cpp_m = sFp[8 * FS - 1 - FX], cmp_m = sFp[9 * FS + 1 - FX];
+        const float cpm_m = sFp[10 * FS - 1 + FX], cmm_m = sFp[11 * FS + 1 + FX];
+        {
+            const float sxp = cpp_m + cpm_m, sxm = cmp_m + cmm_m;
+            const float syp = cpp_m + cmp_m, sym = cpm_m + cmm_m;
+            const float all = sxp + sxm + f_mz;
+            const int qz = p - 1;
+            if (out_col && qz >= zlo && qz <= zhi) {
+                const float r = acc0[0] + all;
+                const float ux = acc0[1] + (sxp - sxm) + bfx;
+                const float uy = acc0[2] + (syp - sym) + bfy;
+                const float uz = acc0[3] - all + bfz;
+                float4 o;
+                o.x = r;
+                const int bz = qz - g.blo[2];
+                if (box_col && bz >= 0 && bz < g.bn[2]) {
+                    const float4 ks = kus_col[(long long)qz * box_plane];
+                    const float inv = 1.f / (1.f + ks.x);
+                    o.y = fmaf(ks.x, ks.y, ux) * inv;
+                    o.z = fmaf(ks.x, ks.z, uy) * inv;
+                    o.w = fmaf(ks.x, ks.w, uz) * inv;
+                } else {
+                    o.y = ux;
+                    o.z = uy;
+                    o.w = uz;
+                }
+                out_col_ptr[(long long)qz * zstride] = o;
+                if (bc_col || qz == 1 || qz == nz - 2) {
+                    V4<float> v;
+                    v.r = o.x;
+                    v.x = o.y;
+                    v.y = o.z;
+                    v.z = o.w;
+                    write_bc_from_compact(g, gx, gy, qz, v, reinterpret_cast<V4<float>*>(a.out));
+                }
+            }
+        }
+        acc0[0] = acc1[0] + (f_rest + fpx + fmx + fpy + fmy);
+        acc0[1] = acc1[1] + (fpx - fmx);
+        acc0[2] = acc1[2] + (fpy - fmy);
+        acc0[3] = acc1[3];
+        {
+            const float sxp = cpp_p + cpm_p, sxm = cmp_p + cmm_p;
+            const float syp = cpp_p + cmp_p, sym = cpm_p + cmm_p;
+            const float all = sxp + sxm + f_pz;
+            acc1[0] = all;
+            acc1[1] = sxp - sxm;
+            acc1[2] = syp - sym;
+            acc1[3] = all;
+        }
+    }
+    if (!ok) {
+        if (tid == 0) {
+            atomicOr(a.err, 8);
+            const long long t0 = clock64();
+            while (clock64() - t0 < (1LL << 28)) {
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <int TY_>
+__global__ void __launch_bounds__(ZCfg<TY_>::NTHR, ZCfg<TY_>::MINB)
+    k_zstep3d(const __grid_constant__ CUtensorMap tmap, const FusedArgs a) {
+    using C = ZCfg<TY_>;
+    constexpr int TX = C::TX, TY = C::TY, HX = C::HX, HY = C::HY, FX = C::FX, FY = C::FY;
+    constexpr int NSLOT = C::NSLOT;
+    extern __shared__ __align__(128) unsigned char smem[];
+    float4* raw = reinterpret_cast<float4*>(smem);
+    float* sFbase = reinterpret_cast<float*>(smem + C::OFF_F);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::OFF_BAR);
+    const Geom& g = a.g;
+    const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+    const int tid = threadIdx.x;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int q0 = blockIdx.z * a.zchunk;
+    const int q1 = min(nz, q0 + a.zchunk);
+    const int nplanes = q1 - q0 + 4;   // raw planes q0-2 .. q1+1 (load index k = plane - q0 + 2)
+    // rim nodes over whole warps: lanes past the last rim node repeat earlier ones (the same
+    // values are stored twice), so no warp splits on the rim work
+    constexpr int RIMW = (C::NHALO + 31) / 32 * 32;
+    const int rr = tid < C::NHALO ? tid : tid - (RIMW - C::NHALO);
+    int hfx = 0, hfy = 0;   // threads past the rim warps keep (0, 0): they read, never store
+    if (tid < RIMW) {
+        if (rr < FX) {
+            hfx = rr;
+        } else if (rr < 2 * FX) {
+            hfx = rr - FX;
+            hfy = FY - 1;
+        } else if (rr < 2 * FX + TY) {
+            hfy = 1 + (rr - 2 * FX);
+        } else {
+            hfx = FX - 1;
+            hfy = 1 + (rr - 2 * FX - TY);
+        }
+    }
+    if ((smem_addr(smem) & 127u) != 0u) {
+        if (tid == 0) atomicOr(a.err, 16);
+        return;
+    }
+    if (tid == 0) {
+        for (int s = 0; s < NSLOT; ++s) mbar_init(smem_addr(&bars[s]));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        for (int k = 0; k < NSLOT && k < nplanes; ++k)
+            tma_load_box(smem_addr(raw + (size_t)k * HX * HY), &tmap, x0 - 2, y0 - 2,
+                         q0 - 2 + k, smem_addr(&bars[k]), C::PLANE_BYTES);
+    }
+    __syncthreads();
+    // a tile whose raw halo lies inside the grid and whose f^eq region and columns keep two
+    // nodes away from the x and y faces takes the path without face tests
+    const bool interior = x0 >= 3 && x0 + TX + 2 <= nx - 1 && y0 >= 3 && y0 + TY + 2 <= ny - 1;
+    if (interior)
+        zbody<TY_, true>(tmap, a, smem, hfx, hfy, q0, q1, nplanes);
+    else
+        zbody<TY_, false>(tmap, a, smem, hfx, hfy, q0, q1, nplanes);
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     if (!fn) {
@@ -441,19 +787,30 @@ int fused_zchunk(const Geom& g, long long tiles) {
     return (g.n[2] + chunks - 1) / chunks;
 }
 
-// One fused forward step src -> dst.  Returns a CUDA error code (cudaSuccess on success).
-cudaError_t launch_fused_step3d(const Geom& g, const V4<float>* src, const V4<float>* kus,
-                                V4<float>* dst, int* err, cudaStream_t st) {
-    CUtensorMap map;
-    if (!encode_state_map(&map, src, g, HX, HY)) return cudaErrorInvalidValue;
+template <int TY_>
+cudaError_t launch_zstep(const Geom& g, const CUtensorMap& map, const FusedArgs& a0,
+                         cudaStream_t st) {
+    using C = ZCfg<TY_>;
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_fused_step3d,
+        cudaError_t e = cudaFuncSetAttribute(k_zstep3d<TY_>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)SMEM_BYTES);
+                                             (int)C::SMEM);
         if (e != cudaSuccess) return e;
         attr = true;
     }
+    FusedArgs a = a0;
+    const int tiles_x = (g.n[0] + C::TX - 1) / C::TX, tiles_y = (g.n[1] + C::TY - 1) / C::TY;
+    a.zchunk = fused_zchunk_waves(g, (long long)tiles_x * tiles_y, C::MINB);
+    const int chunks = (g.n[2] + a.zchunk - 1) / a.zchunk;
+    k_zstep3d<TY_><<<dim3(tiles_x, tiles_y, chunks), C::NTHR, C::SMEM, st>>>(map, a);
+    return cudaGetLastError();
+}
+
+// One fused forward step src -> dst in variant v (0: shared-memory z-march with two barriers
+// per plane, 1: register z-march), both on 32 x 8 tiles.  Returns a CUDA error code.
+cudaError_t launch_fused_step3d(const Geom& g, const V4<float>* src, const V4<float>* kus,
+                                V4<float>* dst, int* err, cudaStream_t st, int v) {
     FusedArgs a;
     a.g = g;
     a.out = reinterpret_cast<float4*>(dst);
@@ -464,6 +821,20 @@ cudaError_t launch_fused_step3d(const Geom& g, const V4<float>* src, const V4<fl
     a.w0 = (float)(2.0 / 9.0);
     a.w1 = (float)(1.0 / 9.0);
     a.w2 = (float)(1.0 / 72.0);
+    CUtensorMap map;
+    if (v == 1) {
+        if (!encode_state_map(&map, src, g, ZCfg<8>::HX, ZCfg<8>::HY)) return cudaErrorInvalidValue;
+        return launch_zstep<8>(g, map, a, st);
+    }
+    if (!encode_state_map(&map, src, g, HX, HY)) return cudaErrorInvalidValue;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_fused_step3d,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)SMEM_BYTES);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
     const int tiles_x = (g.n[0] + TX - 1) / TX, tiles_y = (g.n[1] + TY - 1) / TY;
     a.zchunk = fused_zchunk_waves(g, (long long)tiles_x * tiles_y, 4);
     const int chunks = (g.n[2] + a.zchunk - 1) / a.zchunk;

@@ -125,8 +125,9 @@ struct FaceOffsets {
 bool fused3d_eligible(const Geom& g);
 int fused_zchunk(const Geom& g, long long tiles);
 int fused_zchunk_waves(const Geom& g, long long tiles, int per_sm);
+constexpr int kStep3dVariants = 2;
 cudaError_t launch_fused_step3d(const Geom& g, const V4<float>* src, const V4<float>* kus,
-                                V4<float>* dst, int* err, cudaStream_t st);
+                                V4<float>* dst, int* err, cudaStream_t st, int variant);
 // Offsets of the six face arrays (3 floats per face node) and their total length.
 void face_offsets(const Geom& g, FaceOffsets& fo, long long& total);
 cudaError_t launch_fused_adj3d(const Geom& g, const V4<float>* lam_in, V4<float>* lam_out,

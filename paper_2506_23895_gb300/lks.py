@@ -22,7 +22,7 @@ STATUS = {0: "LKS_OK", 1: "LKS_ERR_ARG", 2: "LKS_ERR_ORDER", 3: "LKS_ERR_NOMEM",
 # every symbol include/lks.h declares
 EXPORTS = ("lks_workspace_bytes", "lks_create", "lks_set_design", "lks_set_motion",
            "lks_set_initial_state", "lks_forward", "lks_adjoint", "lks_get_state",
-           "lks_transfer", "lks_uses_fused", "lks_get_stats", "lks_set_timing", "lks_read_timing",
+           "lks_transfer", "lks_uses_fused", "lks_step_variant", "lks_get_stats", "lks_set_timing", "lks_read_timing",
            "lks_checkpoint_schedule", "lks_step_noalloc", "lks_last_error", "lks_destroy",
            "lks_batch_create", "lks_batch_set_options", "lks_batch_forward", "lks_batch_adjoint",
            "lks_batch_tile_shapes", "lks_batch_tuning", "lks_batch_stats",
@@ -93,6 +93,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.lks_get_stats.argtypes = [P, ctypes.POINTER(ctypes.c_longlong)]
     lib.lks_uses_fused.argtypes = [P]
     lib.lks_uses_fused.restype = ctypes.c_int
+    lib.lks_step_variant.argtypes = [P, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
     lib.lks_set_timing.argtypes = [P, ctypes.c_int]
     lib.lks_read_timing.argtypes = [P, D]
     lib.lks_checkpoint_schedule.argtypes = [ctypes.c_int, ctypes.c_int,
@@ -324,6 +325,13 @@ class Solver:
     def kernels(self) -> str:
         """'fused3d', 'fused2d' or 'plain': which kernels run this context's steps."""
         return {1: "fused3d", 2: "fused2d"}.get(self.lib.lks_uses_fused(self.ctx), "plain")
+
+    def step_variant(self, request: int = -2) -> int:
+        """Fused 3D step variant: request 0..1 fixes one, -1 times them on the first step,
+        -2 only reads; returns the variant in use (-1 before the first fused step)."""
+        v = ctypes.c_int(-1)
+        self._check(self.lib.lks_step_variant(self.ctx, request, ctypes.byref(v)))
+        return v.value
 
     def set_timing(self, stride: int) -> None:
         self._check(self.lib.lks_set_timing(self.ctx, stride))

@@ -200,6 +200,40 @@ def test_fused_fp32_step_matches_plain_fp32_and_oracle(L, name):
     assert rel_l2(gf, go) < 1e-4
 
 
+@pytest.mark.parametrize("name", ["small3d_J1", "ragged3d", "mid3d"])
+def test_fused_step_variants_agree(L, name):
+    """Every variant of the fused 3D forward step (fixed through lks_step_variant) gives the
+    same run as variant 0 up to rounding, within the FP32 tolerances of the oracle; the
+    automatic choice picks one of them."""
+    w = MID3D() if name == "mid3d" else CASES[name]()
+    Jo, go = oracle.gradient(w.problem, w.gamma, w.motion)
+    res = []
+    for v in range(2):
+        s = L.Solver(w.problem, L.FP32)
+        assert s.step_variant(v) == -1
+        s.set_design(w.gamma)
+        s.set_motion(w.motion)
+        J = s.forward()
+        assert s.step_variant() == v
+        res.append((J, s.get_state(), s.adjoint()))
+        s.close()
+    J0, s0, g0 = res[0]
+    for J, st, g in res:
+        assert abs(J - J0) <= 1e-6 * abs(J0)
+        assert rel_max(st, s0) < 1e-6
+        assert rel_l2(g, g0) < 1e-6
+        assert abs(J - Jo) <= 1e-5 * abs(Jo)
+        assert rel_l2(g, go) < 1e-4
+    s = L.Solver(w.problem, L.FP32)
+    s.set_design(w.gamma)
+    s.set_motion(w.motion)
+    s.forward()
+    assert s.step_variant() in (0, 1)
+    with pytest.raises(L.LksError):
+        s.step_variant(2)
+    s.close()
+
+
 def test_kernel_choice_per_context(L):
     w = CASES["small3d_J2"]()
     s = L.Solver(w.problem, L.FP64)
