@@ -190,11 +190,12 @@ lks_status lks_transfer(lks_ctx* ctx, int step, double* kappa_out, double* us_ou
 int lks_uses_fused(const lks_ctx* ctx);
 
 /* Variant of the fused FP32 D3Q15 forward step (lks_uses_fused == 1): 0 a shared-memory
- * z-march with two block barriers per plane, 1 a register z-march with one.  Both evaluate the
- * same arithmetic (Sec. 2.2 f^eq, Eqs. rho and u, the Brinkman update) and agree to rounding.
- * request: 0..1 fixes a variant, -1 (the default) times every variant once on the first fused
- * step and keeps the fastest, -2 changes nothing.  *chosen (may be NULL) receives the variant
- * in use, -1 before the first fused step.  LKS_ERR_ARG for any other request. */
+ * z-march with two block barriers per plane, 1 (the default) a register z-march with one.  Both
+ * evaluate the same arithmetic (Sec. 2.2 f^eq, Eqs. rho and u, the Brinkman update) and agree to
+ * rounding, not bitwise.  request: 0..1 fixes a variant, -1 times every variant once on the
+ * first fused step and keeps the fastest (results then depend on that choice at the rounding
+ * level), -2 changes nothing.  *chosen (may be NULL) receives the variant in use, -1 before the
+ * first fused step.  LKS_ERR_ARG for any other request. */
 lks_status lks_step_variant(lks_ctx* ctx, int request, int* chosen);
 
 /* Counters of the last forward+adjoint: [0] forward steps, [1] recomputed steps,

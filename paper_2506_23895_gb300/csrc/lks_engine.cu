@@ -135,7 +135,7 @@ struct lks_ctx {
     int geo_gen = 0;             // bumped when the footprint box changes
     int tile_fwd = 0, tile_adj = 0;   // tile shapes of the fused 2D kernels
     bool gaxis = false;          // 3D rotation about an axis other than z
-    int step3d_req = -1;         // fused 3D step variant requested (-1: time them once)
+    int step3d_req = 1;          // fused 3D step variant requested (-1: time them once)
     int step3d_var = -1;         // variant in use (-1: not chosen yet)
     double axis[3] = {0.0, 0.0, 1.0};
     AxisScratch as;

@@ -124,7 +124,12 @@ __global__ void __launch_bounds__(NT) k_t_bcT2d(Plan p, int noff, int lam) {
         const int t = (u - pre[i]) * kUnitThreads + threadIdx.x;
         int x, y;
         if (!shell2d(I.g, t, x, y)) continue;
-        const double h = (n >= I.win_begin && n <= I.win_end) ? I.hwin : 0.0;
+        ObjAdd<float> h;   // the objective source of the instance record (formed on the host)
+        h.on = n >= I.win_begin && n <= I.win_end;
+        h.r = I.src_r;
+        h.x = I.src_x;
+        h.y = I.src_y;
+        h.z = 0.f;
         bcT_node<float>(I.g, (V4<float>*)I.bufs[lam], h, x, y, 0);
     }
 }

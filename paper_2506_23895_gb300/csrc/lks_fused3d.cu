@@ -50,7 +50,44 @@ struct FusedArgs {
     int* err;
     int zchunk;
     float A, w0, w1, w2;
+    float bf[3];          // body force in single precision
 };
+
+// Boundary copies sourced by interior node (gx, gy, z) of value o (Eqs. bc_rho, bc_u): every
+// boundary node reached by stepping to the low face (coordinate 1) and/or the high face
+// (coordinate n - 2) along the axes, with the value of its winning face.  Loops over scalar
+// options (no local arrays), so the common path carries no stack traffic.
+__device__ __forceinline__ void write_bc_f(const Geom& g, int gx, int gy, int z, float4 o,
+                                           float4* out) {
+    V4<float> v;
+    v.r = o.x;
+    v.x = o.y;
+    v.y = o.z;
+    v.z = o.w;
+    const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+    const int nxo = 1 + (gx == 1) + (gx == nx - 2);
+    const int nyo = 1 + (gy == 1) + (gy == ny - 2);
+    const int nzo = 1 + (z == 1) + (z == nz - 2);
+#pragma unroll 1
+    for (int i = 0; i < nxo; ++i) {
+        const int mx = i == 0 ? 0 : ((i == 1 && gx == 1) ? 1 : 2);
+        const int bx = mx == 0 ? gx : (mx == 1 ? 0 : nx - 1);
+#pragma unroll 1
+        for (int j = 0; j < nyo; ++j) {
+            const int my = j == 0 ? 0 : ((j == 1 && gy == 1) ? 1 : 2);
+            const int by = my == 0 ? gy : (my == 1 ? 0 : ny - 1);
+#pragma unroll 1
+            for (int k = 0; k < nzo; ++k) {
+                if ((i | j | k) == 0) continue;
+                const int mz = k == 0 ? 0 : ((k == 1 && z == 1) ? 1 : 2);
+                const int bz = mz == 0 ? z : (mz == 1 ? 0 : nz - 1);
+                const int side[3] = {mx - 1, my - 1, mz - 1};
+                const V4<float> b = bc_value(g, winning_face(g, side), v);
+                out[((long long)bz * ny + by) * nx + bx] = make_float4(b.r, b.x, b.y, b.z);
+            }
+        }
+    }
+}
 
 // 2 x first derivative (D = 2 du/dx) of (ux, uy, uz) along one axis from the node c and its
 // neighbours at -1/+1 (and -2/+2 for the one-sided forms).  mode 0: central, 1: one-sided at
@@ -232,7 +269,7 @@ __global__ void __launch_bounds__(NTHR, 4)
     const bool rim_in_xy = hgx >= 0 && hgx < nx && hgy >= 0 && hgy < ny;
     float4* out_col_ptr = a.out + ((long long)gy * nx + gx);
     const int zlo = max(q0, 1), zhi = nz - 2;
-    const float bfx = (float)g.body[0], bfy = (float)g.body[1], bfz = (float)g.body[2];
+    const float bfx = a.bf[0], bfy = a.bf[1], bfz = a.bf[2];
 
     float acc0[4] = {0.f, 0.f, 0.f, 0.f};  // plane p (c_z = 0 and -1 groups still to come)
     float acc1[4] = {0.f, 0.f, 0.f, 0.f};  // plane p + 1
@@ -330,14 +367,7 @@ __global__ void __launch_bounds__(NTHR, 4)
                     o.w = uz;
                 }
                 out_col_ptr[(long long)qz * zstride] = o;
-                if (bc_col || qz == 1 || qz == nz - 2) {
-                    V4<float> v;
-                    v.r = o.x;
-                    v.x = o.y;
-                    v.y = o.z;
-                    v.z = o.w;
-                    write_bc_from_compact(g, gx, gy, qz, v, reinterpret_cast<V4<float>*>(a.out));
-                }
+                if (bc_col || qz == 1 || qz == nz - 2) write_bc_f(g, gx, gy, qz, o, a.out);
             }
         }
         // c_z = 0 group into plane p, c_z = +1 group starts plane p+1
@@ -514,7 +544,7 @@ __device__ __forceinline__ void zbody(const CUtensorMap& tmap, const FusedArgs& 
     const bool rim_in_xy = IN || (hgx >= 0 && hgx < nx && hgy >= 0 && hgy < ny);
     float4* out_col_ptr = a.out + ((long long)gy * nx + gx);
     const int zlo = max(q0, 1), zhi = nz - 2;
-    const float bfx = (float)g.body[0], bfy = (float)g.body[1], bfz = (float)g.body[2];
+    const float bfx = a.bf[0], bfy = a.bf[1], bfz = a.bf[2];
 
     bool ok = true;
     // prologue: planes q0-2 (load 0) and q0-1 (load 1) into registers
@@ -626,14 +656,7 @@ __device__ __forceinline__ void zbody(const CUtensorMap& tmap, const FusedArgs& 
                     o.w = uz;
                 }
                 out_col_ptr[(long long)qz * zstride] = o;
-                if (bc_col || qz == 1 || qz == nz - 2) {
-                    V4<float> v;
-                    v.r = o.x;
-                    v.x = o.y;
-                    v.y = o.z;
-                    v.z = o.w;
-                    write_bc_from_compact(g, gx, gy, qz, v, reinterpret_cast<V4<float>*>(a.out));
-                }
+                if (bc_col || qz == 1 || qz == nz - 2) write_bc_f(g, gx, gy, qz, o, a.out);
             }
         }
         acc0[0] = acc1[0] + (f_rest + fpx + fmx + fpy + fmy);
@@ -821,6 +844,7 @@ cudaError_t launch_fused_step3d(const Geom& g, const V4<float>* src, const V4<fl
     a.w0 = (float)(2.0 / 9.0);
     a.w1 = (float)(1.0 / 9.0);
     a.w2 = (float)(1.0 / 72.0);
+    for (int k = 0; k < 3; ++k) a.bf[k] = (float)g.body[k];
     CUtensorMap map;
     if (v == 1) {
         if (!encode_state_map(&map, src, g, ZCfg<8>::HX, ZCfg<8>::HY)) return cudaErrorInvalidValue;

@@ -54,28 +54,48 @@ struct AdjArgs {
     int zchunk;
     float A, w0, w1, w2;
     float obj_r, obj_u[3]; // d j / d s at target nodes, times the window weight
+    int has_obj;           // any of them non-zero
 };
 
-// Convert lambda to mu at raw-tile slot position v (node gx, gy, gz).  `own` marks a node of the
-// tile: only those write e.
-__device__ __forceinline__ void to_mu(const AdjArgs& a, float4& v, int gx, int gy, int gz,
-                                      bool own) {
+// Per-column facts of a node column (x, y), evaluated once per thread so that the per-plane
+// conversion tests z only: bit 0 interior in x and y (not on an x or y face, inside the grid),
+// bit 1 inside the footprint box in x and y, bit 2 inside the objective target in x and y.
+constexpr int COL_IN = 1, COL_BOX = 2, COL_TGT = 4;
+__device__ __forceinline__ int col_flags(const Geom& g, int gx, int gy) {
+    int f = 0;
+    if (gx >= 1 && gy >= 1 && gx <= g.n[0] - 2 && gy <= g.n[1] - 2) f |= COL_IN;
+    const int bx = gx - g.blo[0], by = gy - g.blo[1];
+    if (g.boxN > 0 && bx >= 0 && by >= 0 && bx < g.bn[0] && by < g.bn[1]) f |= COL_BOX;
+    bool t = gx >= g.obox[0] && gx <= g.obox[1] && gy >= g.obox[2] && gy <= g.obox[3];
+    if (t && g.ocyl_r > 0.0) {
+        const double dx = gx - g.ocyl_c[0], dy = gy - g.ocyl_c[1];
+        t = dx * dx + dy * dy <= g.ocyl_r * g.ocyl_r;
+    }
+    if (t) f |= COL_TGT;
+    return f;
+}
+
+// Convert lambda to mu at raw-tile slot position v (node gx, gy, gz with column flags cf): 0 on
+// boundary nodes and outside the grid; otherwise the objective source (target nodes, has_obj)
+// and the Brinkman transpose (footprint box).  `own` marks a node of the tile: only those write e.
+__device__ __forceinline__ void to_mu(const AdjArgs& a, float4& v, int cf, int gx, int gy, int gz,
+                                      bool own, bool has_obj) {
     const Geom& g = a.g;
-    if (gx <= 0 || gy <= 0 || gz <= 0 || gx >= g.n[0] - 1 || gy >= g.n[1] - 1 ||
-        gz >= g.n[2] - 1) {
-        v = make_float4(0.f, 0.f, 0.f, 0.f);   // boundary node or outside the grid
+    if (!(cf & COL_IN) || gz <= 0 || gz >= g.n[2] - 1) {
+        v = make_float4(0.f, 0.f, 0.f, 0.f);
         return;
     }
     float4 l = v;
-    if ((a.obj_r != 0.f || a.obj_u[0] != 0.f || a.obj_u[1] != 0.f || a.obj_u[2] != 0.f) &&
-        in_target(g, gx, gy, gz)) {
+    if (has_obj && (cf & COL_TGT) && gz >= g.obox[4] && gz <= g.obox[5]) {
         l.x += a.obj_r;
         l.y += a.obj_u[0];
         l.z += a.obj_u[1];
         l.w += a.obj_u[2];
     }
-    long long bi;
-    if (in_box(g, gx, gy, gz, bi)) {
+    const int bz = gz - g.blo[2];
+    if ((cf & COL_BOX) && bz >= 0 && bz < g.bn[2]) {
+        const long long bi =
+            ((long long)bz * g.bn[1] + (gy - g.blo[1])) * g.bn[0] + (gx - g.blo[0]);
         const float4 ks = a.kus[bi];
         const float inv = 1.f / (1.f + ks.x);
         l.y *= inv;
@@ -206,6 +226,9 @@ __global__ void __launch_bounds__(NTHR, 4)
 
     const int gx = x0 + tx, gy = y0 + ty;
     const bool own_in = gx < nx && gy < ny;
+    const int cf_own = col_flags(g, gx, gy);
+    const int cf_halo = col_flags(g, x0 - 2 + cx, y0 - 2 + cy);
+    const bool has_obj = a.has_obj != 0;
     const int hp = (ty + 2) * HX + (tx + 2);       // own node in the raw tile
     const int hc = cy * HX + cx;                   // halo node to convert
     const int hr = (rfy + 1) * HX + (rfx + 1);     // rim node of the moment region
@@ -246,8 +269,9 @@ __global__ void __launch_bounds__(NTHR, 4)
         {
             float4* pl = raw + (size_t)cslot * HX * HY;
             const int gz = p + 1;
-            to_mu(a, pl[hp], gx, gy, gz, own_in);
-            if (tid < NRIM2) to_mu(a, pl[hc], x0 - 2 + cx, y0 - 2 + cy, gz, false);
+            to_mu(a, pl[hp], cf_own, gx, gy, gz, own_in, has_obj);
+            if (tid < NRIM2)
+                to_mu(a, pl[hc], cf_halo, x0 - 2 + cx, y0 - 2 + cy, gz, false, has_obj);
         }
         const int sl_p = cslot;                                   // plane p + 1
         const int sl_0 = cslot == 0 ? NSLOT - 1 : cslot - 1;      // plane p
@@ -437,6 +461,7 @@ cudaError_t launch_fused_adj3d(const Geom& g, const V4<float>* lam_in, V4<float>
         else
             for (int k = 0; k < 3; ++k) a.obj_u[k] = (float)(-h * g.odir[k] / g.ocount);
     }
+    a.has_obj = (a.obj_r != 0.f || a.obj_u[0] != 0.f || a.obj_u[1] != 0.f || a.obj_u[2] != 0.f);
     const int tiles_x = (g.n[0] + TX - 1) / TX, tiles_y = (g.n[1] + TY - 1) / TY;
     a.zchunk = fused_zchunk_waves(g, (long long)tiles_x * tiles_y, 4);
     const int chunks = (g.n[2] + a.zchunk - 1) / a.zchunk;

@@ -204,7 +204,7 @@ __device__ __forceinline__ bool shell_node(const Geom& g, long long t, int& x, i
 }
 
 template <class T>
-__global__ void k_adj_bcT(Geom g, V4<T>* lam, double h) {
+__global__ void k_adj_bcT(Geom g, V4<T>* lam, ObjAdd<T> h) {
     const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     int x, y, z;
     if (!shell_node(g, t, x, y, z)) return;
@@ -216,7 +216,7 @@ __global__ void k_adj_bcT(Geom g, V4<T>* lam, double h) {
 template <class T>
 __global__ void k_adj_mu(Geom g, const V4<T>* __restrict__ lam, const V4<T>* __restrict__ kus,
                          const V4<T>* __restrict__ sn, V4<T>* __restrict__ mu,
-                         T* __restrict__ e, double h, const V4<T>* __restrict__ u3) {
+                         T* __restrict__ e, ObjAdd<T> h, const V4<T>* __restrict__ u3) {
     long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (m >= g.nodes) return;
     int x, y, z;
@@ -449,13 +449,14 @@ template <class T>
 void launch_adj_bcT(const Geom& g, V4<T>* lam, double h, cudaStream_t st) {
     const long long shell = 2LL * ((long long)g.n[1] * g.n[2] + (long long)g.n[0] * g.n[2] +
                                    (long long)g.n[0] * g.n[1]);
-    k_adj_bcT<T><<<grid_for(shell), kThreads, 0, st>>>(g, lam, h);
+    k_adj_bcT<T><<<grid_for(shell), kThreads, 0, st>>>(g, lam, obj_add<T>(g, h));
 }
 
 template <class T>
 void launch_adj_mu(const Geom& g, const V4<T>* lam, const V4<T>* kus, const V4<T>* sn,
                    V4<T>* mu, T* e, double h, cudaStream_t st, const V4<T>* u3) {
-    k_adj_mu<T><<<grid_for(g.nodes), kThreads, 0, st>>>(g, lam, kus, sn, mu, e, h, u3);
+    k_adj_mu<T><<<grid_for(g.nodes), kThreads, 0, st>>>(g, lam, kus, sn, mu, e, obj_add<T>(g, h),
+                                                        u3);
 }
 
 template <class T>

@@ -148,7 +148,7 @@ __device__ __forceinline__ void sens2d_node(const Design& d, const Geom& g,
 // transpose of the kappa transfer), times kappa', added to dJ/dgamma in FP64.  The z shift is
 // the same for every design plane, so each analysis plane's 4 x 4 x-y tap sum is formed once
 // and the four z weights slide over them.
-constexpr int kSensRun = 8;
+constexpr int kSensRun = 4;
 
 template <class T>
 __device__ __forceinline__ void sens_run(const Design& d, const Geom& g, const TransferScratch& ts,
@@ -235,16 +235,39 @@ __device__ __forceinline__ void objective_block(const Geom& g, const V4<T>* __re
 }
 
 // Objective's direct adjoint source at one node (h = window weight or 0 outside the window).
+// Objective source h_n dj/ds at a target node (Sec. 2.5) in the precision T of the state, formed
+// on the host in FP64 and rounded once: the device never divides in FP64.
 template <class T>
-__device__ __forceinline__ void obj_source(const Geom& g, int x, int y, int z, double h,
-                                           V4<T>& l) {
-    if (h == 0.0 || !in_target(g, x, y, z)) return;
+struct ObjAdd {
+    T r, x, y, z;
+    int on;   // h_n != 0
+};
+template <class T>
+inline ObjAdd<T> obj_add(const Geom& g, double h) {
+    ObjAdd<T> o;
+    o.on = h != 0.0;
+    o.r = o.x = o.y = o.z = (T)0;
+    if (h == 0.0) return o;
     if (g.okind == 0) {
-        l.r += (T)(-h / (3.0 * g.ocount));
+        o.r = (T)(-h / (3.0 * g.ocount));
     } else {
-        l.x += (T)(-h * g.odir[0] / g.ocount);
-        l.y += (T)(-h * g.odir[1] / g.ocount);
-        l.z += (T)(-h * g.odir[2] / g.ocount);
+        o.x = (T)(-h * g.odir[0] / g.ocount);
+        o.y = (T)(-h * g.odir[1] / g.ocount);
+        o.z = (T)(-h * g.odir[2] / g.ocount);
+    }
+    return o;
+}
+
+template <class T>
+__device__ __forceinline__ void obj_source(const Geom& g, int x, int y, int z, const ObjAdd<T>& o,
+                                           V4<T>& l) {
+    if (!o.on || !in_target(g, x, y, z)) return;
+    if (g.okind == 0) {
+        l.r += o.r;
+    } else {
+        l.x += o.x;
+        l.y += o.y;
+        l.z += o.z;
     }
 }
 
@@ -254,8 +277,8 @@ __device__ __forceinline__ void obj_source(const Geom& g, int x, int y, int z, d
 // velocity), after their objective source.  Boundary nodes are read only; later kernels treat
 // them as zero.
 template <class T>
-__device__ __forceinline__ void bcT_node(const Geom& g, V4<T>* lam, double h, int x, int y,
-                                         int z) {
+__device__ __forceinline__ void bcT_node(const Geom& g, V4<T>* lam, const ObjAdd<T>& h, int x,
+                                         int y, int z) {
     if (!sources_boundary(g, x, y, z)) return;
     const long long m = node_index(g, x, y, z);
     V4<T> acc = lam[m];

@@ -203,8 +203,8 @@ def test_fused_fp32_step_matches_plain_fp32_and_oracle(L, name):
 @pytest.mark.parametrize("name", ["small3d_J1", "ragged3d", "mid3d"])
 def test_fused_step_variants_agree(L, name):
     """Every variant of the fused 3D forward step (fixed through lks_step_variant) gives the
-    same run as variant 0 up to rounding, within the FP32 tolerances of the oracle; the
-    automatic choice picks one of them."""
+    same run as variant 0 up to rounding, within the FP32 tolerances of the oracle; variant 1 is
+    the default, and the timed choice picks one of them."""
     w = MID3D() if name == "mid3d" else CASES[name]()
     Jo, go = oracle.gradient(w.problem, w.gamma, w.motion)
     res = []
@@ -227,6 +227,9 @@ def test_fused_step_variants_agree(L, name):
     s = L.Solver(w.problem, L.FP32)
     s.set_design(w.gamma)
     s.set_motion(w.motion)
+    s.forward()
+    assert s.step_variant() == 1
+    assert s.step_variant(-1) == -1
     s.forward()
     assert s.step_variant() in (0, 1)
     with pytest.raises(L.LksError):
