@@ -414,12 +414,16 @@ __global__ void __launch_bounds__(NTHR, 4)
 template <int TY_>
 struct ZCfg {
     static constexpr int TX = 32, TY = TY_;
-    static constexpr int HX = TX + 4, HY = TY + 4, FX = TX + 2, FY = TY + 2;
-    static constexpr int NTHR = TX * TY, NHALO = FX * FY - TX * TY, FS = FX * FY;
+    // raw planes: TX + 4 columns with a row pitch of HX = TX + 5 (odd, so that column-strided
+    // accesses spread over all shared-memory banks; the TMA box is HX wide); f^eq region: FW
+    // columns with row pitch FX = FW + 1
+    static constexpr int HX = TX + 5, HY = TY + 4, FW = TX + 2, FX = FW + 1, FY = TY + 2;
+    static constexpr int NTHR = TX * TY, NHALO = FW * FY - TX * TY, FS = FX * FY;
     static constexpr int NSLOT = 5;
     static constexpr int MINB = 3;     // resident blocks per SM
-    static constexpr unsigned PLANE_BYTES = HX * HY * 16;
-    static constexpr size_t OFF_F = (size_t)NSLOT * PLANE_BYTES;
+    static constexpr unsigned PLANE_BYTES = HX * HY * 16;                 // one TMA box
+    static constexpr int SLOT = (PLANE_BYTES + 127) / 128 * 128 / 16;     // float4 per slot
+    static constexpr size_t OFF_F = (size_t)NSLOT * SLOT * 16;
     static constexpr size_t OFF_BAR = OFF_F + (size_t)2 * NCROSS * FS * 4;
     static constexpr size_t SMEM = OFF_BAR + NSLOT * 8;
 };
@@ -511,7 +515,7 @@ __device__ __forceinline__ void zbody(const CUtensorMap& tmap, const FusedArgs& 
                                       unsigned char* smem, int hfx, int hfy, int q0, int q1,
                                       int nplanes) {
     using C = ZCfg<TY_>;
-    constexpr int TX = C::TX, TY = C::TY, HX = C::HX, HY = C::HY, FX = C::FX;
+    constexpr int TX = C::TX, TY = C::TY, HX = C::HX, FX = C::FX;
     constexpr int FS = C::FS, NSLOT = C::NSLOT;
     float4* raw = reinterpret_cast<float4*>(smem);
     float* sFbase = reinterpret_cast<float*>(smem + C::OFF_F);
@@ -554,7 +558,7 @@ __device__ __forceinline__ void zbody(const CUtensorMap& tmap, const FusedArgs& 
         bool good = mbar_wait(smem_addr(&bars[0]), 0);
         good = mbar_wait(smem_addr(&bars[1]), 0) && good;
         const float4* r0 = raw;
-        const float4* r1 = raw + (size_t)HX * HY;
+        const float4* r1 = raw + (size_t)C::SLOT;
         const float4 v = r0[hp];
         um = make_float3(v.y, v.z, v.w);
         c0 = r1[hp];
@@ -571,8 +575,8 @@ __device__ __forceinline__ void zbody(const CUtensorMap& tmap, const FusedArgs& 
 
     for (int p = q0 - 1; ok && p <= q1; ++p) {
         const bool good = mbar_wait(smem_addr(&bars[wslot]), wpar);
-        const float4* r0 = raw + (size_t)s0 * HX * HY;
-        const float4* rp = raw + (size_t)wslot * HX * HY;
+        const float4* r0 = raw + (size_t)s0 * C::SLOT;
+        const float4* rp = raw + (size_t)wslot * C::SLOT;
         float* sF = sFbase + (size_t)((p - q0 + 1) & 1) * NCROSS * FS;
         float* sFp = sF + fop;
         const float4 cpn = rp[hp];
@@ -615,7 +619,7 @@ __device__ __forceinline__ void zbody(const CUtensorMap& tmap, const FusedArgs& 
         // every thread is past its reads of plane p - 1: its slot takes load k(p) - 1 + NSLOT
         if (tid == 0 && ik < nplanes) {
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            tma_load_box(smem_addr(raw + (size_t)islot * HX * HY), &tmap, x0 - 2, y0 - 2,
+            tma_load_box(smem_addr(raw + (size_t)islot * C::SLOT), &tmap, x0 - 2, y0 - 2,
                          q0 - 2 + ik, smem_addr(&bars[islot]), C::PLANE_BYTES);
         }
         ++ik;
@@ -688,7 +692,7 @@ template <int TY_>
 __global__ void __launch_bounds__(ZCfg<TY_>::NTHR, ZCfg<TY_>::MINB)
     k_zstep3d(const __grid_constant__ CUtensorMap tmap, const FusedArgs a) {
     using C = ZCfg<TY_>;
-    constexpr int TX = C::TX, TY = C::TY, HX = C::HX, HY = C::HY, FX = C::FX, FY = C::FY;
+    constexpr int TX = C::TX, TY = C::TY, FW = C::FW, FY = C::FY;
     constexpr int NSLOT = C::NSLOT;
     extern __shared__ __align__(128) unsigned char smem[];
     float4* raw = reinterpret_cast<float4*>(smem);
@@ -707,16 +711,16 @@ __global__ void __launch_bounds__(ZCfg<TY_>::NTHR, ZCfg<TY_>::MINB)
     const int rr = tid < C::NHALO ? tid : tid - (RIMW - C::NHALO);
     int hfx = 0, hfy = 0;   // threads past the rim warps keep (0, 0): they read, never store
     if (tid < RIMW) {
-        if (rr < FX) {
+        if (rr < FW) {
             hfx = rr;
-        } else if (rr < 2 * FX) {
-            hfx = rr - FX;
+        } else if (rr < 2 * FW) {
+            hfx = rr - FW;
             hfy = FY - 1;
-        } else if (rr < 2 * FX + TY) {
-            hfy = 1 + (rr - 2 * FX);
+        } else if (rr < 2 * FW + TY) {
+            hfy = 1 + (rr - 2 * FW);
         } else {
-            hfx = FX - 1;
-            hfy = 1 + (rr - 2 * FX - TY);
+            hfx = FW - 1;
+            hfy = 1 + (rr - 2 * FW - TY);
         }
     }
     if ((smem_addr(smem) & 127u) != 0u) {
@@ -727,7 +731,7 @@ __global__ void __launch_bounds__(ZCfg<TY_>::NTHR, ZCfg<TY_>::MINB)
         for (int s = 0; s < NSLOT; ++s) mbar_init(smem_addr(&bars[s]));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         for (int k = 0; k < NSLOT && k < nplanes; ++k)
-            tma_load_box(smem_addr(raw + (size_t)k * HX * HY), &tmap, x0 - 2, y0 - 2,
+            tma_load_box(smem_addr(raw + (size_t)k * C::SLOT), &tmap, x0 - 2, y0 - 2,
                          q0 - 2 + k, smem_addr(&bars[k]), C::PLANE_BYTES);
     }
     __syncthreads();

@@ -29,16 +29,19 @@ namespace {
 
 constexpr int TX = 32, TY = 8;
 constexpr int HX = TX + 4, HY = TY + 4;     // lambda tile with a two-cell halo
+constexpr int PX = HX + 1;                  // row pitch of a ring plane (odd: columns hit all banks)
 constexpr int FX = TX + 2, FY = TY + 2;     // moment region with a one-cell halo
+constexpr int PF = FX + 1;                  // row pitch of the S~ planes (odd)
 constexpr int NSLOT = 5;
 constexpr int NTHR = TX * TY;
 constexpr int NRIM1 = FX * FY - TX * TY;    // 84 rim nodes of the moment region
 constexpr int NRIM2 = HX * HY - TX * TY;    // 176 halo nodes to convert
 constexpr int NS = 5;                       // S~ components shared in-plane: xx xy xz yy yz
-constexpr unsigned PLANE_BYTES = HX * HY * 16;
+constexpr unsigned PLANE_BYTES = PX * HY * 16;   // bytes one TMA box delivers
+constexpr int SLOT = (PLANE_BYTES + 127) / 128 * 128 / 16;   // float4 per ring slot (128 B aligned)
 constexpr size_t OFF_RAW = 0;
-constexpr size_t OFF_S = OFF_RAW + (size_t)NSLOT * PLANE_BYTES;
-constexpr size_t OFF_BAR = OFF_S + (size_t)2 * NS * FX * FY * 4;
+constexpr size_t OFF_S = OFF_RAW + (size_t)NSLOT * SLOT * 16;
+constexpr size_t OFF_BAR = OFF_S + (size_t)2 * NS * PF * FY * 4;
 constexpr size_t SMEM_BYTES = OFF_BAR + NSLOT * 8;
 
 struct AdjArgs {
@@ -117,7 +120,7 @@ struct Mom {
 __device__ __forceinline__ Mom moments(const AdjArgs& a, const float4* __restrict__ c0,
                                        const float4* __restrict__ cm,
                                        const float4* __restrict__ cp) {
-    const float4 s = c0[0], xp = c0[1], xm = c0[-1], yp = c0[HX], ym = c0[-HX];
+    const float4 s = c0[0], xp = c0[1], xm = c0[-1], yp = c0[PX], ym = c0[-PX];
     const float4 zp = cp[0], zm = cm[0];
     const float gpx = xp.x + xp.y, gmx = xm.x - xm.y;
     const float gpy = yp.x + yp.z, gmy = ym.x - ym.z;
@@ -130,7 +133,7 @@ __device__ __forceinline__ Mom moments(const AdjArgs& a, const float4* __restric
         const float sz = jz == 0 ? 1.f : -1.f;
 #pragma unroll
         for (int jy = 0; jy < 2; ++jy) {
-            const int oy = jy == 0 ? HX : -HX;
+            const int oy = jy == 0 ? PX : -PX;
             const float sy = jy == 0 ? 1.f : -1.f;
             const float4 np = pl[oy + 1], nm = pl[oy - 1];
             const float base_p = np.x + sy * np.z + sz * np.w;
@@ -192,7 +195,7 @@ __global__ void __launch_bounds__(NTHR, 4)
             cx = (tid - 2 * HX) % HX;
             cy = HY - 2 + (tid - 2 * HX) / HX;
         } else {
-            const int t = tid - 4 * HX;   // 64 nodes: columns 0, 1, HX-2, HX-1 of rows 2..HY-3
+            const int t = tid - 4 * HX;   // 32 nodes: columns 0, 1, HX-2, HX-1 of rows 2..HY-3
             const int col = t / TY, row = t % TY;
             cx = col < 2 ? col : HX - 4 + col;
             cy = 2 + row;
@@ -219,7 +222,7 @@ __global__ void __launch_bounds__(NTHR, 4)
         for (int s = 0; s < NSLOT; ++s) mbar_init(smem_addr(&bars[s]));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         for (int k = 0; k < 2 && k < nplanes; ++k)
-            tma_load_box(smem_addr(raw + (size_t)k * HX * HY), &tmap, x0 - 2, y0 - 2,
+            tma_load_box(smem_addr(raw + (size_t)k * SLOT), &tmap, x0 - 2, y0 - 2,
                          q0 - 2 + k, smem_addr(&bars[k]), PLANE_BYTES);
     }
     __syncthreads();
@@ -229,12 +232,12 @@ __global__ void __launch_bounds__(NTHR, 4)
     const int cf_own = col_flags(g, gx, gy);
     const int cf_halo = col_flags(g, x0 - 2 + cx, y0 - 2 + cy);
     const bool has_obj = a.has_obj != 0;
-    const int hp = (ty + 2) * HX + (tx + 2);       // own node in the raw tile
-    const int hc = cy * HX + cx;                   // halo node to convert
-    const int hr = (rfy + 1) * HX + (rfx + 1);     // rim node of the moment region
-    constexpr int FS = FX * FY;
-    const int fo = (ty + 1) * FX + (tx + 1);
-    const int fr = rfy * FX + rfx;
+    const int hp = (ty + 2) * PX + (tx + 2);       // own node in the raw tile
+    const int hc = cy * PX + cx;                   // halo node to convert
+    const int hr = (rfy + 1) * PX + (rfx + 1);     // rim node of the moment region
+    constexpr int FS = PF * FY;
+    const int fo = (ty + 1) * PF + (tx + 1);
+    const int fr = rfy * PF + rfx;
     const long long zstride = (long long)nx * ny;
     const long long col = (long long)gy * nx + gx;
     const float A = a.A;
@@ -255,7 +258,7 @@ __global__ void __launch_bounds__(NTHR, 4)
         }
         if (tid == 0 && ik < nplanes) {
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            tma_load_box(smem_addr(raw + (size_t)islot * HX * HY), &tmap, x0 - 2, y0 - 2,
+            tma_load_box(smem_addr(raw + (size_t)islot * SLOT), &tmap, x0 - 2, y0 - 2,
                          q0 - 2 + ik, smem_addr(&bars[islot]), PLANE_BYTES);
         }
         ++ik;
@@ -267,7 +270,7 @@ __global__ void __launch_bounds__(NTHR, 4)
         if (write_out) u = a.sp[q * zstride + col];
         // 1. lambda -> mu for plane p + 1
         {
-            float4* pl = raw + (size_t)cslot * HX * HY;
+            float4* pl = raw + (size_t)cslot * SLOT;
             const int gz = p + 1;
             to_mu(a, pl[hp], cf_own, gx, gy, gz, own_in, has_obj);
             if (tid < NRIM2)
@@ -283,9 +286,9 @@ __global__ void __launch_bounds__(NTHR, 4)
         __syncthreads();
         if (p < q0 - 1) continue;
         // 2. moments of plane p on the tile and its rim
-        const float4* rm = raw + (size_t)sl_m * HX * HY;
-        const float4* r0 = raw + (size_t)sl_0 * HX * HY;
-        const float4* rp = raw + (size_t)sl_p * HX * HY;
+        const float4* rm = raw + (size_t)sl_m * SLOT;
+        const float4* r0 = raw + (size_t)sl_0 * SLOT;
+        const float4* rp = raw + (size_t)sl_p * SLOT;
         float* sw = sS + (size_t)(p & 1) * NS * FS;
         const Mom m = moments(a, r0 + hp, rm + hp, rp + hp);
         sw[0 * FS + fo] = m.Sxx;
@@ -308,9 +311,9 @@ __global__ void __launch_bounds__(NTHR, 4)
             const float tx_x = sr[0 * FS + fo - 1] - sr[0 * FS + fo + 1];
             const float tx_y = sr[1 * FS + fo - 1] - sr[1 * FS + fo + 1];
             const float tx_z = sr[2 * FS + fo - 1] - sr[2 * FS + fo + 1];
-            const float ty_x = sr[1 * FS + fo - FX] - sr[1 * FS + fo + FX];
-            const float ty_y = sr[3 * FS + fo - FX] - sr[3 * FS + fo + FX];
-            const float ty_z = sr[4 * FS + fo - FX] - sr[4 * FS + fo + FX];
+            const float ty_x = sr[1 * FS + fo - PF] - sr[1 * FS + fo + PF];
+            const float ty_y = sr[3 * FS + fo - PF] - sr[3 * FS + fo + PF];
+            const float ty_z = sr[4 * FS + fo - PF] - sr[4 * FS + fo + PF];
             const float tz_x = szm_x - m.Sxz, tz_y = szm_y - m.Syz, tz_z = szm_z - m.Szz;
             const Mom& c = prev;
             float4 o;
@@ -428,7 +431,8 @@ cudaError_t launch_fused_adj3d(const Geom& g, const V4<float>* lam_in, V4<float>
                                const V4<float>* kus, const V4<float>* sn, const V4<float>* sp,
                                float* e, float* face, double h, int* err, cudaStream_t st) {
     CUtensorMap map;
-    if (!encode_state_map(&map, lam_in, g, HX, HY)) return cudaErrorInvalidValue;
+    // a box one column wider than the tile: the unused last column pads the row pitch
+    if (!encode_state_map(&map, lam_in, g, PX, HY)) return cudaErrorInvalidValue;
     static bool attr = false;
     if (!attr) {
         cudaError_t r = cudaFuncSetAttribute(k_fused_adj3d,
