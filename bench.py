@@ -432,6 +432,7 @@ def run_ours(args):
                         "frac": ach_adj / peak, "traffic": ncu_traffic("adjoint_step"),
                         "kernel": "adjoint stencil step: k_adj_bcT + k_fused_adj3d + "
                                   "k_adj_bcorr",
+                        "concurrent": "the next step's transfer runs beside it on a side stream",
                         "peak_kind": f"{peak_kind} hbm_gbs (copy)",
                         "algorithmic_bytes_per_launch": bytes_adj,
                         "avg_launch_ms": adj_step_ms, "samples": tm["adj_n"]},
@@ -440,6 +441,8 @@ def run_ours(args):
                                 "kernel": "forward stencil step: " + STEP3D_KERNELS.get(
                                     solver.step_variant(), "?"),
                                 "variant": solver.step_variant(),
+                                "concurrent": "the next step's transfer runs beside it on a "
+                                              "side stream",
                                 "peak_kind": f"{peak_kind} hbm_gbs (copy)",
                                 "algorithmic_bytes_per_launch": bytes_fwd,
                                 "avg_launch_ms": fwd_step_ms, "samples": tm["fwd_n"]},

@@ -139,6 +139,22 @@ struct lks_ctx {
     int step3d_var = -1;         // variant in use (-1: not chosen yet)
     double axis[3] = {0.0, 0.0, 1.0};
     AxisScratch as;
+    // 3D transfers in two buffer sets: the current one (kus, k2, ts, as above point into it)
+    // and one the next step's transfer is prefetched into on a side stream
+    struct XSlot {
+        void* kus;
+        void* k2;
+        TransferScratch ts;
+        AxisScratch as;
+    } xs[2];
+    int xcur = 0;
+    bool pf_on = false;          // prefetching enabled (3D with a design grid)
+    int cur_step = -1;           // step whose transfer the current set holds (-1: none)
+    int pf_step = -1;            // step being prefetched into the other set (-1: none)
+    int pf_last = -1;            // step of the previous transfer request
+    int pf_dir = 0;              // direction of the run at that request (+1, -1, 0)
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_main = nullptr, ev_pf = nullptr;
     // design chain: density filter radius (0 = off), projection steepness and threshold
     double fR = 0.0, fbeta = 1.0, feta = 0.5;
     double* gbar = nullptr;      // projected field the solver sees
@@ -302,7 +318,7 @@ double count_target(const lks_config* c) {
 }
 
 struct Layout {
-    size_t off[64];
+    size_t off[96];
     size_t total;
     int pool_slots;
     size_t snap;
@@ -313,10 +329,14 @@ enum {
     L_GACC, L_JSTEP, L_CBASE, L_CFRAC, L_ZTI, L_ZTW, L_TCNT, L_TIDX, L_TW, L_CM, L_DZB, L_DZF,
     L_FLAGS, L_KREFT, L_K2, L_FACE, L_TGT, L_U3, L_MOTION, L_BUFS, L_INST, L_PRE, L_GBAR,
     L_HP, L_FWS, L_GOUT, L_GTMP, L_SCAL, L_CSC, L_KS, L_SEND, L_LEND, L_GBASE, L_GFRAC,
-    L_GCNT, L_GIDX, L_POOL,
+    L_GCNT, L_GIDX,
+    // the second transfer buffer set (3D): same sizes as L_KUS, L_K2, L_CBASE, ...
+    L_KUS2, L_K22, L_CBASE2, L_CFRAC2, L_CSC2, L_ZTI2, L_ZTW2, L_TCNT2, L_TIDX2, L_TW2, L_CM2,
+    L_DZB2, L_DZF2, L_GBASE2, L_GFRAC2, L_GCNT2, L_GIDX2,
+    L_POOL,
     L_COUNT
 };
-static_assert(L_COUNT <= 64, "Layout::off holds 64 regions");
+static_assert(L_COUNT <= 96, "Layout::off holds 96 regions");
 
 Layout make_layout(const lks_config* cfg) {
     Layout L;
@@ -390,6 +410,12 @@ Layout make_layout(const lks_config* cfg) {
     {
         const long long n0 = cfg->nx, n1 = cfg->ny, n2 = dim == 3 ? cfg->nz : 1;
         sz[L_FACE] = (size_t)6 * (n1 * n2 + n0 * n2 + n0 * n1) * 4;
+    }
+    {   // second transfer set for the prefetch of the next step's transfer (3D only)
+        const bool two = dim == 3 && nd > 0;
+        const int first[17] = {L_KUS, L_K2, L_CBASE, L_CFRAC, L_CSC, L_ZTI, L_ZTW, L_TCNT,
+                               L_TIDX, L_TW, L_CM, L_DZB, L_DZF, L_GBASE, L_GFRAC, L_GCNT, L_GIDX};
+        for (int i = 0; i < 17; ++i) sz[L_KUS2 + i] = two ? sz[first[i]] : 0;
     }
     sz[L_POOL] = (size_t)P * state;
     size_t off = 0;
@@ -496,6 +522,55 @@ Motion motion_row(const lks_ctx* c, int n) {
 
 // ---------------------------------------------------------------- single-context steps
 
+// The transfer of step n into buffer set x on stream st (3D and plain 2D paths).
+template <class T>
+lks_status transfer_into(lks_ctx* c, int n, const lks_ctx::XSlot& x, cudaStream_t st) {
+    const Motion m = motion_row(c, n);
+    if (c->gaxis) {
+        launch_transfer_axis<T>(c->d, c->g, m, x.as, (const T*)c->kref, st4<T>(x.kus), st);
+        LAUNCHED();
+        c->stats[4] += 2;
+        return LKS_OK;
+    }
+    launch_design_pos<T>(c->d, c->g, m, x.ts, st);
+    LAUNCHED();
+    launch_transfer<T>(c->d, c->g, m, x.ts, (const T*)c->kref_t, (T*)x.k2, st4<T>(x.kus), st);
+    LAUNCHED();
+    return LKS_OK;
+}
+
+void use_set(lks_ctx* c, int i) {
+    c->xcur = i;
+    c->kus = c->xs[i].kus;
+    c->k2 = c->xs[i].k2;
+    c->ts = c->xs[i].ts;
+    c->as = c->xs[i].as;
+}
+
+// The context's stream waits for any prefetch in flight, which is dropped; the current set
+// keeps its step.
+lks_status transfer_settle(lks_ctx* c) {
+    if (c->pf_step >= 0) CU(cudaStreamWaitEvent(c->st, c->ev_pf, 0));
+    c->pf_step = -1;
+    return LKS_OK;
+}
+
+// Settle and forget the current set too: no side work outlives a run, and the next run
+// (after a possible change of design or motion) starts from fresh transfers.
+lks_status transfer_join(lks_ctx* c) {
+    lks_status s = transfer_settle(c);
+    c->cur_step = -1;
+    c->pf_last = -1;
+    c->pf_dir = 0;
+    return s;
+}
+
+// kappa and u_S of step n in the current buffer set.  3D: the transfer depends on the motion
+// and the design only, so while the step n kernels run, the transfer of the step the run is
+// heading to (n + 1 going forward, n - 1 going backward) is computed into the other set on a
+// side stream, ordered by events; a later request for that step swaps the sets.  A request for
+// the step the current set already holds (the adjoint's first step after a tape segment)
+// launches nothing.
 template <class T>
 lks_status transfer_at(lks_ctx* c, int n) {
     if (c->d.nd == 0 || c->g.boxN == 0) return LKS_OK;
@@ -506,18 +581,39 @@ lks_status transfer_at(lks_ctx* c, int n) {
         c->stats[4] += 3;
         return LKS_OK;
     }
-    const Motion m = motion_row(c, n);
-    if (c->gaxis) {
-        launch_transfer_axis<T>(c->d, c->g, m, c->as, (const T*)c->kref, st4<T>(c->kus), c->st);
-        LAUNCHED();
-        c->stats[4] += 2;
-        return LKS_OK;
+    if (!c->pf_on) return transfer_into<T>(c, n, c->xs[c->xcur], c->st);
+    if (!c->side) {
+        CU(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+        CU(cudaEventCreateWithFlags(&c->ev_main, cudaEventDisableTiming));
+        CU(cudaEventCreateWithFlags(&c->ev_pf, cudaEventDisableTiming));
     }
-    launch_design_pos<T>(c->d, c->g, m, c->ts, c->st);
-    LAUNCHED();
-    launch_transfer<T>(c->d, c->g, m, c->ts, (const T*)c->kref_t, (T*)c->k2, st4<T>(c->kus),
-                       c->st);
-    LAUNCHED();
+    if (c->pf_step == n) {
+        CU(cudaStreamWaitEvent(c->st, c->ev_pf, 0));
+        use_set(c, 1 - c->xcur);
+        c->pf_step = -1;
+    } else if (c->cur_step != n) {
+        lks_status s = transfer_into<T>(c, n, c->xs[c->xcur], c->st);
+        if (s != LKS_OK) return s;
+    }
+    c->cur_step = n;
+    // direction of the run: one step on from the previous request, or the same step again (a
+    // tape segment's last step, then the adjoint of that segment: the run turns around)
+    int dir = 0;
+    if (c->pf_last >= 0 && std::abs(n - c->pf_last) == 1) dir = n - c->pf_last;
+    else if (c->pf_last == n) dir = -c->pf_dir;
+    c->pf_dir = dir;
+    c->pf_last = n;
+    const int next = n + dir;
+    if (dir != 0 && next >= 1 && next <= c->cfg.max_steps && c->pf_step != next) {
+        // a stale prefetch still in flight is overwritten after it, in side-stream order
+        // the other set was last read by work already on the context's stream
+        CU(cudaEventRecord(c->ev_main, c->st));
+        CU(cudaStreamWaitEvent(c->side, c->ev_main, 0));
+        lks_status s = transfer_into<T>(c, next, c->xs[1 - c->xcur], c->side);
+        if (s != LKS_OK) return s;
+        CU(cudaEventRecord(c->ev_pf, c->side));
+        c->pf_step = next;
+    }
     return LKS_OK;
 }
 
@@ -951,6 +1047,10 @@ lks_status do_forward(Group& G, int N) {
         c->work_level = -1;
         c->last = nullptr;
         c->fwd_valid = false;
+        {
+            lks_status s = transfer_join(c);
+            if (s != LKS_OK) return s;
+        }
         CU(cudaMemsetAsync(c->jstep, 0, (size_t)(c->cfg.max_steps + 2) * 8, G.st));
         CU(cudaMemsetAsync(c->flags, 0, 64, G.st));
     }
@@ -965,6 +1065,8 @@ lks_status do_forward(Group& G, int N) {
     std::vector<int> fl(4 * (size_t)G.count);
     for (int k = 0; k < G.count; ++k) {
         lks_ctx* c = G.cs[k];
+        lks_status st = transfer_settle(c);   // the adjoint may reuse the last step's transfer
+        if (st != LKS_OK) return st;
         c->adj_begin = i + 1;
         js[k].assign(c->cfg.max_steps + 2, 0.0);
         CU(cudaMemcpyAsync(js[k].data(), c->jstep, js[k].size() * 8, cudaMemcpyDeviceToHost, G.st));
@@ -1023,6 +1125,10 @@ lks_status do_adjoint(Group& G) {
     for (int k = 0; k < G.count; ++k) {
         lks_ctx* c = G.cs[k];
         c->fwd_valid = false;
+        {
+            lks_status st = transfer_join(c);
+            if (st != LKS_OK) return st;
+        }
         CU(cudaMemcpyAsync(c->l_end, c->lam[c->lam_par], c->snap_bytes, cudaMemcpyDeviceToDevice,
                            G.st));
         c->have_lend = true;
@@ -1321,6 +1427,33 @@ lks_status lks_create(const lks_config* cfg, void* workspace, size_t ws_bytes, l
     c->as.frac = w + L.off[L_GFRAC];
     c->as.cnt = (int*)(w + L.off[L_GCNT]);
     c->as.idx = (int*)(w + L.off[L_GIDX]);
+    {   // the two transfer sets
+        lks_ctx::XSlot& a = c->xs[0];
+        a.kus = c->kus;
+        a.k2 = c->k2;
+        a.ts = c->ts;
+        a.as = c->as;
+        lks_ctx::XSlot& b = c->xs[1];
+        b.kus = w + L.off[L_KUS2];
+        b.k2 = w + L.off[L_K22];
+        b.ts = c->ts;
+        b.ts.col_base = (int*)(w + L.off[L_CBASE2]);
+        b.ts.col_frac = w + L.off[L_CFRAC2];
+        b.ts.col_sc = (float4*)(w + L.off[L_CSC2]);
+        b.ts.zt_idx = (int*)(w + L.off[L_ZTI2]);
+        b.ts.zt_w = w + L.off[L_ZTW2];
+        b.ts.tap_cnt = (int*)(w + L.off[L_TCNT2]);
+        b.ts.tap_idx = (int*)(w + L.off[L_TIDX2]);
+        b.ts.tap_w = w + L.off[L_TW2];
+        b.ts.col_m = w + L.off[L_CM2];
+        b.ts.dz_base = (int*)(w + L.off[L_DZB2]);
+        b.ts.dz_frac = w + L.off[L_DZF2];
+        b.as.base = (int4*)(w + L.off[L_GBASE2]);
+        b.as.frac = w + L.off[L_GFRAC2];
+        b.as.cnt = (int*)(w + L.off[L_GCNT2]);
+        b.as.idx = (int*)(w + L.off[L_GIDX2]);
+        c->pf_on = cfg->dim == 3 && c->d.nd > 0;
+    }
     c->s_end = w + L.off[L_SEND];
     c->l_end = w + L.off[L_LEND];
     c->nbase = c->flags + 8;
@@ -1623,7 +1756,12 @@ lks_status lks_transfer(lks_ctx* c, int step, double* kappa_out, double* us_out)
         std::fill(us_out, us_out + 3 * nodes, 0.0);
         return LKS_OK;
     }
+    {   // a fresh transfer into the current set, with nothing left in flight afterwards
+        lks_status sj = transfer_join(c);
+        if (sj != LKS_OK) return sj;
+    }
     lks_status s = c->prec == LKS_FP64 ? transfer_at<double>(c, step) : transfer_at<float>(c, step);
+    if (s == LKS_OK) s = transfer_join(c);
     if (s != LKS_OK) return s;
     double* tmp = nullptr;
     CU(cudaMalloc(&tmp, nodes * 4 * 8));
@@ -1705,6 +1843,12 @@ void lks_destroy(lks_ctx* c) {
     if (!c) return;
     for (int w = 0; w < 2; ++w)
         for (cudaEvent_t e : c->tev[w]) cudaEventDestroy(e);
+    if (c->side) {
+        cudaStreamSynchronize(c->side);
+        cudaStreamDestroy(c->side);
+        cudaEventDestroy(c->ev_main);
+        cudaEventDestroy(c->ev_pf);
+    }
     if (c->own_ws && c->ws) cudaFree(c->ws);
     delete c;
 }
