@@ -154,7 +154,12 @@ struct lks_ctx {
     int pf_last = -1;            // step of the previous transfer request
     int pf_dir = 0;              // direction of the run at that request (+1, -1, 0)
     cudaStream_t side = nullptr;
-    cudaEvent_t ev_main = nullptr, ev_pf = nullptr;
+    cudaEvent_t ev_main = nullptr, ev_pf = nullptr, ev_join = nullptr;
+    // the sensitivity gather of a 3D adjoint step runs on the side stream too, reading e from
+    // one of two buffers while the next step writes the other
+    void* ebuf[2] = {nullptr, nullptr};
+    int epar = 0;
+    cudaEvent_t ev_adj = nullptr, ev_sens[2] = {nullptr, nullptr};
     // design chain: density filter radius (0 = off), projection steepness and threshold
     double fR = 0.0, fbeta = 1.0, feta = 0.5;
     double* gbar = nullptr;      // projected field the solver sees
@@ -332,7 +337,7 @@ enum {
     L_GCNT, L_GIDX,
     // the second transfer buffer set (3D): same sizes as L_KUS, L_K2, L_CBASE, ...
     L_KUS2, L_K22, L_CBASE2, L_CFRAC2, L_CSC2, L_ZTI2, L_ZTW2, L_TCNT2, L_TIDX2, L_TW2, L_CM2,
-    L_DZB2, L_DZF2, L_GBASE2, L_GFRAC2, L_GCNT2, L_GIDX2,
+    L_DZB2, L_DZF2, L_GBASE2, L_GFRAC2, L_GCNT2, L_GIDX2, L_E2,
     L_POOL,
     L_COUNT
 };
@@ -416,6 +421,7 @@ Layout make_layout(const lks_config* cfg) {
         const int first[17] = {L_KUS, L_K2, L_CBASE, L_CFRAC, L_CSC, L_ZTI, L_ZTW, L_TCNT,
                                L_TIDX, L_TW, L_CM, L_DZB, L_DZF, L_GBASE, L_GFRAC, L_GCNT, L_GIDX};
         for (int i = 0; i < 17; ++i) sz[L_KUS2 + i] = two ? sz[first[i]] : 0;
+        sz[L_E2] = two ? sz[L_E] : 0;
     }
     sz[L_POOL] = (size_t)P * state;
     size_t off = 0;
@@ -547,10 +553,13 @@ void use_set(lks_ctx* c, int i) {
     c->as = c->xs[i].as;
 }
 
-// The context's stream waits for any prefetch in flight, which is dropped; the current set
-// keeps its step.
+// The context's stream waits for all side-stream work (prefetches, sensitivity gathers); a
+// prefetch in flight is dropped, the current set keeps its step.
 lks_status transfer_settle(lks_ctx* c) {
-    if (c->pf_step >= 0) CU(cudaStreamWaitEvent(c->st, c->ev_pf, 0));
+    if (c->side) {
+        CU(cudaEventRecord(c->ev_join, c->side));
+        CU(cudaStreamWaitEvent(c->st, c->ev_join, 0));
+    }
     c->pf_step = -1;
     return LKS_OK;
 }
@@ -586,12 +595,20 @@ lks_status transfer_at(lks_ctx* c, int n) {
         CU(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
         CU(cudaEventCreateWithFlags(&c->ev_main, cudaEventDisableTiming));
         CU(cudaEventCreateWithFlags(&c->ev_pf, cudaEventDisableTiming));
+        CU(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
+        CU(cudaEventCreateWithFlags(&c->ev_adj, cudaEventDisableTiming));
+        CU(cudaEventCreateWithFlags(&c->ev_sens[0], cudaEventDisableTiming));
+        CU(cudaEventCreateWithFlags(&c->ev_sens[1], cudaEventDisableTiming));
     }
     if (c->pf_step == n) {
         CU(cudaStreamWaitEvent(c->st, c->ev_pf, 0));
         use_set(c, 1 - c->xcur);
         c->pf_step = -1;
     } else if (c->cur_step != n) {
+        // the current set may still be read by a sensitivity gather on the side stream (a run
+        // that changed direction or jumped): wait for the side stream before overwriting it
+        CU(cudaEventRecord(c->ev_join, c->side));
+        CU(cudaStreamWaitEvent(c->st, c->ev_join, 0));
         lks_status s = transfer_into<T>(c, n, c->xs[c->xcur], c->st);
         if (s != LKS_OK) return s;
     }
@@ -702,6 +719,11 @@ lks_status adjoint_step(lks_ctx* c, int n, const void* sn, const void* sp) {
     if (s != LKS_OK) return s;
     V4<T>* lc = st4<T>(c->lam[c->lam_par]);
     V4<T>* ln = st4<T>(c->lam[1 - c->lam_par]);
+    const bool side_sens = c->pf_on && c->side && c->d.nd > 0 && c->g.boxN > 0;
+    if (side_sens) {   // e alternates between two buffers; wait for the gather that read this one
+        c->e = c->ebuf[c->epar];
+        CU(cudaStreamWaitEvent(c->st, c->ev_sens[c->epar], 0));
+    }
     const bool tm = timing_begin(c, n, 1);
     launch_adj_bcT<T>(c->g, lc, hn, c->st);
     LAUNCHED();
@@ -724,13 +746,24 @@ lks_status adjoint_step(lks_ctx* c, int n, const void* sn, const void* sp) {
     }
     if (tm) timing_end(c, 1);
     if (c->d.nd > 0 && c->g.boxN > 0) {
+        // on the side stream (3D): after this step's adjoint kernels, before the prefetch that
+        // will next overwrite this step's transfer set; dJ/dgamma sums stay in step order
+        cudaStream_t ss = c->st;
+        if (side_sens) {
+            CU(cudaEventRecord(c->ev_adj, c->st));
+            CU(cudaStreamWaitEvent(c->side, c->ev_adj, 0));
+            ss = c->side;
+        }
         if (c->gaxis)
             launch_sens_axis<T>(c->d, c->g, c->as, (const T*)c->e, (const T*)c->kprime, c->gacc,
-                                c->st);
+                                ss);
         else
-            launch_sens<T>(c->d, c->g, c->ts, (const T*)c->e, (const T*)c->kprime, c->gacc,
-                           c->st);
+            launch_sens<T>(c->d, c->g, c->ts, (const T*)c->e, (const T*)c->kprime, c->gacc, ss);
         LAUNCHED();
+        if (side_sens) {
+            CU(cudaEventRecord(c->ev_sens[c->epar], c->side));
+            c->epar ^= 1;
+        }
     }
     c->lam_par ^= 1;
     return LKS_OK;
@@ -1453,6 +1486,8 @@ lks_status lks_create(const lks_config* cfg, void* workspace, size_t ws_bytes, l
         b.as.cnt = (int*)(w + L.off[L_GCNT2]);
         b.as.idx = (int*)(w + L.off[L_GIDX2]);
         c->pf_on = cfg->dim == 3 && c->d.nd > 0;
+        c->ebuf[0] = c->e;
+        c->ebuf[1] = w + L.off[L_E2];
     }
     c->s_end = w + L.off[L_SEND];
     c->l_end = w + L.off[L_LEND];
@@ -1846,8 +1881,9 @@ void lks_destroy(lks_ctx* c) {
     if (c->side) {
         cudaStreamSynchronize(c->side);
         cudaStreamDestroy(c->side);
-        cudaEventDestroy(c->ev_main);
-        cudaEventDestroy(c->ev_pf);
+        for (cudaEvent_t e : {c->ev_main, c->ev_pf, c->ev_join, c->ev_adj, c->ev_sens[0],
+                              c->ev_sens[1]})
+            cudaEventDestroy(e);
     }
     if (c->own_ws && c->ws) cudaFree(c->ws);
     delete c;
