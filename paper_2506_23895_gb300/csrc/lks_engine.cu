@@ -160,6 +160,12 @@ struct lks_ctx {
     void* ebuf[2] = {nullptr, nullptr};
     int epar = 0;
     cudaEvent_t ev_adj = nullptr, ev_sens[2] = {nullptr, nullptr};
+    // forward and adjoint runs of a 3D context execute on an internal stream of the highest
+    // priority, forked from and joined back to the caller's stream, so that the stencil blocks
+    // win the block scheduler and the side-stream work fills the gaps
+    cudaStream_t run_st = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_back = nullptr;
+    cudaStream_t user_st = nullptr;
     // design chain: density filter radius (0 = off), projection steepness and threshold
     double fR = 0.0, fbeta = 1.0, feta = 0.5;
     double* gbar = nullptr;      // projected field the solver sees
@@ -553,6 +559,45 @@ void use_set(lks_ctx* c, int i) {
     c->as = c->xs[i].as;
 }
 
+// The streams and events of a 3D context's overlapped work, created once: the run stream at
+// the highest priority, the side stream at the lowest.
+lks_status ensure_streams(lks_ctx* c) {
+    if (c->run_st) return LKS_OK;
+    int least = 0, greatest = 0;
+    CU(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+    CU(cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, least));
+    for (cudaEvent_t* e : {&c->ev_main, &c->ev_pf, &c->ev_join, &c->ev_adj, &c->ev_sens[0],
+                           &c->ev_sens[1], &c->ev_fork, &c->ev_back})
+        CU(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+    CU(cudaStreamCreateWithPriority(&c->run_st, cudaStreamNonBlocking, greatest));
+    return LKS_OK;
+}
+
+// Fork a 3D context's run onto its high-priority stream (after the work on the caller's
+// stream) and join it back afterwards.
+lks_status run_fork(lks_ctx* c) {
+    c->user_st = c->st;
+    if (!c->pf_on) return LKS_OK;
+    lks_status s = ensure_streams(c);
+    if (s != LKS_OK) return s;
+    CU(cudaEventRecord(c->ev_fork, c->user_st));
+    CU(cudaStreamWaitEvent(c->run_st, c->ev_fork, 0));
+    c->st = c->run_st;
+    return LKS_OK;
+}
+
+lks_status run_join(lks_ctx* c, lks_status s) {
+    if (c->pf_on && c->st == c->run_st && c->run_st) {
+        cudaError_t e1 = cudaEventRecord(c->ev_back, c->run_st);
+        cudaError_t e2 = cudaStreamWaitEvent(c->user_st, c->ev_back, 0);
+        c->st = c->user_st;
+        if (s == LKS_OK && (e1 != cudaSuccess || e2 != cudaSuccess))
+            return fail(c, LKS_ERR_CUDA, "join of the run's stream failed");
+    }
+    c->st = c->user_st;
+    return s;
+}
+
 // The context's stream waits for all side-stream work (prefetches, sensitivity gathers); a
 // prefetch in flight is dropped, the current set keeps its step.
 lks_status transfer_settle(lks_ctx* c) {
@@ -591,14 +636,9 @@ lks_status transfer_at(lks_ctx* c, int n) {
         return LKS_OK;
     }
     if (!c->pf_on) return transfer_into<T>(c, n, c->xs[c->xcur], c->st);
-    if (!c->side) {
-        CU(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
-        CU(cudaEventCreateWithFlags(&c->ev_main, cudaEventDisableTiming));
-        CU(cudaEventCreateWithFlags(&c->ev_pf, cudaEventDisableTiming));
-        CU(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
-        CU(cudaEventCreateWithFlags(&c->ev_adj, cudaEventDisableTiming));
-        CU(cudaEventCreateWithFlags(&c->ev_sens[0], cudaEventDisableTiming));
-        CU(cudaEventCreateWithFlags(&c->ev_sens[1], cudaEventDisableTiming));
+    {
+        lks_status s = ensure_streams(c);
+        if (s != LKS_OK) return s;
     }
     if (c->pf_step == n) {
         CU(cudaStreamWaitEvent(c->st, c->ev_pf, 0));
@@ -1738,9 +1778,12 @@ lks_status lks_forward(lks_ctx* c, int n_steps, double* J_out) {
     if (n_steps < 1 || n_steps > c->cfg.max_steps)
         return fail(c, LKS_ERR_ARG, "n_steps must be in [1, max_steps]");
     c->fwd_valid = false;
+    lks_status s = run_fork(c);
+    if (s != LKS_OK) return run_join(c, s);
     Group G = self_group(c);
-    lks_status s = c->prec == LKS_FP64 ? do_forward<double>(G, n_steps) : do_forward<float>(G, n_steps);
+    s = c->prec == LKS_FP64 ? do_forward<double>(G, n_steps) : do_forward<float>(G, n_steps);
     c->stats[4] += G.launches;
+    s = run_join(c, s);
     if (s != LKS_OK) return s;
     if (J_out) *J_out = c->J;
     return LKS_OK;
@@ -1749,9 +1792,12 @@ lks_status lks_forward(lks_ctx* c, int n_steps, double* J_out) {
 lks_status lks_adjoint(lks_ctx* c, double* dJdgamma, int on_device) {
     if (!c) return LKS_ERR_ARG;
     if (!c->fwd_valid) return fail(c, LKS_ERR_ORDER, "adjoint needs a preceding forward run");
+    lks_status s = run_fork(c);
+    if (s != LKS_OK) return run_join(c, s);
     Group G = self_group(c);
-    lks_status s = c->prec == LKS_FP64 ? do_adjoint<double>(G) : do_adjoint<float>(G);
+    s = c->prec == LKS_FP64 ? do_adjoint<double>(G) : do_adjoint<float>(G);
     c->stats[4] += G.launches;
+    s = run_join(c, s);
     if (s != LKS_OK) return s;
     if (c->d.nd > 0 && dJdgamma) {
         CU(cudaMemcpyAsync(dJdgamma, design_gradient(c, c->st), (size_t)c->d.nd * 8,
@@ -1878,11 +1924,13 @@ void lks_destroy(lks_ctx* c) {
     if (!c) return;
     for (int w = 0; w < 2; ++w)
         for (cudaEvent_t e : c->tev[w]) cudaEventDestroy(e);
-    if (c->side) {
+    if (c->run_st) {
+        cudaStreamSynchronize(c->run_st);
         cudaStreamSynchronize(c->side);
+        cudaStreamDestroy(c->run_st);
         cudaStreamDestroy(c->side);
         for (cudaEvent_t e : {c->ev_main, c->ev_pf, c->ev_join, c->ev_adj, c->ev_sens[0],
-                              c->ev_sens[1]})
+                              c->ev_sens[1], c->ev_fork, c->ev_back})
             cudaEventDestroy(e);
     }
     if (c->own_ws && c->ws) cudaFree(c->ws);
