@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the batched 2D workload leg")
     ap.add_argument("--batch-horizon", type=int, default=5000)
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the other named workloads (128^2 FP64, 512^2 FP32, 128^3 FP32)")
     ap.add_argument("--workload", choices=["cfg4", "batch2d"], default="cfg4",
                     help="cfg4: the 256^3 3D line (default); batch2d: the batched 2D workload")
     return ap.parse_args()
@@ -297,6 +299,45 @@ def batch2d_leg(args, lks, W, stream, passes=1, warmup=1, clocks=None):
     return res
 
 
+def config_leg(lks, W, idx, prec, stream):
+    """One full forward + adjoint pass of named workload idx (after one untimed pass), timed with
+    CUDA events on the solver's stream: forward and forward+adjoint MLUPS."""
+    import torch
+
+    w = W.config(idx)
+    p = w.problem
+    s = lks.Solver(p, prec, stream=stream)
+    s.set_motion(w.motion)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    g_dev = torch.from_numpy(w.gamma).to(dev)
+    out = torch.empty(w.gamma.shape, dtype=torch.float64, device=dev)
+    s.set_design(g_dev)
+    s.forward()
+    s.adjoint(out=out)
+    torch.cuda.synchronize()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    e[0].record()
+    s.set_design(g_dev)
+    J = s.forward()
+    e[1].record()
+    s.adjoint(out=out)
+    e[2].record()
+    torch.cuda.synchronize()
+    st = s.stats()
+    s.close()
+    del s
+    torch.cuda.empty_cache()
+    node_steps = p.nodes * p.n_steps
+    return {"workload": f"{p.name}: {'D2Q9' if p.dim == 2 else 'D3Q15'} "
+                        f"{'x'.join(str(n) for n in p.n[:p.dim])}, design "
+                        f"{'x'.join(str(l) for l in p.L[:p.dim])}, {p.n_steps} steps",
+            "dtype": "f64" if prec == lks.FP64 else "f32", "unit": UNIT,
+            "value": node_steps / (e[0].elapsed_time(e[2]) / 1000.0) / 1e6,
+            "forward_mlups": node_steps / (e[0].elapsed_time(e[1]) / 1000.0) / 1e6,
+            "ms_per_pass": e[0].elapsed_time(e[2]), "J": J,
+            "recomputed_steps": st["recomputed_steps"], "snapshot_slots": st["snapshot_slots"]}
+
+
 def run_batch_line(args, lks, W, ws, rank, local, dev):
     """--workload batch2d: the batched 2D workload as the measured line (replicas for N > 1)."""
     import torch
@@ -505,6 +546,12 @@ def run_ours(args):
             "tolerance": {"J_rel": 1e-5, "dJdgamma_rel_l2": 1e-4}}
     if rank == 0 and not args.no_batch:
         out["batch2d"] = batch2d_leg(args, lks, W, stream)
+    if rank == 0 and not args.no_configs:
+        # the other named workloads, one pass each (not the metric's configuration)
+        out["other_configs"] = {
+            "cfg0_2d_128_fp64": config_leg(lks, W, 0, lks.FP64, stream),
+            "cfg1_2d_512_fp32": config_leg(lks, W, 1, lks.FP32, stream),
+            "cfg3_3d_128_fp32": config_leg(lks, W, 3, lks.FP32, stream)}
     if rank == 0:
         if ws == 1 and not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(4, n_steps=2)
