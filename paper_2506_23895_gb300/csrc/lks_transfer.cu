@@ -165,15 +165,44 @@ __global__ void k_col_planes(Design d, Geom g, TransferScratch ts, const T* __re
 }
 
 // Stage 2: kappa = sum over the z taps of w_z K2 and u_S = m_z (omega R'(theta) m1 + u_G m0)
-// on every node of the footprint box (u_ref is affine in xi, Eq. rigid_body_velocity).
+// on every node of the footprint box (u_ref is affine in xi, Eq. rigid_body_velocity).  A block
+// covers 32 box columns x 8 box planes; the K2 values those planes need (a window of at most
+// 11 consecutive zeta, the z map being a translation) are staged in shared memory with
+// contiguous reads along zeta, so that the node loop reads no strided global data.
+constexpr int kFillCols = 32, kFillPlanes = 8, kFillSpan = kFillPlanes + 3;
+
 template <class T>
-__global__ void k_fill(Design d, Geom g, Motion m, TransferScratch ts, const T* __restrict__ k2,
-                       V4<T>* __restrict__ kus) {
-    long long bi = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (bi >= g.boxN) return;
+__global__ void __launch_bounds__(kFillCols * kFillPlanes)
+    k_fill(Design d, Geom g, Motion m, TransferScratch ts, const T* __restrict__ k2,
+           V4<T>* __restrict__ kus) {
+    __shared__ T sk[kFillCols][kFillSpan + 1];
+    __shared__ int zlo_s;
     const long long ncols = (long long)g.bn[0] * g.bn[1];
-    const long long col = (unsigned)bi % (unsigned)ncols;
-    const int bz = (int)((unsigned)bi / (unsigned)ncols);
+    const int lc = threadIdx.x % kFillCols, lb = threadIdx.x / kFillCols;
+    const long long col0 = (long long)blockIdx.x * kFillCols;
+    const int bz0 = blockIdx.y * kFillPlanes;
+    if (threadIdx.x == 0) {   // lowest design plane any of the block's box planes reads
+        int lo = 1 << 30;
+        for (int b = bz0; b < min(bz0 + kFillPlanes, g.bn[2]); ++b)
+            for (int t = 0; t < 4; ++t) {
+                const int z = ts.zt_idx[4 * b + t];
+                if (z >= 0) lo = min(lo, z);
+            }
+        zlo_s = lo;
+    }
+    __syncthreads();
+    const int zlo = zlo_s;
+    for (int i = threadIdx.x; i < kFillCols * kFillSpan; i += blockDim.x) {
+        const int c = i / kFillSpan, z = i % kFillSpan;
+        const long long col = col0 + c;
+        T v = (T)0;
+        if (col < ncols && zlo + z < d.L[2]) v = k2[col * d.L[2] + zlo + z];
+        sk[c][z] = v;
+    }
+    __syncthreads();
+    const long long col = col0 + lc;
+    const int bz = bz0 + lb;
+    if (col >= ncols || bz >= g.bn[2]) return;
     const int* zi = ts.zt_idx + 4 * bz;
     const T* zw = (const T*)ts.zt_w + 4 * bz;
     T kap = (T)0, mz = (T)0;
@@ -181,7 +210,9 @@ __global__ void k_fill(Design d, Geom g, Motion m, TransferScratch ts, const T* 
         const int zeta = zi[t];
         if (zeta < 0) continue;
         mz += zw[t];
-        kap += zw[t] * k2[col * d.L[2] + zeta];
+        const int r = zeta - zlo;
+        const T kz = (r < kFillSpan) ? sk[lc][r] : k2[col * d.L[2] + zeta];
+        kap += zw[t] * kz;
     }
     const T* cm = (const T*)ts.col_m + 3 * col;
     // single-precision motion fields for T = float (the same roundings as converting here)
@@ -194,7 +225,7 @@ __global__ void k_fill(Design d, Geom g, Motion m, TransferScratch ts, const T* 
     o.x = mz * ((-s * cm[1] - c * cm[2]) * om + ug0 * cm[0]);
     o.y = mz * ((c * cm[1] - s * cm[2]) * om + ug1 * cm[0]);
     o.z = (g.dim == 3) ? mz * (ug2 * cm[0]) : (T)0;
-    kus[bi] = o;
+    kus[(long long)bz * ncols + col] = o;
 }
 
 // Sensitivity gather: one thread per design column and kSensRun planes (sens_run).
@@ -354,7 +385,9 @@ void launch_transfer(const Design& d, const Geom& g, const Motion& m, TransferSc
     const dim3 grd((unsigned)((d.L[2] + lanes - 1) / lanes),
                    (unsigned)((ncols + blk.y - 1) / blk.y));
     k_col_planes<T><<<grd, blk, 0, st>>>(d, g, ts, kref_t, k2);
-    k_fill<T><<<grid_for(g.boxN), kThreads, 0, st>>>(d, g, m, ts, k2, kus);
+    const dim3 fgrd((unsigned)((ncols + kFillCols - 1) / kFillCols),
+                    (unsigned)((g.bn[2] + kFillPlanes - 1) / kFillPlanes));
+    k_fill<T><<<fgrd, kFillCols * kFillPlanes, 0, st>>>(d, g, m, ts, k2, kus);
 }
 
 template <class T>

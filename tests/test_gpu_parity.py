@@ -272,3 +272,41 @@ def test_full_size_256_cube_two_steps_against_oracle(L):
     assert abs(J32 - Jg) <= 1e-5 * abs(Jg)
     assert rel_max(s32, fo) < 1e-5
     assert rel_l2(g32, go) < 1e-4
+
+
+def test_transfer_buffers_do_not_leak_across_runs(L):
+    """3D contexts compute the next step's transfer on a side stream into a second buffer set;
+    a design change between runs, an explicit lks_transfer in between and a shorter run must
+    all give bitwise the results of a fresh context."""
+    w = CASES["ragged3d"]()
+    g2 = np.clip(w.gamma[::-1].copy() * 0.8 + 0.1, 0.0, 1.0)
+
+    def fresh(gamma, n=None):
+        s = L.Solver(w.problem, L.FP32)
+        s.set_design(gamma)
+        s.set_motion(w.motion)
+        J = s.forward(n)
+        g = s.adjoint()
+        s.close()
+        return J, g
+
+    Ja, ga = fresh(w.gamma)
+    Jb, gb = fresh(g2)
+    Jc, gc = fresh(g2, 11)
+    s = L.Solver(w.problem, L.FP32)
+    s.set_design(w.gamma)
+    s.set_motion(w.motion)
+    J1 = s.forward()
+    g1 = s.adjoint()
+    k_before, _ = s.transfer(5)
+    s.set_design(g2)
+    k_after, _ = s.transfer(5)
+    J2 = s.forward()
+    g2_ = s.adjoint()
+    J3 = s.forward(11)
+    g3 = s.adjoint()
+    s.close()
+    assert J1 == Ja and np.array_equal(g1, ga)
+    assert J2 == Jb and np.array_equal(g2_, gb)
+    assert J3 == Jc and np.array_equal(g3, gc)
+    assert not np.array_equal(k_before, k_after)
