@@ -291,6 +291,18 @@ __device__ __forceinline__ V4<float> gather_out(float f0, float f1, float f2, fl
     return o;
 }
 
+// Does the node rectangle [xa, xb] x [ya, yb] meet the footprint box (the target box)?  Tested
+// once per tile, so that tiles away from the moving body or the objective skip the per-node
+// tests.  Periodic wraps are not taken into account: callers pass the flag only where no node
+// of the rectangle wraps.
+__device__ __forceinline__ bool meets_box(const Geom& g, int xa, int xb, int ya, int yb) {
+    return g.boxN > 0 && xb >= g.blo[0] && xa < g.blo[0] + g.bn[0] && yb >= g.blo[1] &&
+           ya < g.blo[1] + g.bn[1];
+}
+__device__ __forceinline__ bool meets_target(const Geom& g, int xa, int xb, int ya, int yb) {
+    return xb >= g.obox[0] && xa <= g.obox[1] && yb >= g.obox[2] && ya <= g.obox[3];
+}
+
 // kappa, u_S at node (x, y) of the footprint box, else zero.
 __device__ __forceinline__ float4 kus_at(const Inst& I, int x, int y) {
     long long bi;
@@ -316,6 +328,7 @@ __device__ __forceinline__ void step_tile(const Inst& I, int x0, int y0, int src
         }
     }
     __syncthreads();
+    const bool tbox = EDGE || meets_box(g, x0, x0 + TX - 1, y0, y0 + TY - 1);
     const float A = I.Af, bfx = I.bf[0], bfy = I.bf[1];
     // f^eq of every direction at the tile and its one-cell rim
     for (int k = threadIdx.x; k < FN; k += NT) {
@@ -358,8 +371,9 @@ __device__ __forceinline__ void step_tile(const Inst& I, int x0, int y0, int src
         const float f8 = F[7 * FN + f + FX - 1];   // from x - (1, -1)
         const long long m = (long long)y * n0 + x;
         const float kst = g.ks ? ((const float*)g.ks)[m] : 0.f;
-        const V4<float> o =
-            gather_out(f0, f1, f2, f3, f4, f5, f6, f7, f8, kus_at(I, x, y), kst, bfx, bfy);
+        const V4<float> o = gather_out(f0, f1, f2, f3, f4, f5, f6, f7, f8,
+                                       tbox ? kus_at(I, x, y) : make_float4(0.f, 0.f, 0.f, 0.f),
+                                       kst, bfx, bfy);
         out[m] = o;
         if (EDGE) write_bc_from(g, x, y, 0, o, out);
     }
@@ -412,7 +426,9 @@ __device__ __forceinline__ void cp_async_wait1() {
 template <int NTH, int YC>
 __global__ void __launch_bounds__(NTH) k_t_step2d_rows(Plan p, const int* __restrict__ pre,
                                                         int total, int src, int dst) {
-    constexpr int SW = NTH - 2, RW = NTH + 2, NR = 6;
+    // ring of state rows: 8 slots (6 in use: two rows below the f^eq row to three above), so
+    // that the slot of a row is its index & 7, negative indices included
+    constexpr int SW = NTH - 2, RW = NTH + 2, NR = 8;
     __shared__ float4 R[NR][RW];     // state rows, columns x0 - 2 .. x0 + SW + 1
     __shared__ float Fs[6][NTH];     // f_1, f_3, f_5, f_6, f_7, f_8 of the current F-row
     __shared__ Inst sI;
@@ -431,7 +447,8 @@ __global__ void __launch_bounds__(NTH) k_t_step2d_rows(Plan p, const int* __rest
         const float4* sp = (const float4*)sI.bufs[src];
         V4<float>* out = (V4<float>*)sI.bufs[dst];
         const float A = sI.Af, bfx = sI.bf[0], bfy = sI.bf[1];
-        auto slot = [](int r) { return ((r % NR) + NR) % NR; };
+        const bool tbox = p0 || p1 || meets_box(g, x0, x0 + SW, y0, y1 - 1);
+        auto slot = [](int r) { return r & (NR - 1); };
         auto issue_row = [&](int r) {   // state row r (unwrapped index) into its ring slot
             float4* row = R[slot(r)];
             int gy = r;
@@ -507,8 +524,10 @@ __global__ void __launch_bounds__(NTH) k_t_step2d_rows(Plan p, const int* __rest
                 if (ocol && orow) {
                     const long long m = (long long)y * n0 + xc;
                     const float kst = g.ks ? ((const float*)g.ks)[m] : 0.f;
-                    const V4<float> o = gather_out(c0, c1, b2, c3, g4, b5, b6, g7, g8,
-                                                   kus_at(sI, xc, y), kst, bfx, bfy);
+                    const V4<float> o = gather_out(
+                        c0, c1, b2, c3, g4, b5, b6, g7, g8,
+                        tbox ? kus_at(sI, xc, y) : make_float4(0.f, 0.f, 0.f, 0.f), kst, bfx,
+                        bfy);
                     out[m] = o;
                     write_bc_from(g, xc, y, 0, o, out);
                 }
@@ -566,6 +585,9 @@ __device__ __forceinline__ void adj_tile(const Inst& I, int x0, int y0, const Ob
     const int n0 = g.n[0], n1 = g.n[1];
     const float4* lam = (const float4*)I.bufs[lam_in];
     const V4<float>* su = (const V4<float>*)I.bufs[sn];
+    // tiles whose halo misses the footprint box (the target) skip those per-node tests
+    const bool tbox = EDGE || meets_box(g, x0 - 2, x0 + TX + 1, y0 - 2, y0 + TY + 1);
+    const bool ttgt = os.on && (EDGE || meets_target(g, x0 - 2, x0 + TX + 1, y0 - 2, y0 + TY + 1));
     // 1. mu on the tile and a two-cell halo; e on the tile's own box nodes
     for (int k = threadIdx.x; k < HX * HY; k += NT) {
         const int ly = k / HX, lx = k - ly * HX;
@@ -579,14 +601,14 @@ __device__ __forceinline__ void adj_tile(const Inst& I, int x0, int y0, const Ob
             const long long gm = (long long)gy * n0 + gx;
             const float4 lv = __ldg(lam + gm);
             float lr = lv.x, lux = lv.y, luy = lv.z;
-            if (os.on && in_target2(g, os, gx, gy)) {
+            if (ttgt && in_target2(g, os, gx, gy)) {
                 lr += os.r;
                 lux += os.x;
                 luy += os.y;
             }
             long long bi;
             const float kst = g.ks ? ((const float*)g.ks)[gm] : 0.f;
-            if (in_box(g, gx, gy, 0, bi)) {
+            if (tbox && in_box(g, gx, gy, 0, bi)) {
                 const V4<float> ks = I.kus[bi];
                 const float inv = 1.f / (1.f + ks.r + kst);
                 lux *= inv;
