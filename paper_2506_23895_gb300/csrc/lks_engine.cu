@@ -1265,7 +1265,10 @@ void inst_units(const lks_ctx* c, int out[U_COUNT]) {
     const Geom& g = c->g;
     const bool body = c->d.nd > 0 && g.boxN > 0;
     out[U_DCOL] = body ? (int)((c->d.ncol + kUnitThreads - 1) / kUnitThreads) : 0;
-    out[U_BOX] = body ? (int)((g.boxN + kUnitThreads - 1) / kUnitThreads) : 0;
+    // footprint box in tiles of kBoxTile x kBoxTile nodes (the 2D transfer stages the design
+    // nodes a tile reads in shared memory)
+    out[U_BOX] = body ? ((g.bn[0] + kBoxTile - 1) / kBoxTile) * ((g.bn[1] + kBoxTile - 1) / kBoxTile)
+                      : 0;
     out[U_SHELL] = (2 * (g.n[0] + g.n[1]) + kUnitThreads - 1) / kUnitThreads;
     out[U_INST] = 1;
     for (int k = 0; k < kTileCfgs; ++k)

@@ -70,14 +70,98 @@ __global__ void __launch_bounds__(NT) k_t_design_pos(Plan p, int noff) {
     }
 }
 
+// One 16 x 16 tile of the footprint box per work unit.  The design nodes any node of the tile can
+// reach (the tile's inverse rigid image widened by the kernel radius: at most 30 x 30 nodes) are
+// staged in shared memory with contiguous reads; every node then runs the candidate loop of
+// transfer2d_node on the staged copy, in the same order and with the same arithmetic.
+constexpr int kTrWin = 32;   // staged window side (design nodes)
+static_assert(kBoxTile * kBoxTile == NT, "one box tile per block of NT threads");
+
 __global__ void __launch_bounds__(NT) k_t_transfer2d(Plan p, int noff) {
+    __shared__ int2 sb[kTrWin * kTrWin];
+    __shared__ float4 ssc[kTrWin * kTrWin];
+    __shared__ float skr[kTrWin * kTrWin];
+    __shared__ int swin[4];
     const int* pre = p.pre + U_BOX * (p.count + 1);
     const int n = step_of(p, noff);
     for (int u = blockIdx.x; u < p.total[U_BOX]; u += gridDim.x) {
         const int i = find_inst(pre, p.count, u);
         const Inst& I = p.tab[i];
-        const long long bi = (long long)(u - pre[i]) * kUnitThreads + threadIdx.x;
-        if (bi < I.g.boxN) transfer2d_node(I.d, I.g, I.motion[n], I.ts, I.kref, I.kus, bi);
+        const Design& d = I.d;
+        const Geom& g = I.g;
+        const Motion& m = I.motion[n];
+        const int ntx = (g.bn[0] + kBoxTile - 1) / kBoxTile;
+        const int t = u - pre[i];
+        const int bx0 = (t % ntx) * kBoxTile, by0 = (t / ntx) * kBoxTile;
+        const int lx = threadIdx.x % kBoxTile, ly = threadIdx.x / kBoxTile;
+        const int bx = bx0 + lx, by = by0 + ly;
+        const bool node = bx < g.bn[0] && by < g.bn[1];
+        const int x = g.blo[0] + bx, y = g.blo[1] + by;
+        const float c = m.cf, s = m.sf;
+        const float R = 2.f * (fabsf(c) + fabsf(s)) + 0.01f;
+        // this node's candidate window (the same expressions as transfer2d_node)
+        const float px = (float)x - m.xgf[0], py = (float)y - m.xgf[1];
+        const float ic = c * px + s * py + d.xiGf[0];
+        const float jc = -s * px + c * py + d.xiGf[1];
+        const int i0 = max(0, (int)ceilf(ic - R)), i1 = min(d.L[0] - 1, (int)floorf(ic + R));
+        const int j0 = max(0, (int)ceilf(jc - R)), j1 = min(d.L[1] - 1, (int)floorf(jc + R));
+        __syncthreads();   // the previous unit's staged window is no longer read
+        if (threadIdx.x == 0) {
+            swin[0] = 1 << 30;
+            swin[1] = -(1 << 30);
+            swin[2] = 1 << 30;
+            swin[3] = -(1 << 30);
+        }
+        __syncthreads();
+        if (node && i0 <= i1 && j0 <= j1) {
+            atomicMin(&swin[0], i0);
+            atomicMax(&swin[1], i1);
+            atomicMin(&swin[2], j0);
+            atomicMax(&swin[3], j1);
+        }
+        __syncthreads();
+        const int wi0 = swin[0], wj0 = swin[2];
+        const int wni = swin[1] - wi0 + 1, wnj = swin[3] - wj0 + 1;
+        const bool staged = wni <= kTrWin && wnj <= kTrWin;
+        if (staged && wni > 0 && wnj > 0) {
+            const int2* base = reinterpret_cast<const int2*>(I.ts.col_base);
+            for (int e = threadIdx.x; e < wni * wnj; e += NT) {
+                const int jj = e / wni, ii = e - jj * wni;
+                const int k = (wj0 + jj) * d.L[0] + wi0 + ii;
+                sb[jj * kTrWin + ii] = __ldg(base + k);
+                ssc[jj * kTrWin + ii] = __ldg(I.ts.col_sc + k);
+                skr[jj * kTrWin + ii] = __ldg(I.kref + k);
+            }
+        }
+        __syncthreads();
+        if (!node) continue;
+        const long long bi = (long long)by * g.bn[0] + bx;
+        if (!staged) {   // a window wider than the staging area: the global-memory path
+            transfer2d_node(d, g, m, I.ts, I.kref, I.kus, bi);
+            continue;
+        }
+        const float gx0 = d.xiGf[0], gy0 = d.xiGf[1];
+        float kap = 0.f, m0 = 0.f, m1x = 0.f, m1y = 0.f;
+        for (int j = j0; j <= j1; ++j)
+            for (int ii = i0; ii <= i1; ++ii) {
+                const int sk = (j - wj0) * kTrWin + (ii - wi0);
+                const int2 b = sb[sk];
+                const int qx = x - b.x + 1, qy = y - b.y + 1;
+                if ((unsigned)qx > 3u || (unsigned)qy > 3u) continue;
+                const float4 sc = ssc[sk];
+                const float W = tap_weight(qx, sc.x, sc.y) * tap_weight(qy, sc.z, sc.w);
+                kap += W * skr[sk];
+                m0 += W;
+                m1x += W * ((float)ii - gx0);
+                m1y += W * ((float)j - gy0);
+            }
+        const float om = m.omf;
+        V4<float> o;
+        o.r = kap;
+        o.x = (-s * m1x - c * m1y) * om + m.ugf[0] * m0;
+        o.y = (c * m1x - s * m1y) * om + m.ugf[1] * m0;
+        o.z = 0.f;
+        I.kus[bi] = o;
     }
 }
 

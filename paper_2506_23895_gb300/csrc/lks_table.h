@@ -46,9 +46,10 @@ __host__ __device__ constexpr int tile_ty(int k) {
            (k == 7 ? 128 : 64)))));
 }
 
-// Work-unit kinds: design columns and box nodes in blocks of kUnitThreads, boundary-shell
+// Work-unit kinds: design columns in blocks of kUnitThreads, footprint-box tiles, boundary-shell
 // nodes in blocks, one unit per instance (objective), tiles of each shape.
 constexpr int kUnitThreads = 256;
+constexpr int kBoxTile = 16;   // box tiles of the 2D transfer: kBoxTile^2 = kUnitThreads nodes
 enum { U_DCOL = 0, U_BOX, U_SHELL, U_INST, U_TILE0, U_COUNT = U_TILE0 + kTileCfgs };
 
 struct Plan {
