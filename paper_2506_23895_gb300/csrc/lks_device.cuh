@@ -181,47 +181,6 @@ __device__ __forceinline__ void write_bc_from(const Geom& g, int x, int y, int z
     });
 }
 
-// The same in compact loop form, for kernels where the unrolled visitor costs registers on the
-// common path: the options per axis are listed (first the node's own coordinate) and all
-// non-trivial combinations written.
-__device__ __forceinline__ int bc_axis_options(const Geom& g, int a, int ci, int opt[3],
-                                               int side[3]) {
-    opt[0] = ci;
-    side[0] = -1;
-    int k = 1;
-    if (a < g.dim && !g.periodic[a]) {
-        if (ci == 1) {
-            opt[k] = 0;
-            side[k] = 0;
-            ++k;
-        }
-        if (ci == g.n[a] - 2) {
-            opt[k] = g.n[a] - 1;
-            side[k] = 1;
-            ++k;
-        }
-    }
-    return k;
-}
-
-template <class T>
-__device__ void write_bc_from_compact(const Geom& g, int x, int y, int z, const V4<T>& v,
-                                      V4<T>* s) {
-    int ox[3], oy[3], oz[3], sx[3], sy[3], sz[3];
-    const int nx = bc_axis_options(g, 0, x, ox, sx);
-    const int ny = bc_axis_options(g, 1, y, oy, sy);
-    const int nz = bc_axis_options(g, 2, z, oz, sz);
-    if (nx == 1 && ny == 1 && nz == 1) return;
-    for (int k = 0; k < nz; ++k)
-        for (int j = 0; j < ny; ++j)
-            for (int i = 0; i < nx; ++i) {
-                if (i == 0 && j == 0 && k == 0) continue;
-                const int side[3] = {sx[i], sy[j], sz[k]};
-                const int f = winning_face(g, side);
-                s[node_index(g, ox[i], oy[j], oz[k])] = bc_value(g, f, v);
-            }
-}
-
 // ------------------------------------------------------------------ gradient stencil
 // First derivative along an axis: central difference, periodic wrap, and the second-order
 // one-sided difference on a non-periodic boundary node (the reading taken for the velocity

@@ -804,16 +804,6 @@ int fused_zchunk_waves(const Geom& g, long long tiles, int per_sm) {
     return (g.n[2] + best - 1) / best;
 }
 
-// Planes per z chunk: about three resident waves of two blocks per SM, chunks of >= 16 planes.
-int fused_zchunk(const Geom& g, long long tiles) {
-    int dev = 0, nsm = 148;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    int chunks = (int)std::max(1LL, (6LL * nsm + tiles - 1) / tiles);
-    chunks = std::min(chunks, std::max(1, g.n[2] / 16));
-    return (g.n[2] + chunks - 1) / chunks;
-}
-
 template <int TY_>
 cudaError_t launch_zstep(const Geom& g, const CUtensorMap& map, const FusedArgs& a0,
                          cudaStream_t st) {

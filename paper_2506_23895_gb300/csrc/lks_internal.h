@@ -123,7 +123,6 @@ struct FaceOffsets {
     long long off[6];
 };
 bool fused3d_eligible(const Geom& g);
-int fused_zchunk(const Geom& g, long long tiles);
 int fused_zchunk_waves(const Geom& g, long long tiles, int per_sm);
 constexpr int kStep3dVariants = 2;
 cudaError_t launch_fused_step3d(const Geom& g, const V4<float>* src, const V4<float>* kus,
