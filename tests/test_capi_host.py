@@ -110,3 +110,34 @@ def test_checkpoint_schedule_reverses_everything_within_budget(lib, n_seg, slots
         while comb(s + r, s) < n_seg:
             r += 1
         assert adv <= (r + 1) * n_seg
+
+
+def test_rotation_axis_and_transfer_sets_in_the_workspace(lib):
+    """A tilted rotation axis adds the cell-list scratch; a non-unit axis is rejected; the z
+    axis given explicitly (or as all zeros) sizes like the default; 3D contexts carry a second
+    transfer buffer set, 2D ones do not."""
+    w = W.small_duct3d()
+    base = lib.lks_workspace_bytes(ctypes.byref(lks.make_config(w.problem, lks.FP32)))
+    for axis in ((0.0, 0.0, 1.0), (0.0, 0.0, 0.0)):
+        w.problem.rot_axis = axis
+        assert lib.lks_workspace_bytes(ctypes.byref(lks.make_config(w.problem, lks.FP32))) == base
+    w.problem.rot_axis = W.unit((1.0, 2.0, 2.0))
+    tilted = lib.lks_workspace_bytes(ctypes.byref(lks.make_config(w.problem, lks.FP32)))
+    nodes = w.problem.nodes
+    assert tilted >= base + nodes * (4 + 8 * 4)   # cell counts and lists over the whole grid
+    w.problem.rot_axis = (0.0, 0.6, 0.6)
+    assert lib.lks_workspace_bytes(ctypes.byref(lks.make_config(w.problem, lks.FP32))) == 0
+    # the second transfer set of a 3D context holds at least another kappa/u_S box
+    w3 = W.small_duct3d()
+    c3 = lks.make_config(w3.problem, lks.FP32)
+    n3 = lib.lks_workspace_bytes(ctypes.byref(c3))
+    c3.lx = c3.ly = c3.lz = 0          # no design grid: no transfer buffers at all
+    n3_empty = lib.lks_workspace_bytes(ctypes.byref(c3))
+    assert n3 - n3_empty >= 2 * w3.problem.nodes * 16
+
+
+def test_step_variant_argument_checks(lib):
+    lib.lks_step_variant.restype = ctypes.c_int
+    v = ctypes.c_int(7)
+    assert lib.lks_step_variant(None, 0, ctypes.byref(v)) == 1   # LKS_ERR_ARG without a context
+    assert v.value == 7
