@@ -808,13 +808,13 @@ template <int TY_>
 cudaError_t launch_zstep(const Geom& g, const CUtensorMap& map, const FusedArgs& a0,
                          cudaStream_t st) {
     using C = ZCfg<TY_>;
-    static bool attr = false;
-    if (!attr) {
+    static unsigned attr = 0;   // devices whose shared-memory limit is raised
+    if (!device_done(attr)) {
         cudaError_t e = cudaFuncSetAttribute(k_zstep3d<TY_>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)C::SMEM);
         if (e != cudaSuccess) return e;
-        attr = true;
+        device_mark(attr);
     }
     FusedArgs a = a0;
     const int tiles_x = (g.n[0] + C::TX - 1) / C::TX, tiles_y = (g.n[1] + C::TY - 1) / C::TY;
@@ -845,13 +845,13 @@ cudaError_t launch_fused_step3d(const Geom& g, const V4<float>* src, const V4<fl
         return launch_zstep<8>(g, map, a, st);
     }
     if (!encode_state_map(&map, src, g, HX, HY)) return cudaErrorInvalidValue;
-    static bool attr = false;
-    if (!attr) {
+    static unsigned attr = 0;   // devices whose shared-memory limit is raised
+    if (!device_done(attr)) {
         cudaError_t e = cudaFuncSetAttribute(k_fused_step3d,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)SMEM_BYTES);
         if (e != cudaSuccess) return e;
-        attr = true;
+        device_mark(attr);
     }
     const int tiles_x = (g.n[0] + TX - 1) / TX, tiles_y = (g.n[1] + TY - 1) / TY;
     a.zchunk = fused_zchunk_waves(g, (long long)tiles_x * tiles_y, 4);

@@ -91,6 +91,19 @@ struct AxisScratch {
     int* idx;    // [box cells][kCellMax], ascending design index
 };
 
+// Per-device once-only host state (kernel attributes are per device): bit d of `mask` records
+// that the current device d has been set up.  Devices past 31 are set up on every call.
+inline bool device_done(const unsigned& mask) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    return dev < 32 && (mask >> dev & 1u);
+}
+inline void device_mark(unsigned& mask) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 32) mask |= 1u << dev;
+}
+
 // ---- kernel launchers (templated on T = float / double, explicitly instantiated) ----
 template <class T>
 void launch_init_state(const Geom& g, V4<T>* s, cudaStream_t st);
