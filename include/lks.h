@@ -85,7 +85,13 @@ typedef struct {
     int win_begin, win_end;  /* objective window (inclusive step indices, 1-based) */
     size_t ckpt_bytes;       /* device bytes for adjoint snapshots; 0 = full history if it
                                 fits in 8 GB, else the minimum of a two-level scheme */
-    void* stream;            /* cudaStream_t for all work; NULL = legacy default stream */
+    void* stream;            /* cudaStream_t the work is ordered on; NULL = legacy default
+                                stream.  A 3D forward or adjoint run starts after the work
+                                already on it and is complete on it when the call returns: the
+                                run executes on two internal streams of the context (its steps
+                                at the highest priority, the next step's transfer and the
+                                sensitivity gathers at the lowest), forked from and joined back
+                                to this stream by events. */
     int flags;               /* LKS_FLAG_* bits; 0 normally */
     double rot_axis[3];      /* 3D rotation axis of the design grid, a unit vector; all zero or
                                 (0, 0, 1) is the z axis (the paper's 3D rotor, Sec. 3.3).  Any
