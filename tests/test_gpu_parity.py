@@ -49,7 +49,29 @@ def run_gpu(L, w, prec, n=None, ckpt=0, init=None, flags=0, expect_fused=None):
     return J, st, g, stats
 
 
+def corners3d():
+    """A duct whose four walls move at four different tangential velocities (inlet z-, outlet
+    z+), so every edge and corner rule (wall ties to the lower face, wall over inlet and
+    outlet, diagonal-inward density copies) shows in the state; several 32 x 8 tiles with
+    ragged tails."""
+    w = W.small_duct3d(nx=40, ny=19, nz=14, LD=7, n_steps=16, omega=0.02, trans_amp=0.8,
+                       seed=33)
+    w.problem.bc_val = ((0.0, 0.0, 0.011, 1.0), (0.0, 0.0, -0.007, 1.0), (0.0, 0.0, 0.023, 1.0),
+                        (0.0, 0.0, 0.031, 1.0), (0.0, 0.0, 0.04, 1.0), (0.0, 0.0, 0.0, 0.998))
+    return w
+
+
+def corners2d():
+    """A channel with a moving lid and an outlet density off rho0: the corner rules of 2D."""
+    w = W.small_channel2d(nx=45, ny=30, LD=10, n_steps=30, omega=0.015, trans_amp=1.0, seed=34)
+    w.problem.bc_val = ((0.04, 0.0, 0.0, 1.0), (0.0, 0.0, 0.0, 1.003), (0.0, 0.0, 0.0, 1.0),
+                        (0.02, 0.0, 0.0, 1.0), (0.0, 0.0, 0.0, 1.0), (0.0, 0.0, 0.0, 1.0))
+    return w
+
+
 CASES = {
+    "corners3d": corners3d,
+    "corners2d": corners2d,
     "small2d_J1": lambda: W.small_channel2d(),
     "small2d_J2": lambda: W.small_channel2d(obj_kind=W.OBJ_VELOCITY, n_steps=36, seed=21),
     "small3d_J2": lambda: W.small_duct3d(),
@@ -86,7 +108,8 @@ def test_forward_adjoint_fp64_match_oracle(L, name):
     assert rel_max(g, go) < 1e-11
 
 
-@pytest.mark.parametrize("name", ["small2d_J1", "small3d_J2", "ragged2d", "ragged3d"])
+@pytest.mark.parametrize("name", ["small2d_J1", "small3d_J2", "ragged2d", "ragged3d",
+                                  "corners3d", "corners2d"])
 def test_forward_adjoint_fp32_within_tolerance(L, name):
     w = CASES[name]()
     Jg, go = oracle.gradient(w.problem, w.gamma, w.motion)
@@ -187,7 +210,8 @@ MID3D = lambda: W.small_duct3d(nx=70, ny=45, nz=52, LD=14, n_steps=30, omega=0.0
                                trans_amp=2.0, seed=33)
 
 
-@pytest.mark.parametrize("name", ["small3d_J2", "small3d_J1", "ragged3d", "mid3d"])
+@pytest.mark.parametrize("name", ["small3d_J2", "small3d_J1", "ragged3d", "mid3d",
+                                  "corners3d"])
 def test_fused_fp32_step_matches_plain_fp32_and_oracle(L, name):
     w = MID3D() if name == "mid3d" else CASES[name]()
     Jf, sf, gf, _ = run_gpu(L, w, L.FP32, expect_fused=True)
@@ -200,7 +224,7 @@ def test_fused_fp32_step_matches_plain_fp32_and_oracle(L, name):
     assert rel_l2(gf, go) < 1e-4
 
 
-@pytest.mark.parametrize("name", ["small3d_J1", "ragged3d", "mid3d"])
+@pytest.mark.parametrize("name", ["small3d_J1", "ragged3d", "mid3d", "corners3d"])
 def test_fused_step_variants_agree(L, name):
     """Every variant of the fused 3D forward step (fixed through lks_step_variant) gives the
     same run as variant 0 up to rounding, within the FP32 tolerances of the oracle; variant 1 is
