@@ -237,16 +237,30 @@ int lks_checkpoint_schedule(int n_segments, int free_slots, int* triples, int ca
  * synchronised.  The f^eq planes live in a file-scope device array of 32 MiB that stays on
  * every device that loads the library until the process exits: grids needing more
  * (nodes x Q x element size > 32 MiB, e.g. more than about 559k nodes for D3Q15 in FP32) are
- * rejected with LKS_ERR_ARG and a message in err (err_len bytes, may be NULL).  The first call
- * on each device looks up that array's device address (keep it outside stream capture).  All
- * calls share the array, so calls that overlap on the GPU race and must be serialised by the
- * caller; each call rewrites all the scratch it reads.  cudaMalloc, cudaFree and allocating
- * library routines are never called. */
+ * rejected with LKS_ERR_ARG and a message in err (err_len bytes, may be NULL), and so are
+ * state_in, state_out or kappa_us not aligned to one node record (16 bytes in FP32, 32 in
+ * FP64).  A call on a stream that is not being captured looks up that array's device address on
+ * the current device; a call under stream capture reuses the address the last such call found,
+ * so the first call on each device must come before any capture (else LKS_ERR_ORDER), and
+ * after a device reset the next uncaptured call finds the array's new address.  A CUDA error
+ * already pending on the calling thread is reported (LKS_ERR_CUDA) before anything is
+ * launched.  All calls share the array, so calls that overlap on the GPU race and must be
+ * serialised by the caller; each call rewrites all the scratch it reads.  cudaMalloc, cudaFree
+ * and allocating library routines are never called. */
 lks_status lks_step_noalloc(const lks_config* cfg, const void* state_in, void* state_out,
                             const void* kappa_us, char* err, size_t err_len);
 
 const char* lks_last_error(const lks_ctx* ctx);
 void lks_destroy(lks_ctx* ctx);
+
+/* Host-side fault injection for failure-detection tests (the paper has no counterpart): the
+ * nth device allocation the library makes from now on (1 = the next one) reports failure
+ * without calling the allocator, as if the device were out of memory; 0 switches injection
+ * off.  Allocations are those of lks_create without a caller workspace, lks_batch_create and
+ * the temporary buffers of lks_get_state, lks_get_adjoint_state, lks_set_initial_state and
+ * lks_transfer; each returns LKS_ERR_NOMEM when its allocation fails and frees what it had
+ * taken.  Returns the previous setting.  Process-wide; host only, needs no device. */
+int lks_inject_alloc_failure(int nth);
 
 /* ---- batches: many problems in lock step (designs, finite-difference perturbations, grids of
  * different sizes).  The paper solves one problem at a time; a batch runs the same Algorithm 1

@@ -3,6 +3,7 @@
 // sweep (Algorithm 2 structure, exact discrete adjoint) under a binomial checkpoint schedule
 // over tape segments, so that the stored history fits the given device memory.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -203,6 +204,31 @@ lks_status fail(lks_ctx* c, lks_status s, const char* fmt, ...) {
         cudaError_t e_ = (call);                                                          \
         if (e_ != cudaSuccess)                                                            \
             return fail(c, LKS_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_));        \
+    } while (0)
+
+// Host-side fault injection (lks_inject_alloc_failure): a countdown of device allocations; the
+// allocation that brings it to zero reports failure without calling the allocator.
+std::atomic<int> g_fail_alloc{0};
+
+cudaError_t dev_alloc(void** p, size_t bytes) {
+    int k = g_fail_alloc.load();
+    while (k > 0 && !g_fail_alloc.compare_exchange_weak(k, k - 1)) {
+    }
+    if (k == 1) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(p, bytes);
+}
+
+// A device allocation inside an entry point: LKS_ERR_NOMEM with a message on failure.
+#define ALLOC(pp, bytes)                                                                  \
+    do {                                                                                  \
+        if (dev_alloc((void**)(pp), (bytes)) != cudaSuccess) {                            \
+            cudaGetLastError();                                                           \
+            return fail(c, LKS_ERR_NOMEM, "device allocation of %zu bytes failed",        \
+                        (size_t)(bytes));                                                 \
+        }                                                                                 \
     } while (0)
 
 #define LAUNCHED()                                                                        \
@@ -1424,7 +1450,7 @@ lks_status lks_create(const lks_config* cfg, void* workspace, size_t ws_bytes, l
         c->ws = (char*)workspace;
         c->own_ws = false;
     } else {
-        if (cudaMalloc((void**)&c->ws, L.total) != cudaSuccess) {
+        if (dev_alloc((void**)&c->ws, L.total) != cudaSuccess) {
             cudaGetLastError();
             delete c;
             return LKS_ERR_NOMEM;
@@ -1673,7 +1699,7 @@ lks_status lks_get_adjoint_state(const lks_ctx* cc, double* out) {
     if (!c->have_lend) return fail(c, LKS_ERR_ORDER, "no adjoint run yet");
     double* tmp = nullptr;
     const size_t bytes = (size_t)c->g.nodes * 4 * 8;
-    CU(cudaMalloc(&tmp, bytes));
+    ALLOC(&tmp, bytes);
     if (c->prec == LKS_FP64)
         launch_state_to_f64<double>(c->g, (const V4<double>*)c->l_end, tmp, c->st, false);
     else
@@ -1762,7 +1788,7 @@ lks_status lks_set_initial_state(lks_ctx* c, const double* state) {
     if (!state) return c->prec == LKS_FP64 ? reset_initial<double>(c) : reset_initial<float>(c);
     double* tmp = nullptr;
     const size_t bytes = (size_t)c->g.nodes * 4 * 8;
-    CU(cudaMalloc(&tmp, bytes));
+    ALLOC(&tmp, bytes);
     cudaError_t e1 = cudaMemcpyAsync(tmp, state, bytes, cudaMemcpyHostToDevice, c->st);
     if (c->prec == LKS_FP64) launch_state_from_f64<double>(c->g, tmp, st4<double>(c->s0), c->st);
     else launch_state_from_f64<float>(c->g, tmp, st4<float>(c->s0), c->st);
@@ -1815,7 +1841,7 @@ lks_status lks_get_state(const lks_ctx* cc, double* out) {
     if (!c || !out) return LKS_ERR_ARG;
     double* tmp = nullptr;
     const size_t bytes = (size_t)c->g.nodes * 4 * 8;
-    CU(cudaMalloc(&tmp, bytes));
+    ALLOC(&tmp, bytes);
     const void* src = c->last ? c->last : c->s0;
     if (c->prec == LKS_FP64)
         launch_state_to_f64<double>(c->g, (const V4<double>*)src, tmp, c->st);
@@ -1848,7 +1874,7 @@ lks_status lks_transfer(lks_ctx* c, int step, double* kappa_out, double* us_out)
     if (s == LKS_OK) s = transfer_join(c);
     if (s != LKS_OK) return s;
     double* tmp = nullptr;
-    CU(cudaMalloc(&tmp, nodes * 4 * 8));
+    ALLOC(&tmp, nodes * 4 * 8);
     if (c->prec == LKS_FP64)
         launch_box_to_grid<double>(c->g, (const V4<double>*)c->kus, tmp, tmp + nodes, c->st);
     else
@@ -1922,6 +1948,8 @@ lks_status lks_read_timing(lks_ctx* c, double* out4) {
 }
 
 const char* lks_last_error(const lks_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+int lks_inject_alloc_failure(int nth) { return g_fail_alloc.exchange(nth > 0 ? nth : 0); }
 
 void lks_destroy(lks_ctx* c) {
     if (!c) return;
@@ -2121,7 +2149,7 @@ lks_status lks_batch_create(lks_ctx* const* ctxs, int n, lks_batch** out) {
     const size_t pre_bytes = align256(sizeof(int) * U_COUNT * (n + 1));
     if (cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming) != cudaSuccess ||
-        cudaMalloc((void**)&b->dmem, inst_bytes + pre_bytes + 256) != cudaSuccess) {
+        dev_alloc((void**)&b->dmem, inst_bytes + pre_bytes + 256) != cudaSuccess) {
         cudaGetLastError();
         lks_batch_destroy(b);
         return LKS_ERR_NOMEM;

@@ -808,7 +808,7 @@ template <int TY_>
 cudaError_t launch_zstep(const Geom& g, const CUtensorMap& map, const FusedArgs& a0,
                          cudaStream_t st) {
     using C = ZCfg<TY_>;
-    static unsigned attr = 0;   // devices whose shared-memory limit is raised
+    static std::atomic<unsigned> attr{0};   // devices whose shared-memory limit is raised
     if (!device_done(attr)) {
         cudaError_t e = cudaFuncSetAttribute(k_zstep3d<TY_>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -845,7 +845,7 @@ cudaError_t launch_fused_step3d(const Geom& g, const V4<float>* src, const V4<fl
         return launch_zstep<8>(g, map, a, st);
     }
     if (!encode_state_map(&map, src, g, HX, HY)) return cudaErrorInvalidValue;
-    static unsigned attr = 0;   // devices whose shared-memory limit is raised
+    static std::atomic<unsigned> attr{0};   // devices whose shared-memory limit is raised
     if (!device_done(attr)) {
         cudaError_t e = cudaFuncSetAttribute(k_fused_step3d,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,

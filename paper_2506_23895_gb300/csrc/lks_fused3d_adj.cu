@@ -433,7 +433,7 @@ cudaError_t launch_fused_adj3d(const Geom& g, const V4<float>* lam_in, V4<float>
     CUtensorMap map;
     // a box one column wider than the tile: the unused last column pads the row pitch
     if (!encode_state_map(&map, lam_in, g, PX, HY)) return cudaErrorInvalidValue;
-    static unsigned attr = 0;   // devices whose shared-memory limit is raised
+    static std::atomic<unsigned> attr{0};   // devices whose shared-memory limit is raised
     if (!device_done(attr)) {
         cudaError_t r = cudaFuncSetAttribute(k_fused_adj3d,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,

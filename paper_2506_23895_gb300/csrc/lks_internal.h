@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 namespace lks {
 
 // One node of state (rho - rho0, ux, uy, uz) or adjoint (lam_rho, lam_u).  16 B (float) or
@@ -92,16 +94,18 @@ struct AxisScratch {
 };
 
 // Per-device once-only host state (kernel attributes are per device): bit d of `mask` records
-// that the current device d has been set up.  Devices past 31 are set up on every call.
-inline bool device_done(const unsigned& mask) {
+// that the current device d has been set up.  Devices past 31 are set up on every call.  The
+// mask is atomic, so host threads driving contexts at the same time may race to set a device up
+// (the set-up is idempotent) but never lose a bit.
+inline bool device_done(const std::atomic<unsigned>& mask) {
     int dev = 0;
     cudaGetDevice(&dev);
-    return dev < 32 && (mask >> dev & 1u);
+    return dev < 32 && (mask.load(std::memory_order_acquire) >> dev & 1u);
 }
-inline void device_mark(unsigned& mask) {
+inline void device_mark(std::atomic<unsigned>& mask) {
     int dev = 0;
     cudaGetDevice(&dev);
-    if (dev < 32) mask |= 1u << dev;
+    if (dev < 32) mask.fetch_or(1u << dev, std::memory_order_release);
 }
 
 // ---- kernel launchers (templated on T = float / double, explicitly instantiated) ----

@@ -9,11 +9,16 @@
 //
 // The array is created when the library is loaded on a device and stays until the process exits.
 // Host code cannot use its name as a device address (on the host the symbol is only a stand-in),
-// so the first call on each device looks up its address with cudaGetSymbolAddress while that
-// device is current and keeps it.  Do that first call before any stream capture begins.
+// so a call looks up its address with cudaGetSymbolAddress while that device is current.  A call
+// made while cfg->stream is being captured does not look it up (it reuses the address the last
+// uncaptured call on that device found), so make the first call on each device before any stream
+// capture begins; every uncaptured call looks it up again, so a device reset or a re-created
+// primary context (after which the module may load elsewhere) is picked up by the next
+// uncaptured call.
 // All calls share the one array: calls whose kernels overlap on the GPU (two streams, or two
 // host threads) race on it and must be serialised by the caller.  Every call overwrites all of
 // the scratch it reads, so nothing has to be cleared between calls.
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -77,11 +82,38 @@ extern "C" lks_status lks_step_noalloc(const lks_config* cfg, const void* state_
         put_err(err, err_len, "lks_step_noalloc: null configuration or state pointer");
         return LKS_ERR_ARG;
     }
+    {
+        // an error left pending by earlier work on this thread is reported as such, not as a
+        // failure of this call's launches
+        const cudaError_t pending = cudaGetLastError();
+        if (pending != cudaSuccess) {
+            char msg[256];
+            std::snprintf(msg, sizeof(msg),
+                          "lks_step_noalloc: a CUDA error was pending before this call: %s",
+                          cudaGetErrorString(pending));
+            put_err(err, err_len, msg);
+            return LKS_ERR_CUDA;
+        }
+    }
     if (lks_workspace_bytes(cfg) == 0) {
         put_err(err, err_len, "lks_step_noalloc: invalid configuration");
         return LKS_ERR_ARG;
     }
     const size_t tsz = cfg->precision == LKS_FP64 ? 8 : 4;
+    {
+        // the kernels move one node record (4 values) per vector access
+        const uintptr_t rec = 4 * tsz;
+        if ((uintptr_t)state_in % rec || (uintptr_t)state_out % rec ||
+            (uintptr_t)kappa_us % rec) {
+            char msg[160];
+            std::snprintf(msg, sizeof(msg),
+                          "lks_step_noalloc: state_in, state_out and kappa_us must be aligned "
+                          "to one node record (%zu bytes)",
+                          (size_t)rec);
+            put_err(err, err_len, msg);
+            return LKS_ERR_ARG;
+        }
+    }
     const int Q = cfg->dim == 3 ? 15 : 9;
     const long long nodes = (long long)cfg->nx * cfg->ny * (cfg->dim == 3 ? cfg->nz : 1);
     const size_t need = (size_t)nodes * Q * tsz;
@@ -100,10 +132,17 @@ extern "C" lks_status lks_step_noalloc(const lks_config* cfg, const void* state_
         put_err(err, err_len, "lks_step_noalloc: no usable current device");
         return LKS_ERR_CUDA;
     }
+    cudaStream_t st = (cudaStream_t)cfg->stream;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) {
+        cudaGetLastError();
+        put_err(err, err_len, "lks_step_noalloc: cfg->stream is not a usable stream");
+        return LKS_ERR_ARG;
+    }
     void* scratch = nullptr;
     {
         std::lock_guard<std::mutex> lock(g_mu);
-        if (!g_scratch_ptr[dev]) {
+        if (cap == cudaStreamCaptureStatusNone) {
             void* p = nullptr;
             const cudaError_t e = cudaGetSymbolAddress(&p, g_step_scratch);
             if (e != cudaSuccess || !p) {
@@ -112,11 +151,15 @@ extern "C" lks_status lks_step_noalloc(const lks_config* cfg, const void* state_
                 return LKS_ERR_CUDA;
             }
             g_scratch_ptr[dev] = p;
+        } else if (!g_scratch_ptr[dev]) {
+            put_err(err, err_len,
+                    "lks_step_noalloc: the first call on a device must come before stream "
+                    "capture");
+            return LKS_ERR_ORDER;
         }
         scratch = g_scratch_ptr[dev];
     }
     const Geom g = geom_from(cfg, kappa_us != nullptr);
-    cudaStream_t st = (cudaStream_t)cfg->stream;
     if (cfg->precision == LKS_FP64) {
         launch_feq<double>(g, (const V4<double>*)state_in, (double*)scratch, st);
         launch_gather<double>(g, (const double*)scratch, (const V4<double>*)kappa_us,

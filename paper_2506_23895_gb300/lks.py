@@ -27,7 +27,8 @@ EXPORTS = ("lks_workspace_bytes", "lks_create", "lks_set_design", "lks_set_motio
            "lks_batch_create", "lks_batch_set_options", "lks_batch_forward", "lks_batch_adjoint",
            "lks_batch_tile_shapes", "lks_batch_tuning", "lks_batch_stats",
            "lks_batch_last_error", "lks_batch_destroy", "lks_set_filter", "lks_volume",
-           "lks_set_static", "lks_warm_start", "lks_set_adjoint_start", "lks_get_adjoint_state")
+           "lks_set_static", "lks_warm_start", "lks_set_adjoint_start", "lks_get_adjoint_state",
+           "lks_inject_alloc_failure")
 
 
 class LksError(RuntimeError):
@@ -103,6 +104,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.lks_last_error.restype = ctypes.c_char_p
     lib.lks_destroy.argtypes = [P]
     lib.lks_destroy.restype = None
+    lib.lks_inject_alloc_failure.argtypes = [ctypes.c_int]
+    lib.lks_inject_alloc_failure.restype = ctypes.c_int
     lib.lks_set_filter.argtypes = [P, ctypes.c_double, ctypes.c_double, ctypes.c_double]
     lib.lks_set_filter.restype = ctypes.c_int
     lib.lks_volume.argtypes = [P, ctypes.c_double, D, P, ctypes.c_int]

@@ -141,3 +141,19 @@ def test_step_variant_argument_checks(lib):
     v = ctypes.c_int(7)
     assert lib.lks_step_variant(None, 0, ctypes.byref(v)) == 1   # LKS_ERR_ARG without a context
     assert v.value == 7
+
+
+def test_alloc_failure_injection_on_the_host(lib):
+    """The fault-injection countdown: lks_create without a caller workspace fails with
+    LKS_ERR_NOMEM at the injected allocation, leaves no context behind, and the countdown
+    is consumed (host side only: the injected allocation never reaches the driver)."""
+    assert lib.lks_inject_alloc_failure(0) == 0
+    w = W.small_duct3d()
+    c = lks.make_config(w.problem, lks.FP32)
+    out = ctypes.c_void_p(12345)
+    assert lib.lks_inject_alloc_failure(1) == 0
+    rc = lib.lks_create(ctypes.byref(c), None, 0, ctypes.byref(out))
+    assert rc == 3 and not out.value
+    assert lib.lks_inject_alloc_failure(0) == 0   # consumed by that allocation
+    assert lib.lks_inject_alloc_failure(5) == 0
+    assert lib.lks_inject_alloc_failure(0) == 5

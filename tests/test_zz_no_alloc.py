@@ -1,17 +1,20 @@
-"""The allocation-free step (lks_step_noalloc) against the library's normal forward step.
+"""The allocation-free step (lks_step_noalloc) against the library's normal forward step and
+against the CPU oracle.
 
 lks_step_noalloc exists for callers that cannot allocate device memory when they need a step
 (stream capture into a CUDA graph, memory owned by a host framework's pool, loops that must not
-block on the allocator).  It keeps its scratch in a static device array, so this test calls it
-twice in a row through the C ABI and checks both results against lks_forward(1) of a normal
-context, within the tolerances the parity tests use for the precision.  The file name makes
-pytest collect it last.
+block on the allocator).  It keeps its scratch in a static device array, so these tests call it
+twice in a row through the C ABI and check both results against the oracle's step from the same
+state and against lks_forward(1) of a normal context, within the tolerances the parity tests use
+for the precision, with and without a body (kappa_us = NULL).  The file name makes pytest
+collect it last.
 """
 import ctypes
 
 import numpy as np
 import pytest
 
+import oracle
 from paper_2506_23895_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -72,11 +75,71 @@ def test_noalloc_step_matches_forward_step(L, name, prec):
         torch.cuda.synchronize()
         o = out.cpu().numpy().astype(np.float64)
         outs.append(np.stack([o[..., 0] + p.rho0, o[..., 1], o[..., 2], o[..., 3]]))
+    _, orc = oracle.forward(p, w.gamma, w.motion, n_steps=1, init_state=s0)
     tol = 1e-11 if prec == 1 else 1e-5
     for o in outs:
         assert np.all(np.isfinite(o))
         assert np.max(np.abs(o - ref)) <= tol * np.max(np.abs(ref))
+        assert np.max(np.abs(o - orc)) <= tol * np.max(np.abs(orc))
     assert np.array_equal(outs[0], outs[1])
+
+
+def _noalloc(L, cfg, st_in, out, kus):
+    err = ctypes.create_string_buffer(256)
+    rc = L.load().lks_step_noalloc(ctypes.byref(cfg), ctypes.c_void_p(st_in.data_ptr()),
+                                   ctypes.c_void_p(out.data_ptr()),
+                                   None if kus is None else ctypes.c_void_p(kus.data_ptr()),
+                                   err, 256)
+    return rc, err.value.decode()
+
+
+@pytest.mark.parametrize("name,prec", [("2d", 0), ("3d", 0), ("3d", 1)])
+def test_noalloc_step_without_body_matches_oracle(L, name, prec):
+    """kappa_us = NULL: no body anywhere (kappa = 0); a seeded non-uniform state."""
+    import torch
+
+    w = W.small_channel2d() if name == "2d" else W.small_duct3d()
+    p = W.Problem(**{**w.problem.__dict__, "L": (0, 0, 0)})
+    nx, ny, nz = p.n
+    r = W.splitmix64_uniform(77, 4 * nx * ny * nz).reshape(4, nz, ny, nx)
+    s0 = np.empty_like(r)
+    s0[0] = p.rho0 + 0.01 * (r[0] - 0.5)
+    for a in range(3):
+        s0[1 + a] = 0.03 * (r[1 + a] - 0.5)
+    if p.dim == 2:
+        s0[3] = 0.0
+    _, orc = oracle.forward(p, None, np.zeros((2, 8)), n_steps=1, init_state=s0)
+    dtype = np.float64 if prec == 1 else np.float32
+    st_in = torch.from_numpy(_node_records(s0, p.rho0, dtype)).cuda()
+    cfg = L.make_config(p, prec)
+    tol = 1e-11 if prec == 1 else 1e-5
+    outs = []
+    for _ in range(2):
+        out = torch.full_like(st_in, float("nan"))
+        torch.cuda.synchronize()
+        rc, msg = _noalloc(L, cfg, st_in, out, None)
+        assert rc == 0, msg
+        torch.cuda.synchronize()
+        o = out.cpu().numpy().astype(np.float64)
+        outs.append(np.stack([o[..., 0] + p.rho0, o[..., 1], o[..., 2], o[..., 3]]))
+    for o in outs:
+        assert np.max(np.abs(o - orc)) <= tol * np.max(np.abs(orc))
+    assert np.array_equal(outs[0], outs[1])
+
+
+def test_noalloc_step_rejects_misaligned_records(L):
+    """An address that is not a whole node record is refused before anything is launched."""
+    p = W.small_duct3d().problem
+    for prec, bad in ((0, 20), (1, 16)):
+        cfg = L.make_config(p, prec)
+        err = ctypes.create_string_buffer(256)
+        lib = L.load()
+        rc = lib.lks_step_noalloc(ctypes.byref(cfg), ctypes.c_void_p(bad), ctypes.c_void_p(256),
+                                  None, err, 256)
+        assert rc == 1 and b"aligned" in err.value
+        rc = lib.lks_step_noalloc(ctypes.byref(cfg), ctypes.c_void_p(256), ctypes.c_void_p(256),
+                                  ctypes.c_void_p(256 + bad), err, 256)
+        assert rc == 1 and b"aligned" in err.value
 
 
 def test_noalloc_step_rejects_grids_beyond_its_scratch(L):
