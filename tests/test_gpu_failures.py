@@ -87,6 +87,7 @@ def test_divergence_is_reported_and_the_context_recovers(L, name, poison):
 def _free_bytes():
     import torch
     torch.cuda.synchronize()
+    torch.cuda.empty_cache()   # torch's cached blocks are not the library's
     return torch.cuda.mem_get_info()[0]
 
 
