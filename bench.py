@@ -7,10 +7,13 @@ sensitivity accumulation, binomial checkpointing with forward recomputation.  On
 is one full pass of the path: set_design -> forward (Alg. 1, J) -> adjoint (dJ/dgamma).
 MLUPS counts analysis node updates once per time step (nodes * time steps / s / 1e6).
 
-Also reported: the forward-only rate, the plain FP64 GPU path on the same grid over a shorter
-horizon with the FP32-vs-FP64 errors on J and dJ/dgamma, the forward-step kernel against the
-measured HBM copy bandwidth, the end-to-end rate through the public API with host buffers, the
-single-thread FP64 CPU oracle on a bounded sample, and SM clocks during the timed region.
+Also reported: the forward-only rate; the plain FP64 GPU path on the same workload at the full
+horizon (one pass) with the FP32-vs-FP64 errors on J and dJ/dgamma, and its fraction of the
+measured FP64 FMA rate; the forward and adjoint stencil steps against the measured HBM copy
+bandwidth (the "roofline" object names the one with the larger share of the pass); the transfer
+kernels from the committed ncu summary; the end-to-end rate through the public API with host
+buffers; the other named workloads (the 512^2 channel in both precisions, with its FP32 errors);
+the single-thread FP64 CPU oracle on a bounded sample; and SM clocks during the timed region.
 
 `--impl reference` times the CPU oracle (the method's plain FP64 restatement) as the
 reference arm on bounded samples of the same workload.
@@ -42,7 +45,10 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--horizon", type=int, default=None,
                     help="time steps per pass (default: the workload's full horizon)")
-    ap.add_argument("--fp64-horizon", type=int, default=60)
+    ap.add_argument("--fp64-horizon", type=int, default=None,
+                    help="time steps of the plain FP64 pass (default: the full horizon)")
+    ap.add_argument("--e2e-passes", type=int, default=3,
+                    help="passes of the end-to-end leg (at most --steps)")
     ap.add_argument("--timing-stride", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -108,6 +114,23 @@ def kernel_sources_sha1(names):
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()
+
+
+def committed_ncu(name, sources):
+    """A committed ncu summary (profiles/<name>.json) if the kernels it describes are built from
+    the same sources today, else None."""
+    p = os.path.join(ROOT, "profiles", name + ".json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    if d.get("sources_sha1") != kernel_sources_sha1(sources):
+        return None
+    return d
+
+
+TRANSFER_SOURCES = ("lks_transfer.cu", "lks_device.cuh", "lks_internal.h")
+FP64_SOURCES = ("lks_plain.cu", "lks_units.cuh", "lks_device.cuh", "lks_internal.h")
 
 
 def ncu_traffic(step):
@@ -324,11 +347,12 @@ def config_leg(lks, W, idx, prec, stream):
     e[2].record()
     torch.cuda.synchronize()
     st = s.stats()
+    grad = out.cpu().numpy()
     s.close()
     del s
     torch.cuda.empty_cache()
     node_steps = p.nodes * p.n_steps
-    return {"workload": f"{p.name}: {'D2Q9' if p.dim == 2 else 'D3Q15'} "
+    return grad, {"workload": f"{p.name}: {'D2Q9' if p.dim == 2 else 'D3Q15'} "
                         f"{'x'.join(str(n) for n in p.n[:p.dim])}, design "
                         f"{'x'.join(str(l) for l in p.L[:p.dim])}, {p.n_steps} steps",
             "dtype": "f64" if prec == lks.FP64 else "f32", "unit": UNIT,
@@ -468,60 +492,79 @@ def run_ours(args):
                       "l2": "state 268 MB per level > 129 MB L2; no flush needed",
                       "checkpointing": solver.stats()},
            "forward_mlups": fwd_mlups,
-           # the adjoint stencil step holds the largest share of the launch list
-           "roofline": {"bound": "hbm", "achieved": ach_adj, "peak": peak, "unit": "GB/s",
-                        "frac": ach_adj / peak, "traffic": ncu_traffic("adjoint_step"),
-                        "kernel": "adjoint stencil step: k_adj_bcT + k_fused_adj3d + "
-                                  "k_adj_bcorr",
-                        "concurrent": "the next step's transfer runs beside it on a side stream",
-                        "peak_kind": f"{peak_kind} hbm_gbs (copy)",
-                        "algorithmic_bytes_per_launch": bytes_adj,
-                        "avg_launch_ms": adj_step_ms, "samples": tm["adj_n"]},
-           "roofline_forward": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
-                                "frac": ach / peak, "traffic": ncu_traffic("forward_step"),
-                                "kernel": "forward stencil step: " + STEP3D_KERNELS.get(
-                                    solver.step_variant(), "?"),
-                                "variant": solver.step_variant(),
-                                "concurrent": "the next step's transfer runs beside it on a "
-                                              "side stream",
-                                "peak_kind": f"{peak_kind} hbm_gbs (copy)",
-                                "algorithmic_bytes_per_launch": bytes_fwd,
-                                "avg_launch_ms": fwd_step_ms, "samples": tm["fwd_n"]},
            "gpu_launches": launches, "clocks": clk, "J": J}
+    # share of the pass in each stencil step: the forward step runs for every time step and
+    # again for every recomputed one, the adjoint step once per time step
+    ck = solver.stats()
+    pass_ms = t_ms / args.steps
+    share_fwd = fwd_step_ms * (H + ck["recomputed_steps"]) / pass_ms
+    share_adj = adj_step_ms * H / pass_ms
+    rf = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+          "frac": ach / peak, "traffic": ncu_traffic("forward_step"),
+          "kernel": "forward stencil step: " + STEP3D_KERNELS.get(solver.step_variant(), "?"),
+          "variant": solver.step_variant(), "share_of_pass": share_fwd,
+          "launches_per_pass": H + ck["recomputed_steps"],
+          "concurrent": "the next step's transfer runs beside it on a side stream",
+          "peak_kind": f"{peak_kind} hbm_gbs (copy)",
+          "algorithmic_bytes_per_launch": bytes_fwd,
+          "avg_launch_ms": fwd_step_ms, "samples": tm["fwd_n"]}
+    ra = {"bound": "hbm", "achieved": ach_adj, "peak": peak, "unit": "GB/s",
+          "frac": ach_adj / peak, "traffic": ncu_traffic("adjoint_step"),
+          "kernel": "adjoint stencil step: k_adj_bcT + k_fused_adj3d + k_adj_bcorr",
+          "share_of_pass": share_adj, "launches_per_pass": H,
+          "concurrent": "the next step's transfer and the sensitivity gather run beside it on a "
+                        "side stream",
+          "peak_kind": f"{peak_kind} hbm_gbs (copy)",
+          "algorithmic_bytes_per_launch": bytes_adj,
+          "avg_launch_ms": adj_step_ms, "samples": tm["adj_n"]}
+    # the roofline line names the kernel with the larger share of the pass
+    out["roofline"] = dict(rf if share_fwd >= share_adj else ra)
+    out["roofline_forward"] = rf
+    out["roofline_adjoint"] = ra
+    J_last = J
+    g_last = g_dev.cpu().numpy()
     solver.set_timing(0)
 
     # end to end through the public API with pinned host buffers
     if not args.no_e2e:
         gamma_pin = torch.from_numpy(w.gamma).pin_memory()
         g_pin = torch.empty(w.gamma.shape, dtype=torch.float64).pin_memory()
+        n_e2e = max(1, min(args.steps, args.e2e_passes))
         torch.cuda.synchronize()
         barrier()
         t0 = time.perf_counter()
-        for _ in range(args.steps):
+        for _ in range(n_e2e):
             solver.set_design(gamma_pin)
             solver.forward()
             solver.adjoint(out=g_pin)
         torch.cuda.synchronize()
         dt = max_over_ranks(time.perf_counter() - t0, ws, dev)
         barrier()
-        out["e2e"] = {"value": replica_rate(node_steps, args.steps, ws, dt), "unit": UNIT,
+        out["e2e"] = {"value": replica_rate(node_steps, n_e2e, ws, dt), "unit": UNIT,
                       "h2d_bytes_per_step": int(w.gamma.nbytes),
-                      "d2h_bytes_per_step": int(w.gamma.nbytes) + 8}
+                      "d2h_bytes_per_step": int(w.gamma.nbytes) + 8, "passes": n_e2e}
     solver.close()
     del solver
     torch.cuda.empty_cache()
 
-    # plain FP64 GPU path on the same grid over a shorter horizon, with FP32 errors against it
+    # measured FMA rates: the arithmetic roofline of the plain FP64 path
+    if rank == 0:
+        out["alu_peaks"] = {"fp64_tflops": lks.fma_rate(lks.FP64, stream) / 1e12,
+                            "fp32_tflops": lks.fma_rate(lks.FP32, stream) / 1e12,
+                            "how": "lks_fma_rate: independent FMA chains over whole waves of "
+                                   "every SM, CUDA events, 5 launches after a warm-up"}
+    # plain FP64 GPU path on the same workload (the full horizon unless shortened), with the
+    # FP32 errors against it: the FP32 result of the last timed pass when the horizons agree
     if rank == 0 and not args.no_fp64:
-        wh = W.config(4, n_steps=args.fp64_horizon)
+        Hf = H if args.fp64_horizon is None else min(args.fp64_horizon, H)
+        wh = w if Hf == H else W.config(4, n_steps=Hf)
         res = {}
-        for prec in (lks.FP64, lks.FP32):
+        precs = (lks.FP64,) if Hf == H else (lks.FP64, lks.FP32)
+        for prec in precs:
             s = lks.Solver(wh.problem, prec, stream=stream)
             s.set_motion(wh.motion)
             s.set_design(torch.from_numpy(wh.gamma).to(dev))
             gout = torch.empty(wh.gamma.shape, dtype=torch.float64, device=dev)
-            s.forward()
-            s.adjoint(out=gout)  # warm-up pass
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
@@ -529,29 +572,59 @@ def run_ours(args):
             s.adjoint(out=gout)
             e1.record()
             torch.cuda.synchronize()
-            res[prec] = (Jh, gout.cpu().numpy(), e0.elapsed_time(e1))
+            res[prec] = (Jh, gout.cpu().numpy(), e0.elapsed_time(e1), s.stats())
             s.close()
             del s
             torch.cuda.empty_cache()
-        J64, g64, ms64 = res[lks.FP64]
-        J32, g32, ms32 = res[lks.FP32]
+        if Hf == H:
+            res[lks.FP32] = (J_last, g_last, pass_ms, ck)
+        J64, g64, ms64, st64 = res[lks.FP64]
+        J32, g32, ms32, _ = res[lks.FP32]
         out["fp64_plain"] = {
-            "value": nodes * args.fp64_horizon / (ms64 / 1000.0) / 1e6, "unit": UNIT,
-            "time_steps": args.fp64_horizon,
-            "fp32_same_horizon": nodes * args.fp64_horizon / (ms32 / 1000.0) / 1e6}
+            "value": nodes * Hf / (ms64 / 1000.0) / 1e6, "unit": UNIT,
+            "time_steps": Hf, "ms_per_pass": ms64,
+            "recomputed_steps": st64["recomputed_steps"],
+            "fp32_same_horizon": nodes * Hf / (ms32 / 1000.0) / 1e6,
+            "passes": 1}
+        alu = committed_ncu("ncu_fp64_plain", FP64_SOURCES)
+        if alu and alu.get("fp64_flop_per_node_step"):
+            flops = alu["fp64_flop_per_node_step"] * nodes * Hf
+            peak64 = out["alu_peaks"]["fp64_tflops"] * 1e12
+            out["fp64_plain"]["roofline"] = {
+                "bound": "alu", "achieved": flops / (ms64 / 1000.0) / 1e12,
+                "peak": peak64 / 1e12, "unit": "TFLOP/s",
+                "frac": flops / (ms64 / 1000.0) / peak64,
+                "flop_per_node_step": alu["fp64_flop_per_node_step"],
+                "peak_kind": "measured (lks_fma_rate, this run)",
+                "flop_source": "profiles/ncu_fp64_plain.json (ncu FP64 op counts per node-step "
+                               "of forward, recomputation and adjoint)"}
         out["accuracy_fp32_vs_fp64"] = {
-            "time_steps": args.fp64_horizon,
+            "workload": wh.problem.name, "time_steps": Hf, "window": list(wh.problem.win),
+            "J_fp64": J64, "J_fp32": J32,
             "J_rel": abs(J32 - J64) / abs(J64),
             "dJdgamma_rel_l2": float(np.linalg.norm(g32 - g64) / np.linalg.norm(g64)),
             "tolerance": {"J_rel": 1e-5, "dJdgamma_rel_l2": 1e-4}}
+    tr = committed_ncu("ncu_transfer", TRANSFER_SOURCES)
+    if rank == 0 and tr:
+        out["transfer"] = {k: tr[k] for k in ("kernels", "per_step", "note") if k in tr}
     if rank == 0 and not args.no_batch:
         out["batch2d"] = batch2d_leg(args, lks, W, stream)
     if rank == 0 and not args.no_configs:
-        # the other named workloads, one pass each (not the metric's configuration)
-        out["other_configs"] = {
-            "cfg0_2d_128_fp64": config_leg(lks, W, 0, lks.FP64, stream),
-            "cfg1_2d_512_fp32": config_leg(lks, W, 1, lks.FP32, stream),
-            "cfg3_3d_128_fp32": config_leg(lks, W, 3, lks.FP32, stream)}
+        # the other named workloads, one pass each (not the metric's configuration); the 512^2
+        # channel in both precisions, with the FP32 errors against FP64 at its full horizon
+        _, c0 = config_leg(lks, W, 0, lks.FP64, stream)
+        g1_32, c1_32 = config_leg(lks, W, 1, lks.FP32, stream)
+        g1_64, c1_64 = config_leg(lks, W, 1, lks.FP64, stream)
+        _, c3 = config_leg(lks, W, 3, lks.FP32, stream)
+        out["other_configs"] = {"cfg0_2d_128_fp64": c0, "cfg1_2d_512_fp32": c1_32,
+                                "cfg1_2d_512_fp64": c1_64, "cfg3_3d_128_fp32": c3}
+        w1 = W.config(1)
+        out["accuracy_fp32_vs_fp64_cfg1"] = {
+            "workload": w1.problem.name, "time_steps": w1.problem.n_steps,
+            "window": list(w1.problem.win),
+            "J_rel": abs(c1_32["J"] - c1_64["J"]) / abs(c1_64["J"]),
+            "dJdgamma_rel_l2": float(np.linalg.norm(g1_32 - g1_64) / np.linalg.norm(g1_64)),
+            "tolerance": {"J_rel": 1e-5, "dJdgamma_rel_l2": 1e-4}}
     if rank == 0:
         if ws == 1 and not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(4, n_steps=2)

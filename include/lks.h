@@ -253,6 +253,14 @@ lks_status lks_step_noalloc(const lks_config* cfg, const void* state_in, void* s
 const char* lks_last_error(const lks_ctx* ctx);
 void lks_destroy(lks_ctx* ctx);
 
+/* The device's measured fused multiply-add rate in precision (LKS_FP32 or LKS_FP64), in
+ * floating-point operations per second (2 per FMA), for the arithmetic roofline of the paths
+ * that are bound by it (the plain FP64 path).  The paper has no counterpart.  A kernel of
+ * independent FMA chains over whole waves of every SM, timed with CUDA events on `stream`
+ * (a cudaStream_t, may be NULL) over five launches after a warm-up; synchronises.  Allocates
+ * nothing.  LKS_ERR_ARG on a bad precision or NULL output, LKS_ERR_CUDA on a failed launch. */
+lks_status lks_fma_rate(int precision, void* stream, double* flops_per_s);
+
 /* Host-side fault injection for failure-detection tests (the paper has no counterpart): the
  * nth device allocation the library makes from now on (1 = the next one) reports failure
  * without calling the allocator, as if the device were out of memory; 0 switches injection

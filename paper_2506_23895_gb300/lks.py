@@ -28,7 +28,7 @@ EXPORTS = ("lks_workspace_bytes", "lks_create", "lks_set_design", "lks_set_motio
            "lks_batch_tile_shapes", "lks_batch_tuning", "lks_batch_stats",
            "lks_batch_last_error", "lks_batch_destroy", "lks_set_filter", "lks_volume",
            "lks_set_static", "lks_warm_start", "lks_set_adjoint_start", "lks_get_adjoint_state",
-           "lks_inject_alloc_failure")
+           "lks_inject_alloc_failure", "lks_fma_rate")
 
 
 class LksError(RuntimeError):
@@ -106,6 +106,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.lks_destroy.restype = None
     lib.lks_inject_alloc_failure.argtypes = [ctypes.c_int]
     lib.lks_inject_alloc_failure.restype = ctypes.c_int
+    lib.lks_fma_rate.argtypes = [ctypes.c_int, P, D]
+    lib.lks_fma_rate.restype = ctypes.c_int
     lib.lks_set_filter.argtypes = [P, ctypes.c_double, ctypes.c_double, ctypes.c_double]
     lib.lks_set_filter.restype = ctypes.c_int
     lib.lks_volume.argtypes = [P, ctypes.c_double, D, P, ctypes.c_int]
@@ -174,6 +176,18 @@ def make_config(problem, precision: int = FP32, max_steps: Optional[int] = None,
     for a in range(3):
         c.rot_axis[a] = ax[a]
     return c
+
+
+def fma_rate(precision: int, stream=None) -> float:
+    """Measured FMA throughput of the current device in flop/s (2 per FMA)."""
+    lib = load()
+    v = ctypes.c_double(0.0)
+    s = None if stream is None else int(stream.cuda_stream if hasattr(stream, "cuda_stream")
+                                         else stream)
+    st = lib.lks_fma_rate(precision, s, ctypes.byref(v))
+    if st != 0:
+        raise LksError(st, "lks_fma_rate failed")
+    return v.value
 
 
 def checkpoint_schedule(n_segments: int, free_slots: int):

@@ -95,3 +95,52 @@ def test_central_differences_at_seeded_cells(T):
     g32 = s32.adjoint()
     s32.close()
     assert np.linalg.norm(g32 - g) <= 1e-4 * np.linalg.norm(g)
+
+
+def test_central_differences_on_the_512_channel_geometry(T):
+    """Workload 1's geometry: a 512^2 channel with a 192^2 design that rotates and translates
+    sinusoidally (amplitude 20 cells, period 2000 steps), here over one full translation period
+    (2000 steps, J1 over the last 200).  dJ/dgamma through torch.autograd with a snapshot budget
+    that forces binomial checkpointing with recomputation, against central differences
+    (eps = 1e-4, Sec. 2.6) of the GPU FP64 path at 16 seeded cells with gamma in [0.2, 0.8]
+    among the largest sensitivities; then the FP32 path against FP64 within the stated
+    tolerances (1e-5 on J, 1e-4 relative L2 on dJ/dgamma)."""
+    torch, lks, ag = T
+    w = W.config(1, n_steps=2000)
+    p = w.problem
+    state_bytes = p.nodes * 32
+    s = lks.Solver(p, lks.FP64, ckpt_bytes=60 * state_bytes)
+    s.set_motion(w.motion)
+    gam = torch.tensor(w.gamma, device="cuda", requires_grad=True)
+    J = ag.objective(gam, s)
+    J.backward()
+    st = s.stats()
+    assert st["recomputed_steps"] > 0
+    g = gam.grad.cpu().numpy()
+    flat = g.reshape(-1)
+    gflat = w.gamma.reshape(-1)
+    thr = np.quantile(np.abs(flat), 0.99)
+    cand = np.where((gflat > 0.2) & (gflat < 0.8) & (np.abs(flat) >= thr))[0]
+    cells = np.random.default_rng(1).choice(cand, size=min(16, cand.size), replace=False)
+    assert cells.size == 16
+    eps = 1e-4
+    for c in cells:
+        gp = gflat.copy()
+        gm = gflat.copy()
+        gp[c] += eps
+        gm[c] -= eps
+        s.set_design(gp.reshape(w.gamma.shape))
+        Jp = s.forward()
+        s.set_design(gm.reshape(w.gamma.shape))
+        Jm = s.forward()
+        fd = (Jp - Jm) / (2 * eps)
+        assert abs(fd - flat[c]) <= 1e-4 * abs(flat[c]) + 1e-12 * np.abs(flat).max()
+    s.close()
+    s32 = lks.Solver(p, lks.FP32, ckpt_bytes=60 * p.nodes * 16)
+    s32.set_motion(w.motion)
+    s32.set_design(w.gamma)
+    J32 = s32.forward()
+    g32 = s32.adjoint()
+    s32.close()
+    assert abs(J32 - J.item()) <= 1e-5 * abs(J.item())
+    assert np.linalg.norm(g32 - g) <= 1e-4 * np.linalg.norm(g)
