@@ -744,6 +744,432 @@ __global__ void __launch_bounds__(ZCfg<TY_>::NTHR, ZCfg<TY_>::MINB)
         zbody<TY_, false>(tmap, a, smem, hfx, hfy, q0, q1, nplanes);
 }
 
+// ---------------------------------------------------------------- plane-pair z-march variant
+// The same step with two planes per iteration and packed single-precision arithmetic:
+//   * a thread owns one column of a 32 x 8 tile and evaluates f^eq at two consecutive planes
+//     (a, a + 1) per iteration, with the two planes' values held as float2 pairs, so the f^eq
+//     core, the gather sums and the z-accumulation run on paired FP32 instructions
+//     (__ffma2_rn, __fadd2_rn, __fmul2_rn: two operations per instruction issue);
+//   * the 12 values that leave the column travel through shared memory as (plane a, plane a+1)
+//     pairs: an in-plane shift keeps the pairing, so every exchange is one 8-byte store and one
+//     8-byte load for two nodes; the exchange buffers alternate, one block barrier per pair;
+//   * raw planes arrive through the same TMA boxes into a six-slot ring, two new planes per
+//     iteration, every thread waiting on the mbarriers of the planes it reads (bounded waits);
+//   * an iteration completes the outputs of planes a - 1 and a: plane a - 1 from the carried
+//     cz = 0 and cz = +1 sums of plane a - 1 and a - 2 plus the cz = -1 sums of plane a, plane
+//     a from its own cz = 0 sums, the carried cz = +1 sums of plane a - 1 and the cz = -1 sums
+//     of plane a + 1.
+// Derivatives are formed per plane in single precision as in feq_node; the arithmetic of f^eq,
+// the gather and the Brinkman update is that of the other variants, with the sums in a
+// different order (results agree to rounding).
+struct PCfg {
+    static constexpr int TX = 32, TY = 8;
+    static constexpr int HX = TX + 5, HY = TY + 4, FW = TX + 2, FX = FW + 1, FY = TY + 2;
+    static constexpr int NTHR = TX * TY, NHALO = FW * FY - TX * TY, FS = FX * FY;
+    static constexpr int NSLOT = 6;
+    static constexpr int MINB = 2;     // resident blocks per SM
+    static constexpr unsigned PLANE_BYTES = HX * HY * 16;
+    static constexpr int SLOT = (PLANE_BYTES + 127) / 128 * 128 / 16;   // float4 per ring slot
+    static constexpr size_t OFF_F = (size_t)NSLOT * SLOT * 16;
+    static constexpr size_t OFF_BAR = OFF_F + (size_t)2 * NCROSS * FS * 8;
+    static constexpr size_t SMEM = OFF_BAR + NSLOT * 8;
+};
+
+// Packed constants of the pair kernel (both lanes equal).
+struct PairK {
+    float2 A, hA, m15, w0, w1, w13, nw13, c45, w2, w23, nw23, w245, w2x2, nw2x2, mone;
+};
+
+__device__ __forceinline__ float2 padd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 pmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+// a - b: b * (-1) is exact, so this rounds once like a subtraction
+__device__ __forceinline__ float2 psub(float2 a, float2 b, float2 mone) {
+    return __ffma2_rn(b, mone, a);
+}
+
+// Dab = 2 d u_a / d x_b of one plane at one column (naming as in feq_node): c0 points at the
+// node in its ring plane, c is the node, um / up the velocity one plane below / above.
+struct D9 {
+    float xx, yx, zx, xy, yy, zy, xz, yz, zz;
+};
+
+template <bool EDGE>
+__device__ __forceinline__ void deriv_plane(const float4* __restrict__ c0, const float4& c,
+                                            const float3& um, const float3& up, int xm, int ym,
+                                            int zm, const float4& zfar, D9& d) {
+    constexpr int HXs = PCfg::HX;
+    if (EDGE) {
+        const float4 cm4 = make_float4(0.f, um.x, um.y, um.z);
+        const float4 cp4 = make_float4(0.f, up.x, up.y, up.z);
+        deriv2(xm, c, c0[-1], c0[1], xm == 2 ? c0[-2] : c, xm == 1 ? c0[2] : c, d.xx, d.yx, d.zx);
+        deriv2(ym, c, c0[-HXs], c0[HXs], ym == 2 ? c0[-2 * HXs] : c, ym == 1 ? c0[2 * HXs] : c,
+               d.xy, d.yy, d.zy);
+        deriv2(zm, c, cm4, cp4, zfar, zfar, d.xz, d.yz, d.zz);
+    } else {
+        const float4 e = c0[1], w = c0[-1], n = c0[HXs], s = c0[-HXs];
+        d.xx = e.y - w.y;
+        d.yx = e.z - w.z;
+        d.zx = e.w - w.w;
+        d.xy = n.y - s.y;
+        d.yy = n.z - s.z;
+        d.zy = n.w - s.w;
+        d.xz = up.x - um.x;
+        d.yz = up.y - um.y;
+        d.zz = up.z - um.z;
+    }
+}
+
+// f^eq of one column at two planes (lanes: plane a, plane a + 1) from the node values c* and
+// the derivatives of each plane: stores the 12 values that leave the column into the pair
+// planes at sFn (FS pairs apart) and returns rest, +z and -z.  The operations are those of
+// feq_node on pairs.
+__device__ __forceinline__ void feq_pair(const PairK& k, const float4& ca, const float4& cb,
+                                         const D9& da, const D9& db, float2* __restrict__ sFn,
+                                         float2& f_rest, float2& f_pz, float2& f_mz) {
+    constexpr int FS = PCfg::FS;
+    const float2 r = make_float2(ca.x, cb.x), ux = make_float2(ca.y, cb.y);
+    const float2 uy = make_float2(ca.z, cb.z), uz = make_float2(ca.w, cb.w);
+    const float2 ASxx = pmul(k.A, make_float2(da.xx, db.xx));
+    const float2 ASyy = pmul(k.A, make_float2(da.yy, db.yy));
+    const float2 ASzz = pmul(k.A, make_float2(da.zz, db.zz));
+    const float2 ASxy = pmul(k.hA, padd(make_float2(da.xy, db.xy), make_float2(da.yx, db.yx)));
+    const float2 ASxz = pmul(k.hA, padd(make_float2(da.xz, db.xz), make_float2(da.zx, db.zx)));
+    const float2 ASyz = pmul(k.hA, padd(make_float2(da.yz, db.yz), make_float2(da.zy, db.zy)));
+    const float2 uu = pfma(uz, uz, pfma(uy, uy, pmul(ux, ux)));
+    const float2 P = pfma(k.m15, uu, r);
+    f_rest = pmul(k.w0, P);
+    const float2 Px = padd(P, ASxx);
+    {
+        const float2 b = pmul(k.w1, pfma(pmul(k.c45, ux), ux, Px));
+        sFn[0 * FS] = pfma(k.w13, ux, b);
+        sFn[1 * FS] = pfma(k.nw13, ux, b);
+    }
+    {
+        const float2 b = pmul(k.w1, pfma(pmul(k.c45, uy), uy, padd(P, ASyy)));
+        sFn[2 * FS] = pfma(k.w13, uy, b);
+        sFn[3 * FS] = pfma(k.nw13, uy, b);
+    }
+    {
+        const float2 b = pmul(k.w1, pfma(pmul(k.c45, uz), uz, padd(P, ASzz)));
+        f_pz = pfma(k.w13, uz, b);
+        f_mz = pfma(k.nw13, uz, b);
+    }
+    const float2 T0 = pmul(k.w2, padd(padd(Px, ASyy), ASzz));
+    const float2 s1 = padd(ux, uy), d1 = psub(ux, uy, k.mone);
+    const float2 q1 = padd(ASxz, ASyz), q2 = psub(ASyz, ASxz, k.mone);
+    {   // (+,+,+) / (-,-,-)
+        const float2 cu = padd(s1, uz);
+        const float2 sym = pfma(pmul(k.w245, cu), cu, pfma(k.w2x2, padd(ASxy, q1), T0));
+        sFn[4 * FS] = pfma(k.w23, cu, sym);
+        sFn[11 * FS] = pfma(k.nw23, cu, sym);
+    }
+    {   // (-,+,+) / (+,-,-)
+        const float2 cu = psub(uz, d1, k.mone);
+        const float2 sym = pfma(pmul(k.w245, cu), cu, pfma(k.w2x2, psub(q2, ASxy, k.mone), T0));
+        sFn[5 * FS] = pfma(k.w23, cu, sym);
+        sFn[10 * FS] = pfma(k.nw23, cu, sym);
+    }
+    {   // (+,-,+) / (-,+,-)
+        const float2 cu = padd(uz, d1);
+        const float2 sym = pfma(pmul(k.w245, cu), cu, pfma(k.nw2x2, padd(ASxy, q2), T0));
+        sFn[6 * FS] = pfma(k.w23, cu, sym);
+        sFn[9 * FS] = pfma(k.nw23, cu, sym);
+    }
+    {   // (-,-,+) / (+,+,-)
+        const float2 cu = psub(uz, s1, k.mone);
+        const float2 sym = pfma(pmul(k.w245, cu), cu, pfma(k.w2x2, psub(ASxy, q1, k.mone), T0));
+        sFn[7 * FS] = pfma(k.w23, cu, sym);
+        sFn[8 * FS] = pfma(k.nw23, cu, sym);
+    }
+}
+
+struct PairArgs {
+    FusedArgs f;
+    PairK k;
+    float2 bf2[3];   // body force, both lanes
+    int has_bf;
+};
+
+// Write one output node (Brinkman update, store, boundary copies it sources).
+__device__ __forceinline__ void pair_out(const Geom& g, const PairArgs& a, int gx, int gy,
+                                         int qz, float r, float ux, float uy, float uz,
+                                         bool box_col, const float4* kus_col,
+                                         long long box_plane, float4* out_col_ptr,
+                                         long long zstride, bool bc_col) {
+    float4 o;
+    o.x = r;
+    const int bz = qz - g.blo[2];
+    if (box_col && bz >= 0 && bz < g.bn[2]) {
+        const float4 ks = kus_col[(long long)qz * box_plane];
+        const float inv = 1.f / (1.f + ks.x);
+        o.y = fmaf(ks.x, ks.y, ux) * inv;
+        o.z = fmaf(ks.x, ks.z, uy) * inv;
+        o.w = fmaf(ks.x, ks.w, uz) * inv;
+    } else {
+        o.y = ux;
+        o.z = uy;
+        o.w = uz;
+    }
+    out_col_ptr[(long long)qz * zstride] = o;
+    if (bc_col || qz == 1 || qz == g.n[2] - 2) write_bc_f(g, gx, gy, qz, o, a.f.out);
+}
+
+template <bool IN>
+__device__ __forceinline__ void pbody(const CUtensorMap& tmap, const PairArgs& a,
+                                      unsigned char* smem, int hfx, int hfy, int q0, int q1) {
+    using C = PCfg;
+    constexpr int TX = C::TX, TY = C::TY, HX = C::HX, FX = C::FX;
+    constexpr int FS = C::FS, NSLOT = C::NSLOT;
+    float4* raw = reinterpret_cast<float4*>(smem);
+    float2* sFbase = reinterpret_cast<float2*>(smem + C::OFF_F);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::OFF_BAR);
+    const Geom& g = a.f.g;
+    const PairK& k = a.k;
+    const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+    const int tid = threadIdx.x;
+    const int tx = tid % TX, ty = tid / TX;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int gx = x0 + tx, gy = y0 + ty;
+    const int hgx = x0 - 1 + hfx, hgy = y0 - 1 + hfy;
+    const bool edge = !IN && ((x0 - 1 <= 0) || (x0 + TX >= nx - 1) || (y0 - 1 <= 0) ||
+                              (y0 + TY >= ny - 1));
+    const int pxm = axis_mode(gx, nx), pym = axis_mode(gy, ny);
+    const int rxm = axis_mode(hgx, nx), rym = axis_mode(hgy, ny);
+    const int hp = (ty + 2) * HX + (tx + 2);
+    const int hr = (hfy + 1) * HX + (hfx + 1);
+    const int fop = (ty + 1) * FX + (tx + 1);
+    const int forr = hfy * FX + hfx;
+    constexpr int RIMW = (C::NHALO + 31) / 32 * 32;
+    const bool has_rim = tid < RIMW;
+    const bool out_col = IN || (gx >= 1 && gx <= nx - 2 && gy >= 1 && gy <= ny - 2);
+    const bool bc_col = !IN && (gx == 1 || gx == nx - 2 || gy == 1 || gy == ny - 2);
+    const int bxx = gx - g.blo[0], byy = gy - g.blo[1];
+    const bool box_col = g.boxN > 0 && bxx >= 0 && byy >= 0 && bxx < g.bn[0] && byy < g.bn[1];
+    const long long box_plane = (long long)g.bn[0] * g.bn[1];
+    const float4* kus_col =
+        a.f.kus + ((long long)byy * g.bn[0] + bxx) - (long long)g.blo[2] * box_plane;
+    const long long zstride = (long long)nx * ny;
+    const bool in_xy = IN || (gx < nx && gy < ny);
+    const bool rim_in_xy = IN || (hgx >= 0 && hgx < nx && hgy >= 0 && hgy < ny);
+    float4* out_col_ptr = a.f.out + ((long long)gy * nx + gx);
+    const int zlo = max(q0, 1), zhi = min(q1 - 1, nz - 2);
+    const int npairs = ((q1 - q0 + 1) >> 1) + 1;
+    const int nplanes = 2 * npairs + 2;   // raw planes q0-2 .. q0-1+2 npairs (load j = plane - q0 + 2)
+
+    bool ok = true;
+    // prologue: loads 0..3; u of plane q0-2 and the node of plane q0-1 into registers
+    float3 um, rum;
+    float4 ca, rca;
+    {
+        bool good = true;
+        for (int j = 0; j < 4; ++j) good = mbar_wait(smem_addr(&bars[j]), 0) && good;
+        const float4 v = raw[hp];
+        um = make_float3(v.y, v.z, v.w);
+        ca = raw[(size_t)C::SLOT + hp];
+        const float4 rv = raw[hr];
+        rum = make_float3(rv.y, rv.z, rv.w);
+        rca = raw[(size_t)C::SLOT + hr];
+        ok = !__syncthreads_or(!good);
+    }
+    // carried sums: pend = (cz = 0 of plane a-1) + (cz = +1 of plane a-2), pc = cz = +1 of a-1
+    float pend_r = 0.f, pend_x = 0.f, pend_y = 0.f, pend_z = 0.f;
+    float pc_r = 0.f, pc_x = 0.f, pc_y = 0.f, pc_z = 0.f;
+    int ik = NSLOT;   // next load to issue
+    for (int it = 0; ok && it < npairs; ++it) {
+        const int a0 = q0 - 1 + 2 * it;     // planes a0, a0 + 1
+        const int j1 = 2 * it + 2, j2 = 2 * it + 3;   // loads of planes a0 + 1, a0 + 2
+        bool good = true;
+        if (it > 0) good = mbar_wait(smem_addr(&bars[j1 % NSLOT]), (j1 / NSLOT) & 1);
+        good = mbar_wait(smem_addr(&bars[j2 % NSLOT]), (j2 / NSLOT) & 1) && good;
+        const float4* ra = raw + (size_t)((2 * it + 1) % NSLOT) * C::SLOT;
+        const float4* rb = raw + (size_t)(j1 % NSLOT) * C::SLOT;
+        const float4* rc = raw + (size_t)(j2 % NSLOT) * C::SLOT;
+        float2* sF = sFbase + (size_t)(it & 1) * NCROSS * FS;
+        const float4 cb = rb[hp], cc = rc[hp];
+        const float3 ub = make_float3(cb.y, cb.z, cb.w), uc = make_float3(cc.y, cc.z, cc.w);
+        const float3 ua = make_float3(ca.y, ca.z, ca.w);
+        float2 f_rest, f_pz, f_mz;
+        const int zma = a0 == 0 ? 1 : (a0 == nz - 1 ? 2 : 0);
+        const int zmb = a0 + 1 == 0 ? 1 : (a0 + 1 == nz - 1 ? 2 : 0);
+        D9 da, db;
+        if (!edge && zma == 0 && zmb == 0) {
+            const float4 z0 = make_float4(0.f, 0.f, 0.f, 0.f);
+            deriv_plane<false>(ra + hp, ca, um, ub, 0, 0, 0, z0, da);
+            deriv_plane<false>(rb + hp, cb, ua, uc, 0, 0, 0, z0, db);
+            feq_pair(k, ca, cb, da, db, sF + fop, f_rest, f_pz, f_mz);
+            if (has_rim) {
+                const float4 rcb = rb[hr], rcc = rc[hr];
+                const float3 rub = make_float3(rcb.y, rcb.z, rcb.w);
+                const float3 ruc = make_float3(rcc.y, rcc.z, rcc.w);
+                const float3 rua = make_float3(rca.y, rca.z, rca.w);
+                deriv_plane<false>(ra + hr, rca, rum, rub, 0, 0, 0, z0, da);
+                deriv_plane<false>(rb + hr, rcb, rua, ruc, 0, 0, 0, z0, db);
+                float2 d0, d1, d2;
+                feq_pair(k, rca, rcb, da, db, sF + forr, d0, d1, d2);
+                rum = rub;
+                rca = rcc;
+            }
+        } else {
+            // plane two away for one-sided z differences, straight from global memory
+            float4 zfa = make_float4(0.f, 0.f, 0.f, 0.f), zfb = zfa;
+            if (zma != 0 && in_xy)
+                zfa = a.f.src[((long long)(zma == 1 ? 2 : nz - 3) * ny + gy) * nx + gx];
+            if (zmb != 0 && in_xy)
+                zfb = a.f.src[((long long)(zmb == 1 ? 2 : nz - 3) * ny + gy) * nx + gx];
+            deriv_plane<true>(ra + hp, ca, um, ub, pxm, pym, zma, zfa, da);
+            deriv_plane<true>(rb + hp, cb, ua, uc, pxm, pym, zmb, zfb, db);
+            feq_pair(k, ca, cb, da, db, sF + fop, f_rest, f_pz, f_mz);
+            if (has_rim) {
+                const float4 rcb = rb[hr], rcc = rc[hr];
+                const float3 rub = make_float3(rcb.y, rcb.z, rcb.w);
+                const float3 ruc = make_float3(rcc.y, rcc.z, rcc.w);
+                const float3 rua = make_float3(rca.y, rca.z, rca.w);
+                float4 rza = make_float4(0.f, 0.f, 0.f, 0.f), rzb = rza;
+                if (zma != 0 && rim_in_xy)
+                    rza = a.f.src[((long long)(zma == 1 ? 2 : nz - 3) * ny + hgy) * nx + hgx];
+                if (zmb != 0 && rim_in_xy)
+                    rzb = a.f.src[((long long)(zmb == 1 ? 2 : nz - 3) * ny + hgy) * nx + hgx];
+                deriv_plane<true>(ra + hr, rca, rum, rub, rxm, rym, zma, rza, da);
+                deriv_plane<true>(rb + hr, rcb, rua, ruc, rxm, rym, zmb, rzb, db);
+                float2 d0, d1, d2;
+                feq_pair(k, rca, rcb, da, db, sF + forr, d0, d1, d2);
+                rum = rub;
+                rca = rcc;
+            }
+        }
+        um = ub;
+        ca = cc;
+        if (__syncthreads_or(!good)) {
+            ok = false;
+            break;
+        }
+        // every thread is past its reads of planes a0 and a0 + 1: their slots take the next
+        // loads (the first iteration also refills the slot of plane q0 - 2)
+        if (tid == 0) {
+            const int jmax = min(2 * it + 9, nplanes);
+            if (ik < jmax) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            for (; ik < jmax; ++ik)
+                tma_load_box(smem_addr(raw + (size_t)(ik % NSLOT) * C::SLOT), &tmap, x0 - 2,
+                             y0 - 2, q0 - 2 + ik, smem_addr(&bars[ik % NSLOT]), C::PLANE_BYTES);
+        }
+        const float2* sFp = sF + fop;
+        const float2 fpx = sFp[0 * FS - 1], fmx = sFp[1 * FS + 1];
+        const float2 fpy = sFp[2 * FS - FX], fmy = sFp[3 * FS + FX];
+        const float2 cpp_p = sFp[4 * FS - 1 - FX], cmp_p = sFp[5 * FS + 1 - FX];
+        const float2 cpm_p = sFp[6 * FS - 1 + FX], cmm_p = sFp[7 * FS + 1 + FX];
+        const float2 cpp_m = sFp[8 * FS - 1 - FX], cmp_m = sFp[9 * FS + 1 - FX];
+        const float2 cpm_m = sFp[10 * FS - 1 + FX], cmm_m = sFp[11 * FS + 1 + FX];
+        // cz = -1 group of planes (a0, a0 + 1): completes planes (a0 - 1, a0)
+        float2 Mr, Mx, My;
+        {
+            const float2 sxp = padd(cpp_m, cpm_m), sxm = padd(cmp_m, cmm_m);
+            const float2 syp = padd(cpp_m, cmp_m), sym = padd(cpm_m, cmm_m);
+            Mr = padd(padd(sxp, sxm), f_mz);
+            Mx = psub(sxp, sxm, k.mone);
+            My = psub(syp, sym, k.mone);
+        }
+        // cz = 0 group of planes (a0, a0 + 1)
+        const float2 Zr = padd(padd(padd(f_rest, fpx), padd(fmx, fpy)), fmy);
+        const float2 Zx = psub(fpx, fmx, k.mone), Zy = psub(fpy, fmy, k.mone);
+        // cz = +1 group of planes (a0, a0 + 1): into planes (a0 + 1, a0 + 2)
+        float2 Pr, Px, Py;
+        {
+            const float2 sxp = padd(cpp_p, cpm_p), sxm = padd(cmp_p, cmm_p);
+            const float2 syp = padd(cpp_p, cmp_p), sym = padd(cpm_p, cmm_p);
+            Pr = padd(padd(sxp, sxm), f_pz);
+            Px = psub(sxp, sxm, k.mone);
+            Py = psub(syp, sym, k.mone);
+        }
+        // outputs of planes a0 - 1 (lane x) and a0 (lane y)
+        float2 orr = padd(make_float2(pend_r, Zr.x + pc_r), Mr);
+        float2 oxx = padd(make_float2(pend_x, Zx.x + pc_x), Mx);
+        float2 oyy = padd(make_float2(pend_y, Zy.x + pc_y), My);
+        float2 ozz = psub(make_float2(pend_z, pc_z), Mr, k.mone);
+        if (a.has_bf) {
+            oxx = padd(oxx, a.bf2[0]);
+            oyy = padd(oyy, a.bf2[1]);
+            ozz = padd(ozz, a.bf2[2]);
+        }
+        pend_r = Zr.y + Pr.x;
+        pend_x = Zx.y + Px.x;
+        pend_y = Zy.y + Py.x;
+        pend_z = Pr.x;
+        pc_r = Pr.y;
+        pc_x = Px.y;
+        pc_y = Py.y;
+        pc_z = Pr.y;
+        if (out_col) {
+            if (a0 - 1 >= zlo && a0 - 1 <= zhi)
+                pair_out(g, a, gx, gy, a0 - 1, orr.x, oxx.x, oyy.x, ozz.x, box_col, kus_col,
+                         box_plane, out_col_ptr, zstride, bc_col);
+            if (a0 >= zlo && a0 <= zhi)
+                pair_out(g, a, gx, gy, a0, orr.y, oxx.y, oyy.y, ozz.y, box_col, kus_col,
+                         box_plane, out_col_ptr, zstride, bc_col);
+        }
+    }
+    if (!ok) {
+        if (tid == 0) {
+            atomicOr(a.f.err, 8);
+            const long long t0 = clock64();
+            while (clock64() - t0 < (1LL << 28)) {
+            }
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(PCfg::NTHR, PCfg::MINB)
+    k_zpair3d(const __grid_constant__ CUtensorMap tmap, const PairArgs a) {
+    using C = PCfg;
+    constexpr int TX = C::TX, TY = C::TY, FW = C::FW, FY = C::FY;
+    constexpr int NSLOT = C::NSLOT;
+    extern __shared__ __align__(128) unsigned char smem[];
+    float4* raw = reinterpret_cast<float4*>(smem);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::OFF_BAR);
+    const Geom& g = a.f.g;
+    const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+    const int tid = threadIdx.x;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int q0 = blockIdx.z * a.f.zchunk;
+    const int q1 = min(nz, q0 + a.f.zchunk);
+    const int npairs = ((q1 - q0 + 1) >> 1) + 1;
+    const int nplanes = 2 * npairs + 2;
+    constexpr int RIMW = (C::NHALO + 31) / 32 * 32;
+    const int rr = tid < C::NHALO ? tid : tid - (RIMW - C::NHALO);
+    int hfx = 0, hfy = 0;
+    if (tid < RIMW) {
+        if (rr < FW) {
+            hfx = rr;
+        } else if (rr < 2 * FW) {
+            hfx = rr - FW;
+            hfy = FY - 1;
+        } else if (rr < 2 * FW + TY) {
+            hfy = 1 + (rr - 2 * FW);
+        } else {
+            hfx = FW - 1;
+            hfy = 1 + (rr - 2 * FW - TY);
+        }
+    }
+    if ((smem_addr(smem) & 127u) != 0u) {
+        if (tid == 0) atomicOr(a.f.err, 16);
+        return;
+    }
+    if (tid == 0) {
+        for (int s = 0; s < NSLOT; ++s) mbar_init(smem_addr(&bars[s]));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        for (int j = 0; j < NSLOT && j < nplanes; ++j)
+            tma_load_box(smem_addr(raw + (size_t)j * C::SLOT), &tmap, x0 - 2, y0 - 2, q0 - 2 + j,
+                         smem_addr(&bars[j]), C::PLANE_BYTES);
+    }
+    __syncthreads();
+    const bool interior = x0 >= 3 && x0 + TX + 2 <= nx - 1 && y0 >= 3 && y0 + TY + 2 <= ny - 1;
+    if (interior)
+        pbody<true>(tmap, a, smem, hfx, hfy, q0, q1);
+    else
+        pbody<false>(tmap, a, smem, hfx, hfy, q0, q1);
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     if (!fn) {
@@ -824,8 +1250,46 @@ cudaError_t launch_zstep(const Geom& g, const CUtensorMap& map, const FusedArgs&
     return cudaGetLastError();
 }
 
+cudaError_t launch_zpair(const Geom& g, const CUtensorMap& map, const FusedArgs& f0,
+                         cudaStream_t st) {
+    using C = PCfg;
+    static std::atomic<unsigned> attr{0};   // devices whose shared-memory limit is raised
+    if (!device_done(attr)) {
+        cudaError_t e = cudaFuncSetAttribute(k_zpair3d, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)C::SMEM);
+        if (e != cudaSuccess) return e;
+        device_mark(attr);
+    }
+    PairArgs a;
+    a.f = f0;
+    const auto two = [](float v) { return make_float2(v, v); };
+    a.k.A = two(f0.A);
+    a.k.hA = two(0.5f * f0.A);
+    a.k.m15 = two(-1.5f);
+    a.k.w0 = two(f0.w0);
+    a.k.w1 = two(f0.w1);
+    a.k.w13 = two(3.f * f0.w1);
+    a.k.nw13 = two(-3.f * f0.w1);
+    a.k.c45 = two(4.5f);
+    a.k.w2 = two(f0.w2);
+    a.k.w23 = two(3.f * f0.w2);
+    a.k.nw23 = two(-3.f * f0.w2);
+    a.k.w245 = two(4.5f * f0.w2);
+    a.k.w2x2 = two(2.f * f0.w2);
+    a.k.nw2x2 = two(-2.f * f0.w2);
+    a.k.mone = two(-1.f);
+    for (int d = 0; d < 3; ++d) a.bf2[d] = two(f0.bf[d]);
+    a.has_bf = (f0.bf[0] != 0.f || f0.bf[1] != 0.f || f0.bf[2] != 0.f) ? 1 : 0;
+    const int tiles_x = (g.n[0] + C::TX - 1) / C::TX, tiles_y = (g.n[1] + C::TY - 1) / C::TY;
+    a.f.zchunk = fused_zchunk_waves(g, (long long)tiles_x * tiles_y, C::MINB);
+    const int chunks = (g.n[2] + a.f.zchunk - 1) / a.f.zchunk;
+    k_zpair3d<<<dim3(tiles_x, tiles_y, chunks), C::NTHR, C::SMEM, st>>>(map, a);
+    return cudaGetLastError();
+}
+
 // One fused forward step src -> dst in variant v (0: shared-memory z-march with two barriers
-// per plane, 1: register z-march), both on 32 x 8 tiles.  Returns a CUDA error code.
+// per plane, 1: register z-march, 2: plane-pair z-march with packed arithmetic), all on
+// 32 x 8 tiles.  Returns a CUDA error code.
 cudaError_t launch_fused_step3d(const Geom& g, const V4<float>* src, const V4<float>* kus,
                                 V4<float>* dst, int* err, cudaStream_t st, int v) {
     FusedArgs a;
@@ -840,6 +1304,10 @@ cudaError_t launch_fused_step3d(const Geom& g, const V4<float>* src, const V4<fl
     a.w2 = (float)(1.0 / 72.0);
     for (int k = 0; k < 3; ++k) a.bf[k] = (float)g.body[k];
     CUtensorMap map;
+    if (v == 2) {
+        if (!encode_state_map(&map, src, g, PCfg::HX, PCfg::HY)) return cudaErrorInvalidValue;
+        return launch_zpair(g, map, a, st);
+    }
     if (v == 1) {
         if (!encode_state_map(&map, src, g, ZCfg<8>::HX, ZCfg<8>::HY)) return cudaErrorInvalidValue;
         return launch_zstep<8>(g, map, a, st);

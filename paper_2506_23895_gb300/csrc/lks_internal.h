@@ -141,7 +141,7 @@ struct FaceOffsets {
 };
 bool fused3d_eligible(const Geom& g);
 int fused_zchunk_waves(const Geom& g, long long tiles, int per_sm);
-constexpr int kStep3dVariants = 2;
+constexpr int kStep3dVariants = 3;
 cudaError_t launch_fused_step3d(const Geom& g, const V4<float>* src, const V4<float>* kus,
                                 V4<float>* dst, int* err, cudaStream_t st, int variant);
 // Offsets of the six face arrays (3 floats per face node) and their total length.
