@@ -44,6 +44,51 @@ struct Lat<3> {
     }
 };
 
+// ------------------------------------------------------------------ weights as used
+// The constants the kernels multiply by, per number type.  The scheme keeps a uniform state
+// uniform only through exact identities of the lattice weights:
+//   mass        w0 + 2D w1 + 2^D w2 = 1                (coefficient of rho - rho0 in rho*)
+//   velocity    2 (3 w1) + 2^D (3 w2) = 1              (coefficient of u in u*, and of mu_u in
+//                                                       3 U~ in the adjoint)
+//   kinetic     2 (4.5 w1) + 2^D (4.5 w2) = 1.5         (the (c.u)^2 terms against -1.5 u^2)
+//   adjoint     2 (9 w1) + 2^D (9 w2) = 3              (9 S~ against 3 R~)
+// In double the nominal fractions satisfy them to rounding.  In single precision 1/9, 1/72 and
+// 1/3 round so that, e.g., 2 fl(3 fl(1/9)) + 8 fl(3 fl(1/72)) = 1 + 3e-8: every step would
+// multiply the velocity by that factor, a drift that grows over a flow-through time.  So the
+// single-precision kernels multiply by separate constants w3_1 = "3 w1", w3_2 = "3 w2",
+// h_1 = "4.5 w1", h_2 = "4.5 w2", s_1 = "9 w1", s_2 = "9 w2", chosen so that every identity
+// above holds exactly for the stored values: h_1 = 1/2, h_2 = 4.5 w2 and s_1 = 1, s_2 = 9 w2
+// are exact binary fractions; w3_1 = fl(1/3) and w3_2 = (1 - 2 w3_1) / 2^D, which is exact in
+// binary; w1 = fl(1/9) and w2 one ulp below fl(w2 nominal), so that w0 = 1 - 2D w1 - 2^D w2 is
+// a single-precision number.  Each differs from its nominal value by less than 1e-7 relative.
+template <class T, int D>
+struct Wts;
+
+template <>
+struct Wts<double, 3> {
+    static constexpr double w0 = 2.0 / 9.0, w1 = 1.0 / 9.0, w2 = 1.0 / 72.0;
+    static constexpr double w3_1 = 1.0 / 3.0, w3_2 = 1.0 / 24.0;
+    static constexpr double h_1 = 0.5, h_2 = 0.0625, s_1 = 1.0, s_2 = 0.125;
+};
+template <>
+struct Wts<double, 2> {
+    static constexpr double w0 = 4.0 / 9.0, w1 = 1.0 / 9.0, w2 = 1.0 / 36.0;
+    static constexpr double w3_1 = 1.0 / 3.0, w3_2 = 1.0 / 12.0;
+    static constexpr double h_1 = 0.5, h_2 = 0.125, s_1 = 1.0, s_2 = 0.25;
+};
+template <>
+struct Wts<float, 3> {
+    static constexpr float w0 = 0x1.c71c72p-3f, w1 = 0x1.c71c72p-4f, w2 = 0x1.c71c70p-7f;
+    static constexpr float w3_1 = 0x1.555556p-2f, w3_2 = 0x1.555554p-5f;
+    static constexpr float h_1 = 0.5f, h_2 = 0.0625f, s_1 = 1.0f, s_2 = 0.125f;
+};
+template <>
+struct Wts<float, 2> {
+    static constexpr float w0 = 0x1.c71c72p-2f, w1 = 0x1.c71c72p-4f, w2 = 0x1.c71c70p-6f;
+    static constexpr float w3_1 = 0x1.555556p-2f, w3_2 = 0x1.555554p-4f;
+    static constexpr float h_1 = 0.5f, h_2 = 0.125f, s_1 = 1.0f, s_2 = 0.25f;
+};
+
 // ------------------------------------------------------------------ indexing
 
 __device__ __forceinline__ long long node_index(const Geom& g, int x, int y, int z) {

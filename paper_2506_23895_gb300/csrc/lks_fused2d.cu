@@ -321,31 +321,32 @@ __device__ __forceinline__ bool interior_tile(const Geom& g, int x0, int y0) {
 // opposite directions sharing their symmetric part.
 __device__ __forceinline__ void feq8_v(const float4& v, float A, float gxx, float gyx, float gxy,
                                        float gyy, float f[8]) {
-    constexpr float w1 = 1.f / 9.f, w2 = 1.f / 36.f;
+    // the weight products w1, 4.5 w1, 3 w1, ... are those of Wts<float, 2>, which keep the
+    // lattice identities exact in single precision
+    using W = Wts<float, 2>;
     const float ux = v.y, uy = v.z;
     const float base = FMA_(-1.5f, FMA_(ux, ux, MUL_(uy, uy)), v.x);
     const float ax = MUL_(A, MUL_(2.f, gxx)), ay = MUL_(A, MUL_(2.f, gyy));
     const float sd = ADD_(MUL_(2.f, gxx), MUL_(2.f, gyy)), so = MUL_(2.f, ADD_(gxy, gyx));
     const float ad = MUL_(A, ADD_(sd, so)), ae = MUL_(A, SUB_(sd, so));
     const float cpp = ADD_(ux, uy), cmp = SUB_(uy, ux);
-    const float sx = ADD_(FMA_(MUL_(4.5f, ux), ux, base), ax);
-    const float sy = ADD_(FMA_(MUL_(4.5f, uy), uy, base), ay);
-    const float spp = ADD_(FMA_(MUL_(4.5f, cpp), cpp, base), ad);
-    const float smp = ADD_(FMA_(MUL_(4.5f, cmp), cmp, base), ae);
-    f[0] = MUL_(w1, FMA_(3.f, ux, sx));
-    f[1] = MUL_(w1, FMA_(3.f, uy, sy));
-    f[2] = MUL_(w1, FMA_(-3.f, ux, sx));
-    f[3] = MUL_(w1, FMA_(-3.f, uy, sy));
-    f[4] = MUL_(w2, FMA_(3.f, cpp, spp));
-    f[5] = MUL_(w2, FMA_(3.f, cmp, smp));
-    f[6] = MUL_(w2, FMA_(-3.f, cpp, spp));
-    f[7] = MUL_(w2, FMA_(-3.f, cmp, smp));
+    const float sx = FMA_(MUL_(W::h_1, ux), ux, MUL_(W::w1, ADD_(base, ax)));
+    const float sy = FMA_(MUL_(W::h_1, uy), uy, MUL_(W::w1, ADD_(base, ay)));
+    const float spp = FMA_(MUL_(W::h_2, cpp), cpp, MUL_(W::w2, ADD_(base, ad)));
+    const float smp = FMA_(MUL_(W::h_2, cmp), cmp, MUL_(W::w2, ADD_(base, ae)));
+    f[0] = FMA_(W::w3_1, ux, sx);
+    f[1] = FMA_(W::w3_1, uy, sy);
+    f[2] = FMA_(-W::w3_1, ux, sx);
+    f[3] = FMA_(-W::w3_1, uy, sy);
+    f[4] = FMA_(W::w3_2, cpp, spp);
+    f[5] = FMA_(W::w3_2, cmp, smp);
+    f[6] = FMA_(-W::w3_2, cpp, spp);
+    f[7] = FMA_(-W::w3_2, cmp, smp);
 }
 
 // Rest direction: f_0 = w0 (rho - rho0 - 1.5 u^2).
 __device__ __forceinline__ float feq0_v(const float4& v) {
-    constexpr float w0 = 4.f / 9.f;
-    return MUL_(w0, FMA_(-1.5f, FMA_(v.y, v.y, MUL_(v.z, v.z)), v.x));
+    return MUL_(Wts<float, 2>::w0, FMA_(-1.5f, FMA_(v.y, v.y, MUL_(v.z, v.z)), v.x));
 }
 
 // Output node from its nine gathered values: rho* = sum f_i, u* = sum c_i f_i (Eqs. rho, u),
@@ -664,7 +665,7 @@ __device__ __forceinline__ void adj_tile(const Inst& I, int x0, int y0, const Ob
                                          int lam_in, int lam_out, int sn, int sp, float4* M,
                                          float* Q) {
     constexpr int HX = TX + 4, HY = TY + 4, FX = TX + 2, FY = TY + 2, FN = FX * FY;
-    constexpr float w1 = 1.f / 9.f, w2 = 1.f / 36.f, w0 = 4.f / 9.f;
+    using W = Wts<float, 2>;
     const Geom& g = I.g;
     const int n0 = g.n[0], n1 = g.n[1];
     const float4* lam = (const float4*)I.bufs[lam_in];
@@ -720,22 +721,25 @@ __device__ __forceinline__ void adj_tile(const Inst& I, int x0, int y0, const Ob
         const float4 xp = M[s + 1], xm = M[s - 1], yp = M[s + HX], ym = M[s - HX];
         const float4 pp = M[s + HX + 1], mp = M[s + HX - 1], mm = M[s - HX - 1],
                      pm = M[s - HX + 1];
-        const float a1 = w1 * (xp.x + xp.y), a3 = w1 * (xm.x - xm.y);
-        const float a2 = w1 * (yp.x + yp.z), a4 = w1 * (ym.x - ym.z);
-        const float a5 = w2 * (pp.x + pp.y + pp.z), a6 = w2 * (mp.x - mp.y + mp.z);
-        const float a7 = w2 * (mm.x - mm.y - mm.z), a8 = w2 * (pm.x + pm.y - pm.z);
-        Q[k] = w0 * c0.x + a1 + a2 + a3 + a4 + a5 + a6 + a7 + a8;
-        Q[FN + k] = (a1 - a3) + (a5 - a6) + (a8 - a7);
-        Q[2 * FN + k] = (a2 - a4) + (a5 + a6) - (a7 + a8);
-        Q[3 * FN + k] = (a1 + a3) + (a5 + a6) + (a7 + a8);
-        Q[4 * FN + k] = (a5 - a6) + (a7 - a8);
-        Q[5 * FN + k] = (a2 + a4) + (a5 + a6) + (a7 + a8);
+        // F~ of the eight moving directions, then R~, 3 U~ and 9 S~ with the weight products
+        // of Wts<float, 2>
+        const float fxp = xp.x + xp.y, fxm = xm.x - xm.y, fyp = yp.x + yp.z, fym = ym.x - ym.z;
+        const float fpp = pp.x + pp.y + pp.z, fmp = mp.x - mp.y + mp.z;
+        const float fmm = mm.x - mm.y - mm.z, fpm = pm.x + pm.y - pm.z;
+        const float dsum = (fpp + fmp) + (fmm + fpm);
+        Q[k] = W::w0 * c0.x + W::w1 * ((fxp + fxm) + (fyp + fym)) + W::w2 * dsum;
+        Q[FN + k] = W::w3_1 * (fxp - fxm) + W::w3_2 * ((fpp - fmp) + (fpm - fmm));
+        Q[2 * FN + k] = W::w3_1 * (fyp - fym) + W::w3_2 * ((fpp + fmp) - (fmm + fpm));
+        Q[3 * FN + k] = W::s_1 * (fxp + fxm) + W::s_2 * dsum;
+        Q[4 * FN + k] = W::s_2 * ((fpp - fmp) + (fmm - fpm));
+        Q[5 * FN + k] = W::s_1 * (fyp + fym) + W::s_2 * dsum;
     }
     __syncthreads();
-    // 3. lambda^{n-1} = (R~, 3 U~ - 3 R~ u + 9 S~ u + D^T (2 A S~)) on the tile
+    // 3. lambda^{n-1} = (R~, 3 U~ - 3 R~ u + 9 S~ u + D^T (2 A S~)) on the tile; Q holds
+    //    R~, 3 U~ and 9 S~, so the transposed gradient takes 2 A / 9 times the stored values
     const V4<float>* sprev = (const V4<float>*)I.bufs[sp];
     V4<float>* out = (V4<float>*)I.bufs[lam_out];
-    const float twoA = (float)(2.0 * g.A);
+    const float twoA = (float)(2.0 * g.A / 9.0);
     for (int k = threadIdx.x; k < TX * TY; k += NT) {
         const int ty = k / TX, tx = k - ty * TX;
         const int x = x0 + tx, y = y0 + ty;
@@ -744,12 +748,13 @@ __device__ __forceinline__ void adj_tile(const Inst& I, int x0, int y0, const Ob
         const V4<float> v = sprev[(long long)y * n0 + x];
         const float R = Q[q], Ux = Q[FN + q], Uy = Q[2 * FN + q];
         const float Sxx = Q[3 * FN + q], Sxy = Q[4 * FN + q], Syy = Q[5 * FN + q];
-        float lx = 3.f * Ux - 3.f * R * v.x;
-        float ly = 3.f * Uy - 3.f * R * v.y;
-        lx += 9.f * Sxx * v.x;
-        lx += 9.f * Sxy * v.y;
-        ly += 9.f * Sxy * v.x;
-        ly += 9.f * Syy * v.y;
+        const float R3 = 3.f * R;
+        float lx = Ux - R3 * v.x;
+        float ly = Uy - R3 * v.y;
+        lx += Sxx * v.x;
+        lx += Sxy * v.y;
+        ly += Sxy * v.x;
+        ly += Syy * v.y;
         // transposed gradient: rows y' = x - kk e_b whose stencil reaches x; phi_ab = 2 A S~_ab,
         // b = x uses (Sxx, Sxy), b = y uses (Sxy, Syy)
         float ax = 0.f, ay = 0.f;
@@ -797,7 +802,7 @@ __global__ void __launch_bounds__(NT) k_t_adj2d(Plan p, const int* __restrict__ 
     constexpr int HX = TX + 4, HY = TY + 4;
     extern __shared__ float4 smem[];
     float4* M = smem;                          // HY x HX: mu (rho, x, y, -)
-    float* Q = (float*)(smem + HX * HY);       // 6 planes of FY x FX: R, Ux, Uy, Sxx, Sxy, Syy
+    float* Q = (float*)(smem + HX * HY);       // 6 planes of FY x FX: R~, 3 U~, 9 S~ (xx, xy, yy)
     const int n = step_of(p, noff);
     __shared__ Inst sI;
     int cur = -1;

@@ -149,27 +149,28 @@ __device__ __forceinline__ void feq_node(const FusedArgs& a, const float4* __res
     const float ASyz = hA * (Dyz + Dzy);
     const float ux = c.y, uy = c.z, uz = c.w;
     const float P = c.x - 1.5f * (ux * ux + uy * uy + uz * uz);
-    f_rest = a.w0 * P;
-    // axes: w1 (P + 4.5 u_a^2 + A S_aa) +- 3 w1 u_a
-    const float w1 = a.w1, w13 = 3.f * a.w1;
+    using Wf = Wts<float, 3>;
+    f_rest = Wf::w0 * P;
+    // axes: w1 (P + A S_aa) + 4.5 w1 u_a^2 +- 3 w1 u_a (the weight products as in Wts)
+    const float w1 = Wf::w1, w13 = Wf::w3_1;
     {
-        const float b = w1 * (P + 4.5f * ux * ux + ASxx);
+        const float b = fmaf(Wf::h_1 * ux, ux, w1 * (P + ASxx));
         sFn[0 * FS] = b + w13 * ux;
         sFn[1 * FS] = b - w13 * ux;
     }
     {
-        const float b = w1 * (P + 4.5f * uy * uy + ASyy);
+        const float b = fmaf(Wf::h_1 * uy, uy, w1 * (P + ASyy));
         sFn[2 * FS] = b + w13 * uy;
         sFn[3 * FS] = b - w13 * uy;
     }
     {
-        const float b = w1 * (P + 4.5f * uz * uz + ASzz);
+        const float b = fmaf(Wf::h_1 * uz, uz, w1 * (P + ASzz));
         f_pz = b + w13 * uz;
         f_mz = b - w13 * uz;
     }
     // corners (sx, sy, +1) and their opposites (-sx, -sy, -1):
-    // w2 [P + A tr S + 4.5 (c.u)^2 + 2 A (sx sy S_xy + sx S_xz + sy S_yz)] +- 3 w2 (c.u)
-    const float w2 = a.w2, w23 = 3.f * a.w2, w245 = 4.5f * a.w2, w2x2 = 2.f * a.w2;
+    // w2 [P + A tr S + 2 A (sx sy S_xy + sx S_xz + sy S_yz)] + 4.5 w2 (c.u)^2 +- 3 w2 (c.u)
+    const float w2 = Wf::w2, w23 = Wf::w3_2, w245 = Wf::h_2, w2x2 = 2.f * Wf::w2;
     const float T0 = w2 * (P + ASxx + ASyy + ASzz);
     const float s1 = ux + uy, d1 = ux - uy;
     const float q1 = ASxz + ASyz, q2 = ASyz - ASxz;
@@ -463,24 +464,25 @@ __device__ __forceinline__ void feq_reg(const FusedArgs& a, const float4* __rest
     const float ASyz = hA * (Dyz + Dzy);
     const float ux = c.y, uy = c.z, uz = c.w;
     const float P = c.x - 1.5f * (ux * ux + uy * uy + uz * uz);
-    f_rest = a.w0 * P;
-    const float w1 = a.w1, w13 = 3.f * a.w1;
+    using Wf = Wts<float, 3>;
+    f_rest = Wf::w0 * P;
+    const float w1 = Wf::w1, w13 = Wf::w3_1;
     {
-        const float b = w1 * (P + 4.5f * ux * ux + ASxx);
+        const float b = fmaf(Wf::h_1 * ux, ux, w1 * (P + ASxx));
         sFn[0 * FSs] = b + w13 * ux;
         sFn[1 * FSs] = b - w13 * ux;
     }
     {
-        const float b = w1 * (P + 4.5f * uy * uy + ASyy);
+        const float b = fmaf(Wf::h_1 * uy, uy, w1 * (P + ASyy));
         sFn[2 * FSs] = b + w13 * uy;
         sFn[3 * FSs] = b - w13 * uy;
     }
     {
-        const float b = w1 * (P + 4.5f * uz * uz + ASzz);
+        const float b = fmaf(Wf::h_1 * uz, uz, w1 * (P + ASzz));
         f_pz = b + w13 * uz;
         f_mz = b - w13 * uz;
     }
-    const float w2 = a.w2, w23 = 3.f * a.w2, w245 = 4.5f * a.w2, w2x2 = 2.f * a.w2;
+    const float w2 = Wf::w2, w23 = Wf::w3_2, w245 = Wf::h_2, w2x2 = 2.f * Wf::w2;
     const float T0 = w2 * (P + ASxx + ASyy + ASzz);
     const float s1 = ux + uy, d1 = ux - uy;
     const float q1 = ASxz + ASyz, q2 = ASyz - ASxz;
@@ -777,7 +779,7 @@ struct PCfg {
 
 // Packed constants of the pair kernel (both lanes equal).
 struct PairK {
-    float2 A, hA, m15, w0, w1, w13, nw13, c45, w2, w23, nw23, w245, w2x2, nw2x2, mone;
+    float2 A, hA, m15, w0, w1, w13, nw13, h1, w2, w23, nw23, h2, w2x2, nw2x2, mone;
 };
 
 __device__ __forceinline__ float2 padd(float2 a, float2 b) { return __fadd2_rn(a, b); }
@@ -841,17 +843,17 @@ __device__ __forceinline__ void feq_pair(const PairK& k, const float4& ca, const
     f_rest = pmul(k.w0, P);
     const float2 Px = padd(P, ASxx);
     {
-        const float2 b = pmul(k.w1, pfma(pmul(k.c45, ux), ux, Px));
+        const float2 b = pfma(pmul(k.h1, ux), ux, pmul(k.w1, Px));
         sFn[0 * FS] = pfma(k.w13, ux, b);
         sFn[1 * FS] = pfma(k.nw13, ux, b);
     }
     {
-        const float2 b = pmul(k.w1, pfma(pmul(k.c45, uy), uy, padd(P, ASyy)));
+        const float2 b = pfma(pmul(k.h1, uy), uy, pmul(k.w1, padd(P, ASyy)));
         sFn[2 * FS] = pfma(k.w13, uy, b);
         sFn[3 * FS] = pfma(k.nw13, uy, b);
     }
     {
-        const float2 b = pmul(k.w1, pfma(pmul(k.c45, uz), uz, padd(P, ASzz)));
+        const float2 b = pfma(pmul(k.h1, uz), uz, pmul(k.w1, padd(P, ASzz)));
         f_pz = pfma(k.w13, uz, b);
         f_mz = pfma(k.nw13, uz, b);
     }
@@ -860,25 +862,25 @@ __device__ __forceinline__ void feq_pair(const PairK& k, const float4& ca, const
     const float2 q1 = padd(ASxz, ASyz), q2 = psub(ASyz, ASxz, k.mone);
     {   // (+,+,+) / (-,-,-)
         const float2 cu = padd(s1, uz);
-        const float2 sym = pfma(pmul(k.w245, cu), cu, pfma(k.w2x2, padd(ASxy, q1), T0));
+        const float2 sym = pfma(pmul(k.h2, cu), cu, pfma(k.w2x2, padd(ASxy, q1), T0));
         sFn[4 * FS] = pfma(k.w23, cu, sym);
         sFn[11 * FS] = pfma(k.nw23, cu, sym);
     }
     {   // (-,+,+) / (+,-,-)
         const float2 cu = psub(uz, d1, k.mone);
-        const float2 sym = pfma(pmul(k.w245, cu), cu, pfma(k.w2x2, psub(q2, ASxy, k.mone), T0));
+        const float2 sym = pfma(pmul(k.h2, cu), cu, pfma(k.w2x2, psub(q2, ASxy, k.mone), T0));
         sFn[5 * FS] = pfma(k.w23, cu, sym);
         sFn[10 * FS] = pfma(k.nw23, cu, sym);
     }
     {   // (+,-,+) / (-,+,-)
         const float2 cu = padd(uz, d1);
-        const float2 sym = pfma(pmul(k.w245, cu), cu, pfma(k.nw2x2, padd(ASxy, q2), T0));
+        const float2 sym = pfma(pmul(k.h2, cu), cu, pfma(k.nw2x2, padd(ASxy, q2), T0));
         sFn[6 * FS] = pfma(k.w23, cu, sym);
         sFn[9 * FS] = pfma(k.nw23, cu, sym);
     }
     {   // (-,-,+) / (+,+,-)
         const float2 cu = psub(uz, s1, k.mone);
-        const float2 sym = pfma(pmul(k.w245, cu), cu, pfma(k.w2x2, psub(ASxy, q1, k.mone), T0));
+        const float2 sym = pfma(pmul(k.h2, cu), cu, pfma(k.w2x2, psub(ASxy, q1, k.mone), T0));
         sFn[7 * FS] = pfma(k.w23, cu, sym);
         sFn[8 * FS] = pfma(k.nw23, cu, sym);
     }
@@ -1266,17 +1268,18 @@ cudaError_t launch_zpair(const Geom& g, const CUtensorMap& map, const FusedArgs&
     a.k.A = two(f0.A);
     a.k.hA = two(0.5f * f0.A);
     a.k.m15 = two(-1.5f);
-    a.k.w0 = two(f0.w0);
-    a.k.w1 = two(f0.w1);
-    a.k.w13 = two(3.f * f0.w1);
-    a.k.nw13 = two(-3.f * f0.w1);
-    a.k.c45 = two(4.5f);
-    a.k.w2 = two(f0.w2);
-    a.k.w23 = two(3.f * f0.w2);
-    a.k.nw23 = two(-3.f * f0.w2);
-    a.k.w245 = two(4.5f * f0.w2);
-    a.k.w2x2 = two(2.f * f0.w2);
-    a.k.nw2x2 = two(-2.f * f0.w2);
+    using Wf = Wts<float, 3>;
+    a.k.w0 = two(Wf::w0);
+    a.k.w1 = two(Wf::w1);
+    a.k.w13 = two(Wf::w3_1);
+    a.k.nw13 = two(-Wf::w3_1);
+    a.k.h1 = two(Wf::h_1);
+    a.k.w2 = two(Wf::w2);
+    a.k.w23 = two(Wf::w3_2);
+    a.k.nw23 = two(-Wf::w3_2);
+    a.k.h2 = two(Wf::h_2);
+    a.k.w2x2 = two(2.f * Wf::w2);
+    a.k.nw2x2 = two(-2.f * Wf::w2);
     a.k.mone = two(-1.f);
     for (int d = 0; d < 3; ++d) a.bf2[d] = two(f0.bf[d]);
     a.has_bf = (f0.bf[0] != 0.f || f0.bf[1] != 0.f || f0.bf[2] != 0.f) ? 1 : 0;
@@ -1299,9 +1302,9 @@ cudaError_t launch_fused_step3d(const Geom& g, const V4<float>* src, const V4<fl
     a.src = reinterpret_cast<const float4*>(src);
     a.err = err;
     a.A = (float)g.A;
-    a.w0 = (float)(2.0 / 9.0);
-    a.w1 = (float)(1.0 / 9.0);
-    a.w2 = (float)(1.0 / 72.0);
+    a.w0 = Wts<float, 3>::w0;
+    a.w1 = Wts<float, 3>::w1;
+    a.w2 = Wts<float, 3>::w2;
     for (int k = 0; k < 3; ++k) a.bf[k] = (float)g.body[k];
     CUtensorMap map;
     if (v == 2) {

@@ -55,7 +55,7 @@ struct AdjArgs {
     long long face_off[6];
     int* err;
     int zchunk;
-    float A, w0, w1, w2;
+    float A9;              // A / 9
     float obj_r, obj_u[3]; // d j / d s at target nodes, times the window weight
     int has_obj;           // any of them non-zero
 };
@@ -112,6 +112,8 @@ __device__ __forceinline__ void to_mu(const AdjArgs& a, float4& v, int cf, int g
     v = l;
 }
 
+// R = R~, U = 3 U~, S = 9 S~ (the multiples the adjoint equilibrium uses, each formed with the
+// weight products of Wts<float, 3> so that the lattice identities hold exactly).
 struct Mom {
     float R, Ux, Uy, Uz, Sxx, Sxy, Sxz, Syy, Syz, Szz;
 };
@@ -150,20 +152,20 @@ __device__ __forceinline__ Mom moments(const AdjArgs& a, const float4* __restric
     const float Bdp = b_[0][0] - b_[1][0], Bdm = b_[0][1] - b_[1][1];
     const float sG = Ap + Am, szG = Ap - Am, syG = Adp + Adm, syzG = Adp - Adm;
     const float sxG = Bp + Bm, sxzG = Bp - Bm, sxyG = Bdp + Bdm;
-    const float w0 = a.w0, w1 = a.w1, w2 = a.w2;
+    using Wf = Wts<float, 3>;
     Mom m;
     const float ax = gpx + gmx, ay = gpy + gmy, az = gpz + gmz;
-    const float w2G = w2 * sG;
-    m.R = w0 * s.x + w1 * (ax + ay + az) + w2G;
-    m.Ux = w1 * (gpx - gmx) + w2 * sxG;
-    m.Uy = w1 * (gpy - gmy) + w2 * syG;
-    m.Uz = w1 * (gpz - gmz) + w2 * szG;
-    m.Sxx = w1 * ax + w2G;
-    m.Syy = w1 * ay + w2G;
-    m.Szz = w1 * az + w2G;
-    m.Sxy = w2 * sxyG;
-    m.Sxz = w2 * sxzG;
-    m.Syz = w2 * syzG;
+    const float s2G = Wf::s_2 * sG;
+    m.R = Wf::w0 * s.x + Wf::w1 * (ax + ay + az) + Wf::w2 * sG;
+    m.Ux = Wf::w3_1 * (gpx - gmx) + Wf::w3_2 * sxG;
+    m.Uy = Wf::w3_1 * (gpy - gmy) + Wf::w3_2 * syG;
+    m.Uz = Wf::w3_1 * (gpz - gmz) + Wf::w3_2 * szG;
+    m.Sxx = Wf::s_1 * ax + s2G;
+    m.Syy = Wf::s_1 * ay + s2G;
+    m.Szz = Wf::s_1 * az + s2G;
+    m.Sxy = Wf::s_2 * sxyG;
+    m.Sxz = Wf::s_2 * sxzG;
+    m.Syz = Wf::s_2 * syzG;
     return m;
 }
 
@@ -240,7 +242,7 @@ __global__ void __launch_bounds__(NTHR, 4)
     const int fr = rfy * PF + rfx;
     const long long zstride = (long long)nx * ny;
     const long long col = (long long)gy * nx + gx;
-    const float A = a.A;
+    const float A9 = a.A9;   // A / 9: the stored moments are 9 S~
 
     Mom prev = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     float szm_x = 0.f, szm_y = 0.f, szm_z = 0.f;   // S~_{.z} of plane p-2
@@ -316,17 +318,18 @@ __global__ void __launch_bounds__(NTHR, 4)
             const float ty_z = sr[4 * FS + fo - PF] - sr[4 * FS + fo + PF];
             const float tz_x = szm_x - m.Sxz, tz_y = szm_y - m.Syz, tz_z = szm_z - m.Szz;
             const Mom& c = prev;
+            const float R3 = 3.f * c.R;
             float4 o;
             o.x = c.R;
-            o.y = 3.f * (c.Ux - c.R * u.y) + 9.f * (c.Sxx * u.y + c.Sxy * u.z + c.Sxz * u.w) +
-                  A * (tx_x + ty_x + tz_x);
-            o.z = 3.f * (c.Uy - c.R * u.z) + 9.f * (c.Sxy * u.y + c.Syy * u.z + c.Syz * u.w) +
-                  A * (tx_y + ty_y + tz_y);
-            o.w = 3.f * (c.Uz - c.R * u.w) + 9.f * (c.Sxz * u.y + c.Syz * u.z + c.Szz * u.w) +
-                  A * (tx_z + ty_z + tz_z);
+            o.y = (c.Ux - R3 * u.y) + (c.Sxx * u.y + c.Sxy * u.z + c.Sxz * u.w) +
+                  A9 * (tx_x + ty_x + tz_x);
+            o.z = (c.Uy - R3 * u.z) + (c.Sxy * u.y + c.Syy * u.z + c.Syz * u.w) +
+                  A9 * (tx_y + ty_y + tz_y);
+            o.w = (c.Uz - R3 * u.w) + (c.Sxz * u.y + c.Syz * u.z + c.Szz * u.w) +
+                  A9 * (tx_z + ty_z + tz_z);
             a.lam_out[q * zstride + col] = o;
             // boundary nodes keep 2 A S~_{.beta} for the one-sided parts of D^T
-            const float A2 = 2.f * A;
+            const float A2 = 2.f * A9;
             if (gx == 0 || gx == nx - 1) {
                 float* f = a.face + a.face_off[gx == 0 ? 0 : 1] + 3 * ((long long)q * ny + gy);
                 f[0] = A2 * c.Sxx;
@@ -454,10 +457,7 @@ cudaError_t launch_fused_adj3d(const Geom& g, const V4<float>* lam_in, V4<float>
     face_offsets(g, fo, tot);
     for (int f = 0; f < 6; ++f) a.face_off[f] = fo.off[f];
     a.err = err;
-    a.A = (float)g.A;
-    a.w0 = (float)(2.0 / 9.0);
-    a.w1 = (float)(1.0 / 9.0);
-    a.w2 = (float)(1.0 / 72.0);
+    a.A9 = (float)(g.A / 9.0);
     a.obj_r = 0.f;
     a.obj_u[0] = a.obj_u[1] = a.obj_u[2] = 0.f;
     if (h != 0.0) {

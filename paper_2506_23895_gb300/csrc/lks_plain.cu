@@ -64,15 +64,70 @@ __global__ void k_apply_bc(Geom g, V4<T>* s) {
     write_bc_from(g, x, y, z, s[m], s);
 }
 
+// f_i^eq of one node (Sec. 2.2) from rho - rho0, u and S = G + G^T (G_ab = d u_a / d x_b):
+// the symmetric part of each opposite-direction pair (c, -c) is formed once and the pair
+// differs only in the sign of 3 c.u; the weight products are those of Wts<T, D>.  Writes the
+// Q values in the order of Lat<D>.
+template <class T>
+__device__ __forceinline__ void feq_pairs3(const V4<T>& v, const T S[3][3], T A, T* __restrict__ F,
+                                           long long stride) {
+    using W = Wts<T, 3>;
+    const T ux = v.x, uy = v.y, uz = v.z;
+    const T P = v.r - (T)1.5 * (ux * ux + uy * uy + uz * uz);
+    F[0] = W::w0 * P;
+    const T u[3] = {ux, uy, uz};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {   // axes: directions 1 + 2a (+) and 2 + 2a (-)
+        const T sym = W::w1 * (P + A * S[a][a]) + W::h_1 * u[a] * u[a];
+        F[(1 + 2 * a) * stride] = sym + W::w3_1 * u[a];
+        F[(2 + 2 * a) * stride] = sym - W::w3_1 * u[a];
+    }
+    const T tr = S[0][0] + S[1][1] + S[2][2];
+    // corners k = 0..3 have sz = +1 (directions 7..10), their opposites are 14..11
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const T sx = (k & 1) ? (T)-1 : (T)1, sy = (k & 2) ? (T)-1 : (T)1;
+        const T cu = sx * ux + sy * uy + uz;
+        const T cSc = tr + (T)2 * (sx * sy * S[0][1] + sx * S[0][2] + sy * S[1][2]);
+        const T sym = W::w2 * (P + A * cSc) + W::h_2 * cu * cu;
+        F[(7 + k) * stride] = sym + W::w3_2 * cu;
+        F[(14 - k) * stride] = sym - W::w3_2 * cu;
+    }
+}
+
+template <class T>
+__device__ __forceinline__ void feq_pairs2(const V4<T>& v, const T S[3][3], T A, T* __restrict__ F,
+                                           long long stride) {
+    using W = Wts<T, 2>;
+    const T ux = v.x, uy = v.y;
+    const T P = v.r - (T)1.5 * (ux * ux + uy * uy);
+    F[0] = W::w0 * P;
+    const T u[2] = {ux, uy};
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {   // axes: +a is direction 1 + a, -a is 3 + a
+        const T sym = W::w1 * (P + A * S[a][a]) + W::h_1 * u[a] * u[a];
+        F[(1 + a) * stride] = sym + W::w3_1 * u[a];
+        F[(3 + a) * stride] = sym - W::w3_1 * u[a];
+    }
+    const T tr = S[0][0] + S[1][1];
+    // diagonals (+,+) = 5 with (-,-) = 7, (-,+) = 6 with (+,-) = 8
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const T sx = k ? (T)-1 : (T)1;
+        const T cu = sx * ux + uy;
+        const T sym = W::w2 * (P + A * (tr + (T)2 * sx * S[0][1])) + W::h_2 * cu * cu;
+        F[(5 + k) * stride] = sym + W::w3_2 * cu;
+        F[(7 + k) * stride] = sym - W::w3_2 * cu;
+    }
+}
+
 template <class T, int D>
 __global__ void k_feq(Geom g, const V4<T>* __restrict__ s, T* __restrict__ F) {
-    using L = Lat<D>;
     long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (m >= g.nodes) return;
     int c[3];
     node_coords(g, m, c[0], c[1], c[2]);
     const V4<T> v = s[m];
-    const T u[3] = {v.x, v.y, D == 3 ? v.z : (T)0};
     T G[3][3];
 #pragma unroll
     for (int a = 0; a < 3; ++a)
@@ -93,24 +148,13 @@ __global__ void k_feq(Geom g, const V4<T>* __restrict__ s, T* __restrict__ F) {
             if (D == 3) G[2][b] += cf * w.z;
         }
     }
-    T uu = (T)0;
+    T S[3][3];
 #pragma unroll
-    for (int a = 0; a < D; ++a) uu += u[a] * u[a];
-    const T A = (T)g.A;
+    for (int a = 0; a < 3; ++a)
 #pragma unroll
-    for (int i = 0; i < L::Q; ++i) {
-        T cu = (T)0, cSc = (T)0;
-#pragma unroll
-        for (int a = 0; a < D; ++a) {
-            cu += (T)L::c(i, a) * u[a];
-#pragma unroll
-            for (int b = 0; b < D; ++b)
-                if (L::c(i, a) * L::c(i, b) != 0)
-                    cSc += (T)(L::c(i, a) * L::c(i, b)) * (G[a][b] + G[b][a]);
-        }
-        F[(long long)i * g.nodes + m] =
-            (T)L::w(i) * (v.r + (T)3 * cu + (T)4.5 * cu * cu - (T)1.5 * uu + A * cSc);
-    }
+        for (int b = 0; b < 3; ++b) S[a][b] = G[a][b] + G[b][a];
+    if (D == 3) feq_pairs3<T>(v, S, (T)g.A, F + m, g.nodes);
+    else feq_pairs2<T>(v, S, (T)g.A, F + m, g.nodes);
 }
 
 template <class T, int D>
@@ -272,46 +316,111 @@ __device__ __forceinline__ int sym6(int a, int b) {
     return a == b ? a : (a + b == 1 ? 3 : (a + b == 2 ? 4 : 5));
 }
 
+// mu at y + d (0 outside a non-periodic grid).
+template <class T>
+__device__ __forceinline__ V4<T> mu_at(const Geom& g, const V4<T>* __restrict__ mu, const int c[3],
+                                       int dx, int dy, int dz) {
+    int q[3] = {c[0] + dx, c[1] + dy, c[2] + dz};
+    const int d[3] = {dx, dy, dz};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (d[a] == 0) continue;
+        if (g.periodic[a]) q[a] = wrapi(q[a], g.n[a]);
+        else if (q[a] < 0 || q[a] >= g.n[a]) {
+            V4<T> z;
+            z.r = z.x = z.y = z.z = (T)0;
+            return z;
+        }
+    }
+    return mu[node_index(g, q[0], q[1], q[2])];
+}
+
 // Moments of F~_i(y) = mu_rho(y+c_i) + c_i.mu_u(y+c_i) and the adjoint of f^eq's dependence on
-// rho and u at level n-1; phi = 2 A s~ is kept for the transposed gradient.
+// rho and u at level n-1; phi = 2 A s~ is kept for the transposed gradient.  The sums over the
+// lattice run as butterflies over opposite directions and over the sign pattern of the corners:
+//   R~ = sum w F~, U~_a = sum w c_a F~, S~_ab = sum w c_a c_b F~.
 template <class T, int D>
 __global__ void k_adj_moments(Geom g, const V4<T>* __restrict__ mu,
                               const V4<T>* __restrict__ sp, V4<T>* __restrict__ lo,
                               T* __restrict__ phi, V4<T>* __restrict__ u3) {
-    using L = Lat<D>;
     long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (m >= g.nodes) return;
     int c[3];
     node_coords(g, m, c[0], c[1], c[2]);
-    T R = (T)0, U[3] = {(T)0, (T)0, (T)0}, S[6] = {(T)0, (T)0, (T)0, (T)0, (T)0, (T)0};
-#pragma unroll
-    for (int i = 0; i < L::Q; ++i) {
-        int q[3];
-        bool inside = true;
+    T R, U[3] = {(T)0, (T)0, (T)0}, S[6] = {(T)0, (T)0, (T)0, (T)0, (T)0, (T)0};
+    const V4<T> s0 = mu[m];
+    // R = R~, U = 3 U~, S = 9 S~, each with the weight products of Wts<T, D>
+    if (D == 3) {
+        using W = Wts<T, 3>;
+        // axes: F~(+a) = mu_rho + mu_a at y + e_a, F~(-a) = mu_rho - mu_a at y - e_a
+        T ax_sum = (T)0;
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            q[a] = c[a] + (a < D ? L::c(i, a) : 0);
-            if (a < D) {
-                if (g.periodic[a]) q[a] = wrapi(q[a], g.n[a]);
-                else if (q[a] < 0 || q[a] >= g.n[a]) inside = false;
-            }
+            const V4<T> p = mu_at<T>(g, mu, c, a == 0, a == 1, a == 2);
+            const V4<T> q = mu_at<T>(g, mu, c, -(a == 0), -(a == 1), -(a == 2));
+            const T pa = a == 0 ? p.x : (a == 1 ? p.y : p.z);
+            const T qa = a == 0 ? q.x : (a == 1 ? q.y : q.z);
+            const T fp = p.r + pa, fm = q.r - qa;
+            ax_sum += fp + fm;
+            U[a] = W::w3_1 * (fp - fm);
+            S[a] = W::s_1 * (fp + fm);   // 9 S~_aa, corners added below
         }
-        if (!inside) continue;
-        const V4<T> mv = mu[node_index(g, q[0], q[1], q[2])];
-        T Ft = mv.r;
-        if (L::c(i, 0) != 0) Ft += (T)L::c(i, 0) * mv.x;
-        if (L::c(i, 1) != 0) Ft += (T)L::c(i, 1) * mv.y;
-        if (D == 3 && L::c(i, 2) != 0) Ft += (T)L::c(i, 2) * mv.z;
-        const T wF = (T)L::w(i) * Ft;
-        R += wF;
+        // corners: sums of F~ over the 8 sign patterns weighted by 1, sx, sy, sz, sx sy, sx sz,
+        // sy sz
+        T c1 = 0, cx = 0, cy = 0, cz = 0, cxy = 0, cxz = 0, cyz = 0;
 #pragma unroll
-        for (int a = 0; a < D; ++a) {
-            if (L::c(i, a) == 0) continue;
-            U[a] += (T)L::c(i, a) * wF;
-#pragma unroll
-            for (int b = a; b < D; ++b)
-                if (L::c(i, b) != 0) S[sym6(a, b)] += (T)(L::c(i, a) * L::c(i, b)) * wF;
+        for (int k = 0; k < 8; ++k) {
+            const int sx = (k & 1) ? -1 : 1, sy = (k & 2) ? -1 : 1, sz = (k & 4) ? -1 : 1;
+            const V4<T> n = mu_at<T>(g, mu, c, sx, sy, sz);
+            const T f = n.r + (T)sx * n.x + (T)sy * n.y + (T)sz * n.z;
+            c1 += f;
+            cx += (T)sx * f;
+            cy += (T)sy * f;
+            cz += (T)sz * f;
+            cxy += (T)(sx * sy) * f;
+            cxz += (T)(sx * sz) * f;
+            cyz += (T)(sy * sz) * f;
         }
+        R = W::w0 * s0.r + W::w1 * ax_sum + W::w2 * c1;
+        U[0] += W::w3_2 * cx;
+        U[1] += W::w3_2 * cy;
+        U[2] += W::w3_2 * cz;
+        S[0] += W::s_2 * c1;
+        S[1] += W::s_2 * c1;
+        S[2] += W::s_2 * c1;
+        S[3] = W::s_2 * cxy;
+        S[4] = W::s_2 * cxz;
+        S[5] = W::s_2 * cyz;
+    } else {
+        using W = Wts<T, 2>;
+        T ax_sum = (T)0;
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+            const V4<T> p = mu_at<T>(g, mu, c, a == 0, a == 1, 0);
+            const V4<T> q = mu_at<T>(g, mu, c, -(a == 0), -(a == 1), 0);
+            const T pa = a == 0 ? p.x : p.y, qa = a == 0 ? q.x : q.y;
+            const T fp = p.r + pa, fm = q.r - qa;
+            ax_sum += fp + fm;
+            U[a] = W::w3_1 * (fp - fm);
+            S[a] = W::s_1 * (fp + fm);
+        }
+        T c1 = 0, cx = 0, cy = 0, cxy = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int sx = (k & 1) ? -1 : 1, sy = (k & 2) ? -1 : 1;
+            const V4<T> n = mu_at<T>(g, mu, c, sx, sy, 0);
+            const T f = n.r + (T)sx * n.x + (T)sy * n.y;
+            c1 += f;
+            cx += (T)sx * f;
+            cy += (T)sy * f;
+            cxy += (T)(sx * sy) * f;
+        }
+        R = W::w0 * s0.r + W::w1 * ax_sum + W::w2 * c1;
+        U[0] += W::w3_2 * cx;
+        U[1] += W::w3_2 * cy;
+        S[0] += W::s_2 * c1;
+        S[1] += W::s_2 * c1;
+        S[3] = W::s_2 * cxy;
     }
     const V4<T> v = sp[m];
     const T u[3] = {v.x, v.y, D == 3 ? v.z : (T)0};
@@ -322,9 +431,9 @@ __global__ void k_adj_moments(Geom g, const V4<T>* __restrict__ mu,
     for (int a = 0; a < 3; ++a) {
         lu[a] = (T)0;
         if (a < D) {
-            lu[a] = (T)3 * U[a] - (T)3 * R * u[a];
+            lu[a] = U[a] - (T)3 * R * u[a];
 #pragma unroll
-            for (int b = 0; b < D; ++b) lu[a] += (T)9 * S[sym6(a, b)] * u[b];
+            for (int b = 0; b < D; ++b) lu[a] += S[sym6(a, b)] * u[b];
         }
     }
     o.x = lu[0];
@@ -334,12 +443,12 @@ __global__ void k_adj_moments(Geom g, const V4<T>* __restrict__ mu,
     if (u3) {
         V4<T> a;
         a.r = (T)0;
-        a.x = (T)3 * U[0];
-        a.y = (T)3 * U[1];
-        a.z = (D == 3) ? (T)3 * U[2] : (T)0;
+        a.x = U[0];
+        a.y = U[1];
+        a.z = (D == 3) ? U[2] : (T)0;
         u3[m] = a;
     }
-    const T twoA = (T)(2.0 * g.A);
+    const T twoA = (T)(2.0 * g.A / 9.0);   // phi = 2 A S~ from the stored 9 S~
 #pragma unroll
     for (int k = 0; k < 6; ++k) phi[(long long)k * g.nodes + m] = twoA * S[k];
 }
