@@ -396,7 +396,7 @@ def run_batch_line(args, lks, W, ws, rank, local, dev):
 
 
 # kernel of each fused 3D forward-step variant (lks_step_variant)
-STEP3D_KERNELS = {0: "k_fused_step3d", 1: "k_zstep3d<8>"}
+STEP3D_KERNELS = {0: "k_fused_step3d", 1: "k_zstep3d<8>", 2: "k_zpair3d"}
 
 
 def run_ours(args):

@@ -89,6 +89,17 @@ struct Wts<float, 2> {
     static constexpr float h_1 = 0.5f, h_2 = 0.125f, s_1 = 1.0f, s_2 = 0.25f;
 };
 
+// The identities, checked at compile time (each sum is exact in double).
+template <class W, int D>
+constexpr bool weights_consistent() {
+    return (double)W::w0 + 2.0 * D * (double)W::w1 + (double)(1 << D) * (double)W::w2 == 1.0 &&
+           2.0 * (double)W::w3_1 + (double)(1 << D) * (double)W::w3_2 == 1.0 &&
+           2.0 * (double)W::h_1 + (double)(1 << D) * (double)W::h_2 == 1.5 &&
+           2.0 * (double)W::s_1 + (double)(1 << D) * (double)W::s_2 == 3.0;
+}
+static_assert(weights_consistent<Wts<float, 3>, 3>(), "D3Q15 single-precision weights");
+static_assert(weights_consistent<Wts<float, 2>, 2>(), "D2Q9 single-precision weights");
+
 // ------------------------------------------------------------------ indexing
 
 __device__ __forceinline__ long long node_index(const Geom& g, int x, int y, int z) {

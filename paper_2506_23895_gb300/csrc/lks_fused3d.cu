@@ -917,11 +917,68 @@ __device__ __forceinline__ void pair_out(const Geom& g, const PairArgs& a, int g
     if (bc_col || qz == 1 || qz == g.n[2] - 2) write_bc_f(g, gx, gy, qz, o, a.f.out);
 }
 
-template <bool IN>
+// The z derivative at a z-face plane is the one-sided difference; with a ghost value
+// g = 3 u(0) - 3 u(1) + u(2) below plane 0 (or 3 u(n-1) - 3 u(n-2) + u(n-3) above plane n-1) the
+// central difference u(1) - g (g - u(n-2)) equals it, so the pair path keeps one formula.
+__device__ __forceinline__ float3 zghost(const float3& f, const float3& s, const float3& t) {
+    return make_float3(fmaf(3.f, f.x - s.x, t.x), fmaf(3.f, f.y - s.y, t.y),
+                       fmaf(3.f, f.z - s.z, t.z));
+}
+
+__device__ __forceinline__ float3 u3(const float4& v) { return make_float3(v.y, v.z, v.w); }
+
+// z derivatives (2 d u / d z) of the pair's planes a0 (da) and a0 + 1 (db) at a z face, from
+// the ghost value: um, ua, ub, uc are u at a0 - 1 .. a0 + 2; col points at the column in the
+// source state (for u(2) or u(nz - 3) when the pair does not hold it).
+__device__ __forceinline__ void zface_fix(int a0, int nz, const float3& um, const float3& ua,
+                                       const float3& ub, const float3& uc,
+                                       const float4* __restrict__ col, long long zstride,
+                                       D9& da, D9& db) {
+    if (a0 == 0) {   // plane 0 first: ghost below it
+        const float3 gh = zghost(ua, ub, uc);
+        da.xz = ub.x - gh.x;
+        da.yz = ub.y - gh.y;
+        da.zz = ub.z - gh.z;
+    }
+    if (a0 == -1) {  // plane 0 second
+        const float3 gh = zghost(ub, uc, u3(col[2 * zstride]));
+        db.xz = uc.x - gh.x;
+        db.yz = uc.y - gh.y;
+        db.zz = uc.z - gh.z;
+    }
+    if (a0 + 1 == nz - 1) {   // plane nz-1 second: ghost above it
+        const float3 gh = zghost(ub, ua, um);
+        db.xz = gh.x - ua.x;
+        db.yz = gh.y - ua.y;
+        db.zz = gh.z - ua.z;
+    }
+    if (a0 == nz - 1) {   // plane nz-1 first
+        const float3 gh = zghost(ua, um, u3(col[(long long)(nz - 3) * zstride]));
+        da.xz = gh.x - um.x;
+        da.yz = gh.y - um.y;
+        da.zz = gh.z - um.z;
+    }
+}
+
+// A wait that first polls once (the common case: the plane has landed), then falls back to
+// the bounded wait.
+__device__ __forceinline__ bool mbar_wait_once(uint32_t bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;"
+        " selp.u32 %0, 1, 0, p; }"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return done ? true : mbar_wait(bar, parity);
+}
+
+// The plane-pair march of one interior tile (its raw halo inside the grid, no x or y face
+// within two nodes): no face tests in x and y; z-face planes through ghost values.
 __device__ __forceinline__ void pbody(const CUtensorMap& tmap, const PairArgs& a,
                                       unsigned char* smem, int hfx, int hfy, int q0, int q1) {
     using C = PCfg;
-    constexpr int TX = C::TX, TY = C::TY, HX = C::HX, FX = C::FX;
+    constexpr int TX = C::TX, HX = C::HX, FX = C::FX;
     constexpr int FS = C::FS, NSLOT = C::NSLOT;
     float4* raw = reinterpret_cast<float4*>(smem);
     float2* sFbase = reinterpret_cast<float2*>(smem + C::OFF_F);
@@ -931,109 +988,72 @@ __device__ __forceinline__ void pbody(const CUtensorMap& tmap, const PairArgs& a
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
     const int tid = threadIdx.x;
     const int tx = tid % TX, ty = tid / TX;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * C::TY;
     const int gx = x0 + tx, gy = y0 + ty;
     const int hgx = x0 - 1 + hfx, hgy = y0 - 1 + hfy;
-    const bool edge = !IN && ((x0 - 1 <= 0) || (x0 + TX >= nx - 1) || (y0 - 1 <= 0) ||
-                              (y0 + TY >= ny - 1));
-    const int pxm = axis_mode(gx, nx), pym = axis_mode(gy, ny);
-    const int rxm = axis_mode(hgx, nx), rym = axis_mode(hgy, ny);
     const int hp = (ty + 2) * HX + (tx + 2);
     const int hr = (hfy + 1) * HX + (hfx + 1);
     const int fop = (ty + 1) * FX + (tx + 1);
     const int forr = hfy * FX + hfx;
     constexpr int RIMW = (C::NHALO + 31) / 32 * 32;
     const bool has_rim = tid < RIMW;
-    const bool out_col = IN || (gx >= 1 && gx <= nx - 2 && gy >= 1 && gy <= ny - 2);
-    const bool bc_col = !IN && (gx == 1 || gx == nx - 2 || gy == 1 || gy == ny - 2);
+    const bool bc_col = false;
     const int bxx = gx - g.blo[0], byy = gy - g.blo[1];
     const bool box_col = g.boxN > 0 && bxx >= 0 && byy >= 0 && bxx < g.bn[0] && byy < g.bn[1];
     const long long box_plane = (long long)g.bn[0] * g.bn[1];
     const float4* kus_col =
         a.f.kus + ((long long)byy * g.bn[0] + bxx) - (long long)g.blo[2] * box_plane;
     const long long zstride = (long long)nx * ny;
-    const bool in_xy = IN || (gx < nx && gy < ny);
-    const bool rim_in_xy = IN || (hgx >= 0 && hgx < nx && hgy >= 0 && hgy < ny);
     float4* out_col_ptr = a.f.out + ((long long)gy * nx + gx);
+    const float4* src_col = a.f.src + ((long long)gy * nx + gx);
+    const float4* src_rim = a.f.src + ((long long)hgy * nx + hgx);
     const int zlo = max(q0, 1), zhi = min(q1 - 1, nz - 2);
     const int npairs = ((q1 - q0 + 1) >> 1) + 1;
-    const int nplanes = 2 * npairs + 2;   // raw planes q0-2 .. q0-1+2 npairs (load j = plane - q0 + 2)
+    const int nplanes = 2 * npairs + 2;
 
     bool ok = true;
-    // prologue: loads 0..3; u of plane q0-2 and the node of plane q0-1 into registers
     float3 um, rum;
     float4 ca, rca;
     {
         bool good = true;
-        for (int j = 0; j < 4; ++j) good = mbar_wait(smem_addr(&bars[j]), 0) && good;
-        const float4 v = raw[hp];
-        um = make_float3(v.y, v.z, v.w);
+        for (int j = 0; j < 4; ++j) good = mbar_wait_once(smem_addr(&bars[j]), 0) && good;
+        um = u3(raw[hp]);
         ca = raw[(size_t)C::SLOT + hp];
-        const float4 rv = raw[hr];
-        rum = make_float3(rv.y, rv.z, rv.w);
+        rum = u3(raw[hr]);
         rca = raw[(size_t)C::SLOT + hr];
         ok = !__syncthreads_or(!good);
     }
-    // carried sums: pend = (cz = 0 of plane a-1) + (cz = +1 of plane a-2), pc = cz = +1 of a-1
     float pend_r = 0.f, pend_x = 0.f, pend_y = 0.f, pend_z = 0.f;
     float pc_r = 0.f, pc_x = 0.f, pc_y = 0.f, pc_z = 0.f;
-    int ik = NSLOT;   // next load to issue
+    int ik = NSLOT;
+    // ring slots and phase parities of the loads of planes a0, a0 + 1, a0 + 2
+    int sa = 1, sb = 2, sc = 3, pb = 0, pcp = 0;
     for (int it = 0; ok && it < npairs; ++it) {
-        const int a0 = q0 - 1 + 2 * it;     // planes a0, a0 + 1
-        const int j1 = 2 * it + 2, j2 = 2 * it + 3;   // loads of planes a0 + 1, a0 + 2
+        const int a0 = q0 - 1 + 2 * it;
         bool good = true;
-        if (it > 0) good = mbar_wait(smem_addr(&bars[j1 % NSLOT]), (j1 / NSLOT) & 1);
-        good = mbar_wait(smem_addr(&bars[j2 % NSLOT]), (j2 / NSLOT) & 1) && good;
-        const float4* ra = raw + (size_t)((2 * it + 1) % NSLOT) * C::SLOT;
-        const float4* rb = raw + (size_t)(j1 % NSLOT) * C::SLOT;
-        const float4* rc = raw + (size_t)(j2 % NSLOT) * C::SLOT;
+        if (it > 0) good = mbar_wait_once(smem_addr(&bars[sb]), pb);
+        good = mbar_wait_once(smem_addr(&bars[sc]), pcp) && good;
+        const float4* ra = raw + (size_t)sa * C::SLOT;
+        const float4* rb = raw + (size_t)sb * C::SLOT;
+        const float4* rc = raw + (size_t)sc * C::SLOT;
         float2* sF = sFbase + (size_t)(it & 1) * NCROSS * FS;
         const float4 cb = rb[hp], cc = rc[hp];
-        const float3 ub = make_float3(cb.y, cb.z, cb.w), uc = make_float3(cc.y, cc.z, cc.w);
-        const float3 ua = make_float3(ca.y, ca.z, ca.w);
+        const float3 ub = u3(cb), uc = u3(cc), ua = u3(ca);
+        const bool zface = a0 <= 0 || a0 + 1 >= nz - 1;
         float2 f_rest, f_pz, f_mz;
-        const int zma = a0 == 0 ? 1 : (a0 == nz - 1 ? 2 : 0);
-        const int zmb = a0 + 1 == 0 ? 1 : (a0 + 1 == nz - 1 ? 2 : 0);
-        D9 da, db;
-        if (!edge && zma == 0 && zmb == 0) {
+        {
+            D9 da, db;
             const float4 z0 = make_float4(0.f, 0.f, 0.f, 0.f);
             deriv_plane<false>(ra + hp, ca, um, ub, 0, 0, 0, z0, da);
             deriv_plane<false>(rb + hp, cb, ua, uc, 0, 0, 0, z0, db);
+            if (zface) zface_fix(a0, nz, um, ua, ub, uc, src_col, zstride, da, db);
             feq_pair(k, ca, cb, da, db, sF + fop, f_rest, f_pz, f_mz);
             if (has_rim) {
                 const float4 rcb = rb[hr], rcc = rc[hr];
-                const float3 rub = make_float3(rcb.y, rcb.z, rcb.w);
-                const float3 ruc = make_float3(rcc.y, rcc.z, rcc.w);
-                const float3 rua = make_float3(rca.y, rca.z, rca.w);
+                const float3 rua = u3(rca), rub = u3(rcb), ruc = u3(rcc);
                 deriv_plane<false>(ra + hr, rca, rum, rub, 0, 0, 0, z0, da);
                 deriv_plane<false>(rb + hr, rcb, rua, ruc, 0, 0, 0, z0, db);
-                float2 d0, d1, d2;
-                feq_pair(k, rca, rcb, da, db, sF + forr, d0, d1, d2);
-                rum = rub;
-                rca = rcc;
-            }
-        } else {
-            // plane two away for one-sided z differences, straight from global memory
-            float4 zfa = make_float4(0.f, 0.f, 0.f, 0.f), zfb = zfa;
-            if (zma != 0 && in_xy)
-                zfa = a.f.src[((long long)(zma == 1 ? 2 : nz - 3) * ny + gy) * nx + gx];
-            if (zmb != 0 && in_xy)
-                zfb = a.f.src[((long long)(zmb == 1 ? 2 : nz - 3) * ny + gy) * nx + gx];
-            deriv_plane<true>(ra + hp, ca, um, ub, pxm, pym, zma, zfa, da);
-            deriv_plane<true>(rb + hp, cb, ua, uc, pxm, pym, zmb, zfb, db);
-            feq_pair(k, ca, cb, da, db, sF + fop, f_rest, f_pz, f_mz);
-            if (has_rim) {
-                const float4 rcb = rb[hr], rcc = rc[hr];
-                const float3 rub = make_float3(rcb.y, rcb.z, rcb.w);
-                const float3 ruc = make_float3(rcc.y, rcc.z, rcc.w);
-                const float3 rua = make_float3(rca.y, rca.z, rca.w);
-                float4 rza = make_float4(0.f, 0.f, 0.f, 0.f), rzb = rza;
-                if (zma != 0 && rim_in_xy)
-                    rza = a.f.src[((long long)(zma == 1 ? 2 : nz - 3) * ny + hgy) * nx + hgx];
-                if (zmb != 0 && rim_in_xy)
-                    rzb = a.f.src[((long long)(zmb == 1 ? 2 : nz - 3) * ny + hgy) * nx + hgx];
-                deriv_plane<true>(ra + hr, rca, rum, rub, rxm, rym, zma, rza, da);
-                deriv_plane<true>(rb + hr, rcb, rua, ruc, rxm, rym, zmb, rzb, db);
+                if (zface) zface_fix(a0, nz, rum, rua, rub, ruc, src_rim, zstride, da, db);
                 float2 d0, d1, d2;
                 feq_pair(k, rca, rcb, da, db, sF + forr, d0, d1, d2);
                 rum = rub;
@@ -1046,14 +1066,24 @@ __device__ __forceinline__ void pbody(const CUtensorMap& tmap, const PairArgs& a
             ok = false;
             break;
         }
-        // every thread is past its reads of planes a0 and a0 + 1: their slots take the next
-        // loads (the first iteration also refills the slot of plane q0 - 2)
         if (tid == 0) {
             const int jmax = min(2 * it + 9, nplanes);
             if (ik < jmax) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             for (; ik < jmax; ++ik)
                 tma_load_box(smem_addr(raw + (size_t)(ik % NSLOT) * C::SLOT), &tmap, x0 - 2,
                              y0 - 2, q0 - 2 + ik, smem_addr(&bars[ik % NSLOT]), C::PLANE_BYTES);
+        }
+        // advance the slots by two planes
+        sa = sc;
+        sb += 2;
+        if (sb >= NSLOT) {
+            sb -= NSLOT;
+            pb ^= 1;
+        }
+        sc += 2;
+        if (sc >= NSLOT) {
+            sc -= NSLOT;
+            pcp ^= 1;
         }
         const float2* sFp = sF + fop;
         const float2 fpx = sFp[0 * FS - 1], fmx = sFp[1 * FS + 1];
@@ -1062,7 +1092,6 @@ __device__ __forceinline__ void pbody(const CUtensorMap& tmap, const PairArgs& a
         const float2 cpm_p = sFp[6 * FS - 1 + FX], cmm_p = sFp[7 * FS + 1 + FX];
         const float2 cpp_m = sFp[8 * FS - 1 - FX], cmp_m = sFp[9 * FS + 1 - FX];
         const float2 cpm_m = sFp[10 * FS - 1 + FX], cmm_m = sFp[11 * FS + 1 + FX];
-        // cz = -1 group of planes (a0, a0 + 1): completes planes (a0 - 1, a0)
         float2 Mr, Mx, My;
         {
             const float2 sxp = padd(cpp_m, cpm_m), sxm = padd(cmp_m, cmm_m);
@@ -1071,10 +1100,8 @@ __device__ __forceinline__ void pbody(const CUtensorMap& tmap, const PairArgs& a
             Mx = psub(sxp, sxm, k.mone);
             My = psub(syp, sym, k.mone);
         }
-        // cz = 0 group of planes (a0, a0 + 1)
         const float2 Zr = padd(padd(padd(f_rest, fpx), padd(fmx, fpy)), fmy);
         const float2 Zx = psub(fpx, fmx, k.mone), Zy = psub(fpy, fmy, k.mone);
-        // cz = +1 group of planes (a0, a0 + 1): into planes (a0 + 1, a0 + 2)
         float2 Pr, Px, Py;
         {
             const float2 sxp = padd(cpp_p, cpm_p), sxm = padd(cmp_p, cmm_p);
@@ -1083,7 +1110,6 @@ __device__ __forceinline__ void pbody(const CUtensorMap& tmap, const PairArgs& a
             Px = psub(sxp, sxm, k.mone);
             Py = psub(syp, sym, k.mone);
         }
-        // outputs of planes a0 - 1 (lane x) and a0 (lane y)
         float2 orr = padd(make_float2(pend_r, Zr.x + pc_r), Mr);
         float2 oxx = padd(make_float2(pend_x, Zx.x + pc_x), Mx);
         float2 oyy = padd(make_float2(pend_y, Zy.x + pc_y), My);
@@ -1101,14 +1127,12 @@ __device__ __forceinline__ void pbody(const CUtensorMap& tmap, const PairArgs& a
         pc_x = Px.y;
         pc_y = Py.y;
         pc_z = Pr.y;
-        if (out_col) {
-            if (a0 - 1 >= zlo && a0 - 1 <= zhi)
-                pair_out(g, a, gx, gy, a0 - 1, orr.x, oxx.x, oyy.x, ozz.x, box_col, kus_col,
-                         box_plane, out_col_ptr, zstride, bc_col);
-            if (a0 >= zlo && a0 <= zhi)
-                pair_out(g, a, gx, gy, a0, orr.y, oxx.y, oyy.y, ozz.y, box_col, kus_col,
-                         box_plane, out_col_ptr, zstride, bc_col);
-        }
+        if (a0 - 1 >= zlo && a0 - 1 <= zhi)
+            pair_out(g, a, gx, gy, a0 - 1, orr.x, oxx.x, oyy.x, ozz.x, box_col, kus_col,
+                     box_plane, out_col_ptr, zstride, bc_col);
+        if (a0 >= zlo && a0 <= zhi)
+            pair_out(g, a, gx, gy, a0, orr.y, oxx.y, oyy.y, ozz.y, box_col, kus_col, box_plane,
+                     out_col_ptr, zstride, bc_col);
     }
     if (!ok) {
         if (tid == 0) {
@@ -1121,22 +1145,24 @@ __device__ __forceinline__ void pbody(const CUtensorMap& tmap, const PairArgs& a
     }
 }
 
+// Interior tiles march plane pairs; tiles near an x or y face take the register z-march of
+// variant 1 (zbody, its own five-slot ring inside the same shared memory) for their face rules.
 __global__ void __launch_bounds__(PCfg::NTHR, PCfg::MINB)
     k_zpair3d(const __grid_constant__ CUtensorMap tmap, const PairArgs a) {
     using C = PCfg;
+    using Z = ZCfg<8>;
+    static_assert(C::TX == Z::TX && C::TY == Z::TY && C::SLOT == Z::SLOT && C::HX == Z::HX &&
+                      C::HY == Z::HY && Z::SMEM <= C::SMEM,
+                  "edge tiles reuse the register z-march in the same shared memory");
     constexpr int TX = C::TX, TY = C::TY, FW = C::FW, FY = C::FY;
-    constexpr int NSLOT = C::NSLOT;
     extern __shared__ __align__(128) unsigned char smem[];
     float4* raw = reinterpret_cast<float4*>(smem);
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::OFF_BAR);
     const Geom& g = a.f.g;
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
     const int tid = threadIdx.x;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const int q0 = blockIdx.z * a.f.zchunk;
     const int q1 = min(nz, q0 + a.f.zchunk);
-    const int npairs = ((q1 - q0 + 1) >> 1) + 1;
-    const int nplanes = 2 * npairs + 2;
     constexpr int RIMW = (C::NHALO + 31) / 32 * 32;
     const int rr = tid < C::NHALO ? tid : tid - (RIMW - C::NHALO);
     int hfx = 0, hfy = 0;
@@ -1157,19 +1183,33 @@ __global__ void __launch_bounds__(PCfg::NTHR, PCfg::MINB)
         if (tid == 0) atomicOr(a.f.err, 16);
         return;
     }
-    if (tid == 0) {
-        for (int s = 0; s < NSLOT; ++s) mbar_init(smem_addr(&bars[s]));
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        for (int j = 0; j < NSLOT && j < nplanes; ++j)
-            tma_load_box(smem_addr(raw + (size_t)j * C::SLOT), &tmap, x0 - 2, y0 - 2, q0 - 2 + j,
-                         smem_addr(&bars[j]), C::PLANE_BYTES);
-    }
-    __syncthreads();
     const bool interior = x0 >= 3 && x0 + TX + 2 <= nx - 1 && y0 >= 3 && y0 + TY + 2 <= ny - 1;
-    if (interior)
-        pbody<true>(tmap, a, smem, hfx, hfy, q0, q1);
-    else
-        pbody<false>(tmap, a, smem, hfx, hfy, q0, q1);
+    if (interior) {
+        const int npairs = ((q1 - q0 + 1) >> 1) + 1;
+        const int nplanes = 2 * npairs + 2;
+        uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::OFF_BAR);
+        if (tid == 0) {
+            for (int s = 0; s < C::NSLOT; ++s) mbar_init(smem_addr(&bars[s]));
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+            for (int j = 0; j < C::NSLOT && j < nplanes; ++j)
+                tma_load_box(smem_addr(raw + (size_t)j * C::SLOT), &tmap, x0 - 2, y0 - 2,
+                             q0 - 2 + j, smem_addr(&bars[j]), C::PLANE_BYTES);
+        }
+        __syncthreads();
+        pbody(tmap, a, smem, hfx, hfy, q0, q1);
+    } else {
+        const int nplanes = q1 - q0 + 4;
+        uint64_t* bars = reinterpret_cast<uint64_t*>(smem + Z::OFF_BAR);
+        if (tid == 0) {
+            for (int s = 0; s < Z::NSLOT; ++s) mbar_init(smem_addr(&bars[s]));
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+            for (int j = 0; j < Z::NSLOT && j < nplanes; ++j)
+                tma_load_box(smem_addr(raw + (size_t)j * Z::SLOT), &tmap, x0 - 2, y0 - 2,
+                             q0 - 2 + j, smem_addr(&bars[j]), Z::PLANE_BYTES);
+        }
+        __syncthreads();
+        zbody<8, false>(tmap, a.f, smem, hfx, hfy, q0, q1, nplanes);
+    }
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
