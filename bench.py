@@ -548,7 +548,7 @@ def run_ours(args):
     torch.cuda.empty_cache()
 
     # measured FMA rates: the arithmetic roofline of the plain FP64 path
-    if rank == 0:
+    if rank == 0 and not args.no_fp64:
         out["alu_peaks"] = {"fp64_tflops": lks.fma_rate(lks.FP64, stream) / 1e12,
                             "fp32_tflops": lks.fma_rate(lks.FP32, stream) / 1e12,
                             "how": "lks_fma_rate: independent FMA chains over whole waves of "
