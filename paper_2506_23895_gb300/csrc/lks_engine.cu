@@ -796,6 +796,16 @@ lks_status lks_step_variant(lks_ctx* c, int request, int* chosen) {
     return LKS_OK;
 }
 
+lks_status lks_adjoint_variant(lks_ctx* c, int request, int* chosen) {
+    if (!c || request < -2 || request == -1 || request >= kAdj3dVariants)
+        return c ? fail(c, LKS_ERR_ARG, "adjoint variant must be -2 or in [0, %d]",
+                        kAdj3dVariants - 1)
+                 : LKS_ERR_ARG;
+    if (request >= 0) c->adj3d_var = request;
+    if (chosen) *chosen = c->adj3d_var;
+    return LKS_OK;
+}
+
 lks_status lks_get_stats(const lks_ctx* c, long long* st5) {
     if (!c || !st5) return LKS_ERR_ARG;
     for (int i = 0; i < 5; ++i) st5[i] = c->stats[i];

@@ -960,19 +960,6 @@ __device__ __forceinline__ void zface_fix(int a0, int nz, const float3& um, cons
     }
 }
 
-// A wait that first polls once (the common case: the plane has landed), then falls back to
-// the bounded wait.
-__device__ __forceinline__ bool mbar_wait_once(uint32_t bar, uint32_t parity) {
-    uint32_t done;
-    asm volatile(
-        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;"
-        " selp.u32 %0, 1, 0, p; }"
-        : "=r"(done)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return done ? true : mbar_wait(bar, parity);
-}
-
 // The plane-pair march of one interior tile (its raw halo inside the grid, no x or y face
 // within two nodes): no face tests in x and y; z-face planes through ghost values.
 __device__ __forceinline__ void pbody(const CUtensorMap& tmap, const PairArgs& a,

@@ -169,6 +169,10 @@ __device__ __forceinline__ Mom moments(const AdjArgs& a, const float4* __restric
     return m;
 }
 
+// ONEBAR = false: per plane a barrier after the TMA wait and one after the conversion.
+// ONEBAR = true: every thread waits on the plane it converts and the conversion runs one plane
+// further ahead, so a single barrier per plane orders everything.
+template <bool ONEBAR>
 __global__ void __launch_bounds__(NTHR, 4)
     k_fused_adj3d(const __grid_constant__ CUtensorMap tmap, const AdjArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -223,7 +227,7 @@ __global__ void __launch_bounds__(NTHR, 4)
     if (tid == 0) {
         for (int s = 0; s < NSLOT; ++s) mbar_init(smem_addr(&bars[s]));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        for (int k = 0; k < 2 && k < nplanes; ++k)
+        for (int k = 0; k < (ONEBAR ? NSLOT : 2) && k < nplanes; ++k)
             tma_load_box(smem_addr(raw + (size_t)k * SLOT), &tmap, x0 - 2, y0 - 2,
                          q0 - 2 + k, smem_addr(&bars[k]), PLANE_BYTES);
     }
@@ -247,50 +251,11 @@ __global__ void __launch_bounds__(NTHR, 4)
     Mom prev = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     float szm_x = 0.f, szm_y = 0.f, szm_z = 0.f;   // S~_{.z} of plane p-2
     bool ok = true;
-    int cslot = 0;                 // slot of the plane being converted (k = p - q0 + 3)
-    int wpar = 0;                  // parity of the load in cslot
-    int ik = 2, islot = 2;         // next load to issue
-
-    for (int p = q0 - 3; p <= q1; ++p) {
-        bool good = true;
-        if (tid == 0) good = mbar_wait(smem_addr(&bars[cslot]), wpar);
-        if (__syncthreads_or(!good)) {
-            ok = false;
-            break;
-        }
-        if (tid == 0 && ik < nplanes) {
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            tma_load_box(smem_addr(raw + (size_t)islot * SLOT), &tmap, x0 - 2, y0 - 2,
-                         q0 - 2 + ik, smem_addr(&bars[islot]), PLANE_BYTES);
-        }
-        ++ik;
-        if (++islot == NSLOT) islot = 0;
-        // u^{n-1} of this column's output plane p - 1, fetched before the stencil work
+    // moments of plane p from the converted planes p-1 (rm), p (r0), p+1 (rp) on the tile and
+    // its rim, then lambda^{n-1} of plane p-1 (u: u^{n-1} there)
+    auto plane = [&](int p, const float4* rm, const float4* r0, const float4* rp,
+                     const float4& u, bool write_out) {
         const int q = p - 1;
-        const bool write_out = q >= q0 && own_in;
-        float4 u = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (write_out) u = a.sp[q * zstride + col];
-        // 1. lambda -> mu for plane p + 1
-        {
-            float4* pl = raw + (size_t)cslot * SLOT;
-            const int gz = p + 1;
-            to_mu(a, pl[hp], cf_own, gx, gy, gz, own_in, has_obj);
-            if (tid < NRIM2)
-                to_mu(a, pl[hc], cf_halo, x0 - 2 + cx, y0 - 2 + cy, gz, false, has_obj);
-        }
-        const int sl_p = cslot;                                   // plane p + 1
-        const int sl_0 = cslot == 0 ? NSLOT - 1 : cslot - 1;      // plane p
-        const int sl_m = sl_0 == 0 ? NSLOT - 1 : sl_0 - 1;        // plane p - 1
-        if (++cslot == NSLOT) {
-            cslot = 0;
-            wpar ^= 1;
-        }
-        __syncthreads();
-        if (p < q0 - 1) continue;
-        // 2. moments of plane p on the tile and its rim
-        const float4* rm = raw + (size_t)sl_m * SLOT;
-        const float4* r0 = raw + (size_t)sl_0 * SLOT;
-        const float4* rp = raw + (size_t)sl_p * SLOT;
         float* sw = sS + (size_t)(p & 1) * NS * FS;
         const Mom m = moments(a, r0 + hp, rm + hp, rp + hp);
         sw[0 * FS + fo] = m.Sxx;
@@ -353,6 +318,85 @@ __global__ void __launch_bounds__(NTHR, 4)
         szm_y = prev.Syz;
         szm_z = prev.Szz;
         prev = m;
+    };
+
+    if (!ONEBAR) {
+        int cslot = 0;                 // slot of the plane being converted (k = p - q0 + 3)
+        int wpar = 0;                  // parity of the load in cslot
+        int ik = 2, islot = 2;         // next load to issue
+        for (int p = q0 - 3; p <= q1; ++p) {
+            bool good = true;
+            if (tid == 0) good = mbar_wait(smem_addr(&bars[cslot]), wpar);
+            if (__syncthreads_or(!good)) {
+                ok = false;
+                break;
+            }
+            if (tid == 0 && ik < nplanes) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                tma_load_box(smem_addr(raw + (size_t)islot * SLOT), &tmap, x0 - 2, y0 - 2,
+                             q0 - 2 + ik, smem_addr(&bars[islot]), PLANE_BYTES);
+            }
+            ++ik;
+            if (++islot == NSLOT) islot = 0;
+            // u^{n-1} of this column's output plane p - 1, fetched before the stencil work
+            const int q = p - 1;
+            const bool write_out = q >= q0 && own_in;
+            float4 u = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (write_out) u = a.sp[q * zstride + col];
+            // 1. lambda -> mu for plane p + 1
+            {
+                float4* pl = raw + (size_t)cslot * SLOT;
+                const int gz = p + 1;
+                to_mu(a, pl[hp], cf_own, gx, gy, gz, own_in, has_obj);
+                if (tid < NRIM2)
+                    to_mu(a, pl[hc], cf_halo, x0 - 2 + cx, y0 - 2 + cy, gz, false, has_obj);
+            }
+            const int sl_p = cslot;                                   // plane p + 1
+            const int sl_0 = cslot == 0 ? NSLOT - 1 : cslot - 1;      // plane p
+            const int sl_m = sl_0 == 0 ? NSLOT - 1 : sl_0 - 1;        // plane p - 1
+            if (++cslot == NSLOT) {
+                cslot = 0;
+                wpar ^= 1;
+            }
+            __syncthreads();
+            if (p < q0 - 1) continue;
+            plane(p, raw + (size_t)sl_m * SLOT, raw + (size_t)sl_0 * SLOT,
+                  raw + (size_t)sl_p * SLOT, u, write_out);
+        }
+    } else {
+        // one barrier per plane: iteration p converts plane p + 2 (load kc) while it forms the
+        // moments of plane p from planes converted before the previous barrier
+        int kc = 0;
+        for (int p = q0 - 4; p <= q1; ++p, ++kc) {
+            bool good = true;
+            const int q = p - 1;
+            const bool write_out = q >= q0 && own_in;
+            float4 u = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (write_out) u = a.sp[q * zstride + col];
+            if (kc < nplanes) {
+                good = mbar_wait_once(smem_addr(&bars[kc % NSLOT]), (kc / NSLOT) & 1);
+                float4* pl = raw + (size_t)(kc % NSLOT) * SLOT;
+                const int gz = p + 2;
+                to_mu(a, pl[hp], cf_own, gx, gy, gz, own_in, has_obj);
+                if (tid < NRIM2)
+                    to_mu(a, pl[hc], cf_halo, x0 - 2 + cx, y0 - 2 + cy, gz, false, has_obj);
+            }
+            if (p >= q0 - 1)
+                plane(p, raw + (size_t)((kc - 3) % NSLOT) * SLOT,
+                      raw + (size_t)((kc - 2) % NSLOT) * SLOT,
+                      raw + (size_t)((kc - 1) % NSLOT) * SLOT, u, write_out);
+            if (__syncthreads_or(!good)) {
+                ok = false;
+                break;
+            }
+            // the slot of plane p - 1 (load kc - 3) is free: it takes load kc + 2
+            const int kn = kc + 2;
+            if (tid == 0 && kn >= NSLOT && kn < nplanes) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                tma_load_box(smem_addr(raw + (size_t)(kn % NSLOT) * SLOT), &tmap, x0 - 2,
+                             y0 - 2, q0 - 2 + kn, smem_addr(&bars[kn % NSLOT]), PLANE_BYTES);
+            }
+        }
     }
     if (!ok) {
         if (tid == 0) {
@@ -432,15 +476,19 @@ void face_offsets(const Geom& g, FaceOffsets& fo, long long& total) {
 
 cudaError_t launch_fused_adj3d(const Geom& g, const V4<float>* lam_in, V4<float>* lam_out,
                                const V4<float>* kus, const V4<float>* sn, const V4<float>* sp,
-                               float* e, float* face, double h, int* err, cudaStream_t st) {
+                               float* e, float* face, double h, int* err, cudaStream_t st,
+                               int variant) {
     CUtensorMap map;
     // a box one column wider than the tile: the unused last column pads the row pitch
     if (!encode_state_map(&map, lam_in, g, PX, HY)) return cudaErrorInvalidValue;
     static std::atomic<unsigned> attr{0};   // devices whose shared-memory limit is raised
     if (!device_done(attr)) {
-        cudaError_t r = cudaFuncSetAttribute(k_fused_adj3d,
+        cudaError_t r = cudaFuncSetAttribute(k_fused_adj3d<false>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)SMEM_BYTES);
+        if (r == cudaSuccess)
+            r = cudaFuncSetAttribute(k_fused_adj3d<true>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
         if (r != cudaSuccess) return r;
         device_mark(attr);
     }
@@ -469,7 +517,10 @@ cudaError_t launch_fused_adj3d(const Geom& g, const V4<float>* lam_in, V4<float>
     const int tiles_x = (g.n[0] + TX - 1) / TX, tiles_y = (g.n[1] + TY - 1) / TY;
     a.zchunk = fused_zchunk_waves(g, (long long)tiles_x * tiles_y, 4);
     const int chunks = (g.n[2] + a.zchunk - 1) / a.zchunk;
-    k_fused_adj3d<<<dim3(tiles_x, tiles_y, chunks), NTHR, SMEM_BYTES, st>>>(map, a);
+    if (variant == 1)
+        k_fused_adj3d<true><<<dim3(tiles_x, tiles_y, chunks), NTHR, SMEM_BYTES, st>>>(map, a);
+    else
+        k_fused_adj3d<false><<<dim3(tiles_x, tiles_y, chunks), NTHR, SMEM_BYTES, st>>>(map, a);
     cudaError_t r = cudaGetLastError();
     if (r != cudaSuccess) return r;
     const long long shell = 6LL * ((long long)g.n[1] * g.n[2] + (long long)g.n[0] * g.n[2] +

@@ -146,9 +146,12 @@ cudaError_t launch_fused_step3d(const Geom& g, const V4<float>* src, const V4<fl
                                 V4<float>* dst, int* err, cudaStream_t st, int variant);
 // Offsets of the six face arrays (3 floats per face node) and their total length.
 void face_offsets(const Geom& g, FaceOffsets& fo, long long& total);
+// variant 0: two block barriers per plane; 1: one barrier per plane (conversion one plane ahead)
+constexpr int kAdj3dVariants = 2;
 cudaError_t launch_fused_adj3d(const Geom& g, const V4<float>* lam_in, V4<float>* lam_out,
                                const V4<float>* kus, const V4<float>* sn, const V4<float>* sp,
-                               float* e, float* face, double h, int* err, cudaStream_t st);
+                               float* e, float* face, double h, int* err, cudaStream_t st,
+                               int variant);
 
 template <class T>
 void launch_design_prep(const Design& d, const double* gamma, double kappa_max, double q,

@@ -366,21 +366,27 @@ __global__ void k_adj_moments(Geom g, const V4<T>* __restrict__ mu,
             S[a] = W::s_1 * (fp + fm);   // 9 S~_aa, corners added below
         }
         // corners: sums of F~ over the 8 sign patterns weighted by 1, sx, sy, sz, sx sy, sx sz,
-        // sy sz
-        T c1 = 0, cx = 0, cy = 0, cz = 0, cxy = 0, cxz = 0, cyz = 0;
+        // sy sz, as butterflies over sx, then sy, then sz
+        T f[8];
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
             const int sx = (k & 1) ? -1 : 1, sy = (k & 2) ? -1 : 1, sz = (k & 4) ? -1 : 1;
             const V4<T> n = mu_at<T>(g, mu, c, sx, sy, sz);
-            const T f = n.r + (T)sx * n.x + (T)sy * n.y + (T)sz * n.z;
-            c1 += f;
-            cx += (T)sx * f;
-            cy += (T)sy * f;
-            cz += (T)sz * f;
-            cxy += (T)(sx * sy) * f;
-            cxz += (T)(sx * sz) * f;
-            cyz += (T)(sy * sz) * f;
+            const T bx = sx > 0 ? n.r + n.x : n.r - n.x;
+            const T by = sy > 0 ? bx + n.y : bx - n.y;
+            f[k] = sz > 0 ? by + n.z : by - n.z;
         }
+        T a[4], b[4];   // over sx: index (sy, sz) = k >> 1
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            a[j] = f[2 * j] + f[2 * j + 1];
+            b[j] = f[2 * j] - f[2 * j + 1];
+        }
+        // over sy: index sz
+        const T A0 = a[0] + a[1], A1 = a[2] + a[3], Ay0 = a[0] - a[1], Ay1 = a[2] - a[3];
+        const T B0 = b[0] + b[1], B1 = b[2] + b[3], By0 = b[0] - b[1], By1 = b[2] - b[3];
+        const T c1 = A0 + A1, cz = A0 - A1, cy = Ay0 + Ay1, cyz = Ay0 - Ay1;
+        const T cx = B0 + B1, cxz = B0 - B1, cxy = By0 + By1;
         R = W::w0 * s0.r + W::w1 * ax_sum + W::w2 * c1;
         U[0] += W::w3_2 * cx;
         U[1] += W::w3_2 * cy;
@@ -404,17 +410,16 @@ __global__ void k_adj_moments(Geom g, const V4<T>* __restrict__ mu,
             U[a] = W::w3_1 * (fp - fm);
             S[a] = W::s_1 * (fp + fm);
         }
-        T c1 = 0, cx = 0, cy = 0, cxy = 0;
+        T f[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             const int sx = (k & 1) ? -1 : 1, sy = (k & 2) ? -1 : 1;
             const V4<T> n = mu_at<T>(g, mu, c, sx, sy, 0);
-            const T f = n.r + (T)sx * n.x + (T)sy * n.y;
-            c1 += f;
-            cx += (T)sx * f;
-            cy += (T)sy * f;
-            cxy += (T)(sx * sy) * f;
+            const T bx = sx > 0 ? n.r + n.x : n.r - n.x;
+            f[k] = sy > 0 ? bx + n.y : bx - n.y;
         }
+        const T a0 = f[0] + f[1], a1 = f[2] + f[3], b0 = f[0] - f[1], b1 = f[2] - f[3];
+        const T c1 = a0 + a1, cy = a0 - a1, cx = b0 + b1, cxy = b0 - b1;
         R = W::w0 * s0.r + W::w1 * ax_sum + W::w2 * c1;
         U[0] += W::w3_2 * cx;
         U[1] += W::w3_2 * cy;

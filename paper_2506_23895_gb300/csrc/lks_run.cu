@@ -318,7 +318,7 @@ lks_status adjoint_step(lks_ctx* c, int n, const void* sn, const void* sp) {
         cudaError_t e = launch_fused_adj3d(c->g, (const V4<float>*)lc, (V4<float>*)ln,
                                            (const V4<float>*)c->kus, (const V4<float>*)sn,
                                            (const V4<float>*)sp, (float*)c->e, c->face, hn,
-                                           c->flags + 3, c->st);
+                                           c->flags + 3, c->st, c->adj3d_var);
         if (e != cudaSuccess) return fail(c, LKS_ERR_CUDA, "fused adjoint: %s", cudaGetErrorString(e));
         c->stats[4] += 2;
     } else {

@@ -45,6 +45,19 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
     }
 }
 
+// A wait that first polls once (the common case: the copy has landed), then falls back to the
+// bounded wait.
+__device__ __forceinline__ bool mbar_wait_once(uint32_t bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;"
+        " selp.u32 %0, 1, 0, p; }"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return done ? true : mbar_wait(bar, parity);
+}
+
 struct Geom;
 // Host: tensor map over a float4-per-node state {4, nx, ny, nz} with box {4, bx, by, 1}.
 bool encode_state_map(CUtensorMap* map, const void* base, const Geom& g, int bx, int by);

@@ -28,7 +28,7 @@ EXPORTS = ("lks_workspace_bytes", "lks_create", "lks_set_design", "lks_set_motio
            "lks_batch_tile_shapes", "lks_batch_tuning", "lks_batch_stats",
            "lks_batch_last_error", "lks_batch_destroy", "lks_set_filter", "lks_volume",
            "lks_set_static", "lks_warm_start", "lks_set_adjoint_start", "lks_get_adjoint_state",
-           "lks_inject_alloc_failure", "lks_fma_rate")
+           "lks_inject_alloc_failure", "lks_fma_rate", "lks_adjoint_variant")
 
 
 class LksError(RuntimeError):
@@ -95,6 +95,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.lks_uses_fused.argtypes = [P]
     lib.lks_uses_fused.restype = ctypes.c_int
     lib.lks_step_variant.argtypes = [P, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+    lib.lks_adjoint_variant.argtypes = [P, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+    lib.lks_adjoint_variant.restype = ctypes.c_int
     lib.lks_set_timing.argtypes = [P, ctypes.c_int]
     lib.lks_read_timing.argtypes = [P, D]
     lib.lks_checkpoint_schedule.argtypes = [ctypes.c_int, ctypes.c_int,
@@ -348,6 +350,12 @@ class Solver:
         first step, -2 only reads; returns the variant in use (-1 before the first fused step)."""
         v = ctypes.c_int(-1)
         self._check(self.lib.lks_step_variant(self.ctx, request, ctypes.byref(v)))
+        return v.value
+
+    def adjoint_variant(self, request: int = -2) -> int:
+        """Fix (0..1) or read (-2) the fused 3D adjoint variant; returns the variant in use."""
+        v = ctypes.c_int(-1)
+        self._check(self.lib.lks_adjoint_variant(self.ctx, request, ctypes.byref(v)))
         return v.value
 
     def set_timing(self, stride: int) -> None:

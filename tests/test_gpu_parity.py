@@ -334,3 +334,29 @@ def test_transfer_buffers_do_not_leak_across_runs(L):
     assert J2 == Jb and np.array_equal(g2_, gb)
     assert J3 == Jc and np.array_equal(g3, gc)
     assert not np.array_equal(k_before, k_after)
+
+
+@pytest.mark.parametrize("name", ["small3d_J1", "ragged3d", "mid3d", "corners3d"])
+def test_fused_adjoint_variants_agree(L, name):
+    """Both schedules of the fused 3D adjoint (two barriers per plane; conversion two planes
+    ahead with one barrier) evaluate the same arithmetic in the same order: the gradients are
+    bitwise equal, and within the FP32 tolerances of the oracle."""
+    w = MID3D() if name == "mid3d" else CASES[name]()
+    Jo, go = oracle.gradient(w.problem, w.gamma, w.motion)
+    res = []
+    for v in range(2):
+        s = L.Solver(w.problem, L.FP32)
+        assert s.adjoint_variant(v) == v
+        s.set_design(w.gamma)
+        s.set_motion(w.motion)
+        J = s.forward()
+        res.append((J, s.adjoint()))
+        assert s.adjoint_variant() == v
+        s.close()
+    assert res[0][0] == res[1][0]
+    assert np.array_equal(res[0][1], res[1][1])
+    assert rel_l2(res[1][1], go) < 1e-4
+    s = L.Solver(w.problem, L.FP32)
+    with pytest.raises(L.LksError):
+        s.adjoint_variant(2)
+    s.close()
