@@ -207,8 +207,9 @@ lks_status lks_step_variant(lks_ctx* ctx, int request, int* chosen);
 /* Variant of the fused FP32 3D adjoint step (Sec. 2.4's adjoint equations, Eqs. arho, au, as;
  * used when lks_uses_fused returns 1): 0 converts lambda to mu one plane ahead of the moments
  * with two block barriers per plane, 1 converts two planes ahead with one barrier per plane.
- * Both evaluate the same arithmetic in the same order (results bitwise equal).  request 0..1
- * fixes the variant, -2 changes nothing; *chosen (may be NULL) receives the variant in use.
+ * Both evaluate the same arithmetic in the same order (results bitwise equal); 1 is the default.
+ * request 0..1 fixes the variant, -2 changes nothing; *chosen (may be NULL) receives the variant
+ * in use.
  * LKS_ERR_ARG for any other request.  Host only. */
 lks_status lks_adjoint_variant(lks_ctx* ctx, int request, int* chosen);
 

@@ -107,7 +107,7 @@ struct lks_ctx {
     bool gaxis = false;          // 3D rotation about an axis other than z
     int step3d_req = 1;          // fused 3D step variant requested (-1: time them once)
     int step3d_var = -1;         // variant in use (-1: not chosen yet)
-    int adj3d_var = 0;           // fused 3D adjoint variant (kAdj3dVariants)
+    int adj3d_var = 1;           // fused 3D adjoint variant (kAdj3dVariants)
     double axis[3] = {0.0, 0.0, 1.0};
     AxisScratch as;
     // 3D transfers in two buffer sets: the current one (kus, k2, ts, as above point into it)

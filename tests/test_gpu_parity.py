@@ -357,6 +357,7 @@ def test_fused_adjoint_variants_agree(L, name):
     assert np.array_equal(res[0][1], res[1][1])
     assert rel_l2(res[1][1], go) < 1e-4
     s = L.Solver(w.problem, L.FP32)
+    assert s.adjoint_variant() == 1   # the one-barrier schedule is the default
     with pytest.raises(L.LksError):
         s.adjoint_variant(2)
     s.close()
