@@ -16,6 +16,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "lks_device.cuh"
 #include "lks_tma.cuh"
@@ -574,9 +575,14 @@ __device__ __forceinline__ void zbody(const CUtensorMap& tmap, const FusedArgs& 
     int s0 = 1;                    // slot of plane p
     int wslot = 2, wpar = 0;       // slot / parity of plane p + 1
     int islot = 0, ik = NSLOT;     // next refill: slot and load index
-
-    for (int p = q0 - 1; ok && p <= q1; ++p) {
-        const bool good = mbar_wait(smem_addr(&bars[wslot]), wpar);
+    // the output node of plane p - 1 in the column, advanced one plane per iteration (it is
+    // only dereferenced for planes inside the grid)
+    float4* outp = out_col_ptr + (long long)(q0 - 3) * zstride;
+    // One plane p.  STEADY (interior tiles, planes away from the z faces and from the chunk's
+    // first output): no z-face derivative modes, no output-range and no boundary-copy tests.
+    auto plane = [&](int p, auto steady) {
+        constexpr bool STEADY = decltype(steady)::value;
+        const bool good = mbar_wait_once(smem_addr(&bars[wslot]), wpar);
         const float4* r0 = raw + (size_t)s0 * C::SLOT;
         const float4* rp = raw + (size_t)wslot * C::SLOT;
         float* sF = sFbase + (size_t)((p - q0 + 1) & 1) * NCROSS * FS;
@@ -587,8 +593,8 @@ __device__ __forceinline__ void zbody(const CUtensorMap& tmap, const FusedArgs& 
         if (has_rim) rcpn = rp[hr];
         const float3 rup = make_float3(rcpn.y, rcpn.z, rcpn.w);
         float f_rest, f_pz, f_mz;
-        const int zm = (p == 0) ? 1 : (p == nz - 1 ? 2 : 0);
-        if (!edge && zm == 0) {
+        const int zm = STEADY ? 0 : ((p == 0) ? 1 : (p == nz - 1 ? 2 : 0));
+        if (STEADY || (!edge && zm == 0)) {
             const float4 z0 = make_float4(0.f, 0.f, 0.f, 0.f);
             feq_reg<HX, FS, false>(a, r0 + hp, c0, um, up, sFp, 0, 0, 0, z0, f_rest, f_pz, f_mz);
             if (has_rim) {
@@ -616,7 +622,7 @@ __device__ __forceinline__ void zbody(const CUtensorMap& tmap, const FusedArgs& 
         rc0 = rcpn;
         if (__syncthreads_or(!good)) {
             ok = false;
-            break;
+            return;
         }
         // every thread is past its reads of plane p - 1: its slot takes load k(p) - 1 + NSLOT
         if (tid == 0 && ik < nplanes) {
@@ -637,12 +643,13 @@ __device__ __forceinline__ void zbody(const CUtensorMap& tmap, const FusedArgs& 
         const float cpm_p = sFp[6 * FS - 1 + FX], cmm_p = sFp[7 * FS + 1 + FX];
         const float cpp_m = sFp[8 * FS - 1 - FX], cmp_m = sFp[9 * FS + 1 - FX];
         const float cpm_m = sFp[10 * FS - 1 + FX], cmm_m = sFp[11 * FS + 1 + FX];
+        outp += zstride;   // plane p - 1
         {
             const float sxp = cpp_m + cpm_m, sxm = cmp_m + cmm_m;
             const float syp = cpp_m + cmp_m, sym = cpm_m + cmm_m;
             const float all = sxp + sxm + f_mz;
             const int qz = p - 1;
-            if (out_col && qz >= zlo && qz <= zhi) {
+            if (STEADY || (out_col && qz >= zlo && qz <= zhi)) {
                 const float r = acc0[0] + all;
                 const float ux = acc0[1] + (sxp - sxm) + bfx;
                 const float uy = acc0[2] + (syp - sym) + bfy;
@@ -661,8 +668,9 @@ __device__ __forceinline__ void zbody(const CUtensorMap& tmap, const FusedArgs& 
                     o.z = uy;
                     o.w = uz;
                 }
-                out_col_ptr[(long long)qz * zstride] = o;
-                if (bc_col || qz == 1 || qz == nz - 2) write_bc_f(g, gx, gy, qz, o, a.out);
+                *outp = o;
+                if (!STEADY && (bc_col || qz == 1 || qz == nz - 2))
+                    write_bc_f(g, gx, gy, qz, o, a.out);
             }
         }
         acc0[0] = acc1[0] + (f_rest + fpx + fmx + fpy + fmy);
@@ -678,6 +686,14 @@ __device__ __forceinline__ void zbody(const CUtensorMap& tmap, const FusedArgs& 
             acc1[2] = syp - sym;
             acc1[3] = all;
         }
+    };
+    // steady planes: output plane p - 1 in [max(q0, 2), nz - 3] and f^eq plane p off the faces
+    const int ps0 = max(q0 + 1, 3), ps1 = min(q1, nz - 2);
+    for (int p = q0 - 1; ok && p <= q1; ++p) {
+        if (IN && p >= ps0 && p <= ps1)
+            plane(p, std::true_type{});
+        else
+            plane(p, std::false_type{});
     }
     if (!ok) {
         if (tid == 0) {
