@@ -688,13 +688,12 @@ __device__ __forceinline__ void zbody(const CUtensorMap& tmap, const FusedArgs& 
         }
     };
     // steady planes: output plane p - 1 in [max(q0, 2), nz - 3] and f^eq plane p off the faces
-    const int ps0 = max(q0 + 1, 3), ps1 = min(q1, nz - 2);
-    for (int p = q0 - 1; ok && p <= q1; ++p) {
-        if (IN && p >= ps0 && p <= ps1)
-            plane(p, std::true_type{});
-        else
-            plane(p, std::false_type{});
-    }
+    const int ps0 = IN ? max(q0 + 1, 3) : q1 + 1, ps1 = IN ? min(q1, nz - 2) : q1;
+    int p = q0 - 1;
+    for (; ok && p <= q1 && p < ps0; ++p) plane(p, std::false_type{});
+#pragma unroll 1
+    for (; ok && p <= ps1; ++p) plane(p, std::true_type{});
+    for (; ok && p <= q1; ++p) plane(p, std::false_type{});
     if (!ok) {
         if (tid == 0) {
             atomicOr(a.err, 8);
@@ -1251,14 +1250,15 @@ bool encode_state_map(CUtensorMap* map, const void* base, const Geom& g, int bx,
 }
 
 // Planes per z chunk so that the grid fills a whole number of waves of `per_sm` resident
-// blocks per SM (the smallest such count with chunks of at least 24 planes), else as few
-// chunks as that floor allows.
+// blocks per SM, weighing each chunk's three warm-up planes: the chunk count with the best
+// product of wave fill and useful-plane fraction, chunks of at least 8 planes (small grids need
+// many chunks to fill the SMs at all).
 int fused_zchunk_waves(const Geom& g, long long tiles, int per_sm) {
     int dev = 0, nsm = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     const long long slots = (long long)nsm * per_sm;
-    const int maxc = std::max(1, g.n[2] / 24);
+    const int maxc = std::max(1, g.n[2] / 8);
     int best = 1;
     double best_eff = 0.0;
     for (int c = 1; c <= maxc; ++c) {

@@ -23,6 +23,7 @@ namespace lks {
 namespace {
 
 constexpr int kThreads = 256;
+constexpr int kSmallThreads = 64;
 inline unsigned grid_for(long long n) { return (unsigned)((n + kThreads - 1) / kThreads); }
 
 __global__ void k_design_prep_check(long long nd, const double* gamma, int* bad) {
@@ -371,7 +372,10 @@ void launch_design_pos(const Design& d, const Geom& g, const Motion& m, Transfer
                        cudaStream_t st) {
     if (d.nd == 0 || g.boxN == 0) return;
     const long long n = d.ncol + d.L[2] + g.bn[2];
-    k_design_pos<T><<<grid_for(n), kThreads, 0, st>>>(d, g, m, ts);
+    // small blocks: these grids are a few hundred to a few thousand threads, and their
+    // dependent scattered reads want as many SMs as possible
+    k_design_pos<T><<<(unsigned)((n + kSmallThreads - 1) / kSmallThreads), kSmallThreads, 0, st>>>(
+        d, g, m, ts);
 }
 
 template <class T>
@@ -379,7 +383,8 @@ void launch_transfer(const Design& d, const Geom& g, const Motion& m, TransferSc
                      const T* kref_t, T* k2, V4<T>* kus, cudaStream_t st) {
     if (d.nd == 0 || g.boxN == 0) return;
     const long long ncols = (long long)g.bn[0] * g.bn[1];
-    k_tap_lists<T><<<grid_for(ncols), kThreads, 0, st>>>(d, g, m, ts);
+    k_tap_lists<T><<<(unsigned)((ncols + kSmallThreads - 1) / kSmallThreads), kSmallThreads, 0,
+                     st>>>(d, g, m, ts);
     const int lanes = d.L[2] >= 32 ? 32 : (d.L[2] >= 8 ? 8 : 1);
     const dim3 blk(lanes, kThreads / lanes);
     const dim3 grd((unsigned)((d.L[2] + lanes - 1) / lanes),
