@@ -83,13 +83,16 @@ __device__ __forceinline__ void feq_pairs3(const V4<T>& v, const T S[3][3], T A,
         F[(2 + 2 * a) * stride] = sym - W::w3_1 * u[a];
     }
     const T tr = S[0][0] + S[1][1] + S[2][2];
-    // corners k = 0..3 have sz = +1 (directions 7..10), their opposites are 14..11
+    // corners k = 0..3 have sz = +1 (directions 7..10), their opposites are 14..11:
+    // c.S.c = tr S + 2 (sx sy S_xy + sx S_xz + sy S_yz)
+    const T base = W::w2 * (P + A * tr), A2w = (T)2 * A * W::w2;
+    const T xy = A2w * S[0][1], xz = A2w * S[0][2], yz = A2w * S[1][2];
+    const T cross[4] = {xy + xz + yz, -xy - xz + yz, -xy + xz - yz, xy - xz - yz};
+    const T cuv[4] = {ux + uy + uz, -ux + uy + uz, ux - uy + uz, -ux - uy + uz};
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        const T sx = (k & 1) ? (T)-1 : (T)1, sy = (k & 2) ? (T)-1 : (T)1;
-        const T cu = sx * ux + sy * uy + uz;
-        const T cSc = tr + (T)2 * (sx * sy * S[0][1] + sx * S[0][2] + sy * S[1][2]);
-        const T sym = W::w2 * (P + A * cSc) + W::h_2 * cu * cu;
+        const T cu = cuv[k];
+        const T sym = (base + cross[k]) + W::h_2 * cu * cu;
         F[(7 + k) * stride] = sym + W::w3_2 * cu;
         F[(14 - k) * stride] = sym - W::w3_2 * cu;
     }
@@ -133,19 +136,34 @@ __global__ void k_feq(Geom g, const V4<T>* __restrict__ s, T* __restrict__ F) {
     for (int a = 0; a < 3; ++a)
 #pragma unroll
         for (int b = 0; b < 3; ++b) G[a][b] = (T)0;
+    bool inner = true;   // central differences along every axis without a wrap
 #pragma unroll
-    for (int b = 0; b < D; ++b) {
-        const int i = c[b], n = g.n[b], per = g.periodic[b];
+    for (int b = 0; b < D; ++b) inner = inner && c[b] >= 1 && c[b] <= g.n[b] - 2;
+    if (inner) {
+        long long st = 1;
 #pragma unroll
-        for (int off = -2; off <= 2; ++off) {
-            const T cf = (T)deriv_coef(i, n, per, off);
-            if (cf == (T)0) continue;
-            int q[3] = {c[0], c[1], c[2]};
-            q[b] = wrapi(i + off, n);
-            const V4<T> w = s[node_index(g, q[0], q[1], q[2])];
-            G[0][b] += cf * w.x;
-            G[1][b] += cf * w.y;
-            if (D == 3) G[2][b] += cf * w.z;
+        for (int b = 0; b < D; ++b) {
+            const V4<T> wp = s[m + st], wm = s[m - st];
+            G[0][b] = (T)0.5 * (wp.x - wm.x);
+            G[1][b] = (T)0.5 * (wp.y - wm.y);
+            if (D == 3) G[2][b] = (T)0.5 * (wp.z - wm.z);
+            st *= g.n[b];
+        }
+    } else {
+#pragma unroll
+        for (int b = 0; b < D; ++b) {
+            const int i = c[b], n = g.n[b], per = g.periodic[b];
+#pragma unroll
+            for (int off = -2; off <= 2; ++off) {
+                const T cf = (T)deriv_coef(i, n, per, off);
+                if (cf == (T)0) continue;
+                int q[3] = {c[0], c[1], c[2]};
+                q[b] = wrapi(i + off, n);
+                const V4<T> w = s[node_index(g, q[0], q[1], q[2])];
+                G[0][b] += cf * w.x;
+                G[1][b] += cf * w.y;
+                if (D == 3) G[2][b] += cf * w.z;
+            }
         }
     }
     T S[3][3];
