@@ -10,8 +10,8 @@
 //                 the z taps of every analysis plane of the footprint box;
 //   k_tap_lists   for each analysis column of the box, the design columns whose support covers
 //                 it (found through the inverse rigid map) with their x-y weights, in design
-//                 index order, plus the moments m0 = sum W, m1 = sum W (xi - xi_G);
-//   k_col_planes  for every box column and design plane, the x-y transfer of kappa_ref;
+//                 index order, the moments m0 = sum W, m1 = sum W (xi - xi_G), and for every
+//                 design plane the x-y transfer of kappa_ref;
 //   k_fill        kappa = sum over the z taps of that, u_S = omega R'(theta) m1 + u_G m0, on
 //                 the box: deterministic gathers, no atomics;
 //   k_sens        for each design node, sum_x W(x - x_ref) e(x) over its 4^d support (the
@@ -103,69 +103,100 @@ __global__ void k_design_pos(Design d, Geom g, Motion m, TransferScratch ts) {
     }
 }
 
+// One warp per box column.  The lanes test the candidate design columns of a window around the
+// inverse rigid map (j outer, i inner, 32 at a time); a ballot keeps the accepted ones in that
+// order, and every lane sums the moments over them in the same order, so the lists and sums are
+// those of a sequential scan.  The window is found in single precision with a margin far above
+// its rounding: it only has to contain the support, each candidate is tested exactly.  The warp
+// then forms K2[col][zeta] = sum over the taps of W_xy kappa_ref(zeta, tap), the x-y transfer of
+// every design plane, lanes running along zeta (coalesced in kref_t), taps in list order.
+constexpr int kTapWarps = kThreads / 32;
+
 template <class T>
-__global__ void k_tap_lists(Design d, Geom g, Motion m, TransferScratch ts) {
+__global__ void __launch_bounds__(kThreads)
+    k_tap_lists(Design d, Geom g, Motion m, TransferScratch ts, const T* __restrict__ kref_t,
+                T* __restrict__ k2) {
+    __shared__ T s_w[kTapWarps][kMaxTaps];
+    __shared__ int s_k[kTapWarps][kMaxTaps];
     const long long ncols = (long long)g.bn[0] * g.bn[1];
-    long long col = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (col >= ncols) return;
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long col = (long long)blockIdx.x * kTapWarps + wid;
+    if (col >= ncols) return;   // whole warps
     const int x = g.blo[0] + (int)(col % g.bn[0]);
     const int y = g.blo[1] + (int)(col / g.bn[0]);
     // inverse rigid map: design coordinates of this analysis column
-    const double px = x - m.xG[0], py = y - m.xG[1];
-    const double ic = m.c * px + m.s * py + d.xiG[0];
-    const double jc = -m.s * px + m.c * py + d.xiG[1];
-    const double R = 2.0 * (fabs(m.c) + fabs(m.s)) + 1e-6;
-    const int i0 = max(0, (int)ceil(ic - R)), i1 = min(d.L[0] - 1, (int)floor(ic + R));
-    const int j0 = max(0, (int)ceil(jc - R)), j1 = min(d.L[1] - 1, (int)floor(jc + R));
+    const float px = (float)x - m.xgf[0], py = (float)y - m.xgf[1];
+    const float ic = fmaf(m.cf, px, fmaf(m.sf, py, d.xiGf[0]));
+    const float jc = fmaf(-m.sf, px, fmaf(m.cf, py, d.xiGf[1]));
+    const float R = 2.f * (fabsf(m.cf) + fabsf(m.sf)) + 0.01f;
+    const int i0 = max(0, (int)ceilf(ic - R)), i1 = min(d.L[0] - 1, (int)floorf(ic + R));
+    const int j0 = max(0, (int)ceilf(jc - R)), j1 = min(d.L[1] - 1, (int)floorf(jc + R));
+    const int wi = i1 - i0 + 1;
+    const int nc = (wi > 0 && j1 >= j0) ? wi * (j1 - j0 + 1) : 0;
+    // xi - xi_G in T: from the single-precision centre where that is exact
+    const bool fxi = sizeof(T) == 4 && (double)d.xiGf[0] == d.xiG[0] &&
+                     (double)d.xiGf[1] == d.xiG[1];
     const T* frac = (const T*)ts.col_frac;
     int* tidx = ts.tap_idx + col * kMaxTaps;
     T* tw = (T*)ts.tap_w + col * kMaxTaps;
     int cnt = 0;
+    bool over = false;
     T m0 = (T)0, m1x = (T)0, m1y = (T)0;
-    for (int j = j0; j <= j1; ++j)
-        for (int i = i0; i <= i1; ++i) {
-            const long long k = (long long)j * d.L[0] + i;
+    for (int b = 0; b < nc && !over; b += 32) {
+        const int c = b + lane;
+        int k = 0;
+        T W = (T)0, di = (T)0, dj = (T)0;
+        if (c < nc) {
+            const int j = j0 + c / wi, i = i0 + c % wi;
+            k = j * d.L[0] + i;
             const T rx = (T)(x - ts.col_base[2 * k]) - frac[2 * k];
             const T ry = (T)(y - ts.col_base[2 * k + 1]) - frac[2 * k + 1];
-            if (!(fabs(rx) < (T)2 && fabs(ry) < (T)2)) continue;   // exact in T
-            const T W = peskin(rx) * peskin(ry);
-            if (W == (T)0) continue;
+            if (fabs(rx) < (T)2 && fabs(ry) < (T)2) W = peskin(rx) * peskin(ry);   // exact in T
+            di = fxi ? (T)((float)i - d.xiGf[0]) : (T)(i - d.xiG[0]);
+            dj = fxi ? (T)((float)j - d.xiGf[1]) : (T)(j - d.xiG[1]);
+        }
+        const unsigned acc = __ballot_sync(0xffffffffu, W != (T)0);
+        const int pos = cnt + __popc(acc & ((1u << lane) - 1u));
+        if (W != (T)0 && pos < kMaxTaps) {
+            tidx[pos] = k;
+            tw[pos] = W;
+            s_k[wid][pos] = k;
+            s_w[wid][pos] = W;
+        }
+        for (unsigned r = acc; r != 0u; r &= r - 1u) {   // warp-uniform: taps in window order
             if (cnt == kMaxTaps) {
-                atomicOr(ts.err, 1);
+                over = true;
                 break;
             }
-            tidx[cnt] = (int)k;
-            tw[cnt] = W;
+            const int src = __ffs(r) - 1;
+            const T Ws = __shfl_sync(0xffffffffu, W, src);
+            m0 += Ws;
+            m1x += Ws * __shfl_sync(0xffffffffu, di, src);
+            m1y += Ws * __shfl_sync(0xffffffffu, dj, src);
             ++cnt;
-            m0 += W;
-            m1x += W * (T)(i - d.xiG[0]);
-            m1y += W * (T)(j - d.xiG[1]);
         }
-    ts.tap_cnt[col] = cnt;
-    T* cm = (T*)ts.col_m + 3 * col;
-    cm[0] = m0;
-    cm[1] = m1x;
-    cm[2] = m1y;
+    }
+    if (lane == 0) {
+        if (over) atomicOr(ts.err, 1);
+        ts.tap_cnt[col] = cnt;
+        T* cm = (T*)ts.col_m + 3 * col;
+        cm[0] = m0;
+        cm[1] = m1x;
+        cm[2] = m1y;
+    }
+    __syncwarp();
+    const int lz = d.L[2];
+    const T* sw = s_w[wid];
+    const int* sk = s_k[wid];
+    for (int z = lane; z < lz; z += 32) {
+        T a = (T)0;
+#pragma unroll 4
+        for (int e = 0; e < cnt; ++e) a += sw[e] * kref_t[(long long)sk[e] * lz + z];
+        k2[col * lz + z] = a;
+    }
 }
 
-// Stage 1: K2[col][zeta] = sum over the column's taps of W_xy * kappa_ref(zeta, tap): the x-y
-// transfer of every design plane, lanes running over zeta (coalesced in kref_t).
-template <class T>
-__global__ void k_col_planes(Design d, Geom g, TransferScratch ts, const T* __restrict__ kref_t,
-                             T* __restrict__ k2) {
-    const int zeta = blockIdx.x * blockDim.x + threadIdx.x;
-    const long long col = blockIdx.y * (long long)blockDim.y + threadIdx.y;
-    const long long ncols = (long long)g.bn[0] * g.bn[1];
-    if (zeta >= d.L[2] || col >= ncols) return;
-    const int cnt = ts.tap_cnt[col];
-    const int* tidx = ts.tap_idx + col * kMaxTaps;
-    const T* tw = (const T*)ts.tap_w + col * kMaxTaps;
-    T acc = (T)0;
-    for (int e = 0; e < cnt; ++e) acc += tw[e] * kref_t[(long long)tidx[e] * d.L[2] + zeta];
-    k2[col * d.L[2] + zeta] = acc;
-}
-
-// Stage 2: kappa = sum over the z taps of w_z K2 and u_S = m_z (omega R'(theta) m1 + u_G m0)
+// The fill: kappa = sum over the z taps of w_z K2 and u_S = m_z (omega R'(theta) m1 + u_G m0)
 // on every node of the footprint box (u_ref is affine in xi, Eq. rigid_body_velocity).  A block
 // covers 32 box columns x 8 box planes; the K2 values those planes need (a window of at most
 // 11 consecutive zeta, the z map being a translation) are staged in shared memory with
@@ -383,13 +414,8 @@ void launch_transfer(const Design& d, const Geom& g, const Motion& m, TransferSc
                      const T* kref_t, T* k2, V4<T>* kus, cudaStream_t st) {
     if (d.nd == 0 || g.boxN == 0) return;
     const long long ncols = (long long)g.bn[0] * g.bn[1];
-    k_tap_lists<T><<<(unsigned)((ncols + kSmallThreads - 1) / kSmallThreads), kSmallThreads, 0,
-                     st>>>(d, g, m, ts);
-    const int lanes = d.L[2] >= 32 ? 32 : (d.L[2] >= 8 ? 8 : 1);
-    const dim3 blk(lanes, kThreads / lanes);
-    const dim3 grd((unsigned)((d.L[2] + lanes - 1) / lanes),
-                   (unsigned)((ncols + blk.y - 1) / blk.y));
-    k_col_planes<T><<<grd, blk, 0, st>>>(d, g, ts, kref_t, k2);
+    k_tap_lists<T><<<(unsigned)((ncols + kTapWarps - 1) / kTapWarps), kThreads, 0, st>>>(
+        d, g, m, ts, kref_t, k2);
     const dim3 fgrd((unsigned)((ncols + kFillCols - 1) / kFillCols),
                     (unsigned)((g.bn[2] + kFillPlanes - 1) / kFillPlanes));
     k_fill<T><<<fgrd, kFillCols * kFillPlanes, 0, st>>>(d, g, m, ts, k2, kus);
