@@ -89,7 +89,7 @@ lks_status batch_prepare(lks_batch* b, int n_steps) {
             }
             BCU(launch_set_int(b->nbase, 0, b->st));
             BCU(launch_t_design_pos(b->plan, 1, b->st));
-            BCU(launch_t_transfer2d(b->plan, 1, b->st));
+            BCU(launch_t_transfer2d(b->plan, 1, -1, b->st));
             for (lks_ctx* c : b->cs) {
                 BCU(cudaMemsetAsync(c->lam[0], 0, c->snap_bytes, b->st));
                 BCU(cudaMemsetAsync(c->lam[1], 0, c->snap_bytes, b->st));
@@ -102,9 +102,9 @@ lks_status batch_prepare(lks_batch* b, int n_steps) {
             for (int k = 0; k < kTileCfgs; ++k) b->tune_ms[w][k] = -1.f;
             for (int k = 0; k < ncfg; ++k) {
                 auto run = [&]() -> cudaError_t {
-                    return w == 0 ? launch_t_step2d(b->plan, k, BUF_INIT, BUF_S1, b->st)
+                    return w == 0 ? launch_t_step2d(b->plan, k, BUF_INIT, BUF_S1, -1, b->st)
                                   : launch_t_adj2d(b->plan, k, 1, BUF_LAM0, BUF_LAM1, BUF_INIT,
-                                                   BUF_INIT, b->st);
+                                                   BUF_INIT, -1, b->st);
                 };
                 cudaError_t e = cudaSuccess;
                 for (int r = 0; r < 2 && e == cudaSuccess; ++r) e = run();

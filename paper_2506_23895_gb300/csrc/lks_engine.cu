@@ -158,6 +158,7 @@ double count_target(const lks_config* c) {
 struct Layout {
     size_t off[96];
     size_t total;
+    int ktape_slots;   // slots of the transfer tape (0: none)
     int pool_slots;
     size_t snap;
 };
@@ -171,7 +172,7 @@ enum {
     // the second transfer buffer set (3D): same sizes as L_KUS, L_K2, L_CBASE, ...
     L_KUS2, L_K22, L_CBASE2, L_CFRAC2, L_CSC2, L_ZTI2, L_ZTW2, L_TCNT2, L_TIDX2, L_TW2, L_CM2,
     L_DZB2, L_DZF2, L_GBASE2, L_GFRAC2, L_GCNT2, L_GIDX2, L_E2,
-    L_POOL,
+    L_KTAPE, L_POOL,
     L_COUNT
 };
 static_assert(L_COUNT <= 96, "Layout::off holds 96 regions");
@@ -255,6 +256,18 @@ Layout make_layout(const lks_config* cfg) {
                                L_TIDX, L_TW, L_CM, L_DZB, L_DZF, L_GBASE, L_GFRAC, L_GCNT, L_GIDX};
         for (int i = 0; i < 17; ++i) sz[L_KUS2 + i] = two ? sz[first[i]] : 0;
         sz[L_E2] = two ? sz[L_E] : 0;
+    }
+    // FP32 2D contexts with a design keep the transfer (kappa, u_S on the footprint box) of each
+    // taped step, so that the adjoint of the step reads it instead of transferring again; a tape
+    // of up to max(ceil(sqrt(N)) + 2, 64) steps (the checkpointed schedules' tape length, and
+    // short full-history runs), each slot sized for the whole grid (the box is known only once
+    // the motion is set)
+    {
+        const bool t2d = cfg->precision == LKS_FP32 && dim == 2 && nd > 0 &&
+                         !(cfg->flags & (LKS_FLAG_PLAIN_KERNELS | LKS_FLAG_PAPER_ALKS));
+        const long long kt = std::max((long long)std::ceil(std::sqrt((double)N)) + 2, 64LL);
+        L.ktape_slots = t2d ? (int)std::min(P, kt) : 0;
+        sz[L_KTAPE] = (size_t)L.ktape_slots * state;
     }
     sz[L_POOL] = (size_t)P * state;
     size_t off = 0;
@@ -403,6 +416,8 @@ lks_status lks_create(const lks_config* cfg, void* workspace, size_t ws_bytes, l
     c->snap_bytes = L.snap;
     c->fused2d = (c->prec == LKS_FP32) && g.dim == 2 &&
                  !(cfg->flags & (LKS_FLAG_PLAIN_KERNELS | LKS_FLAG_PAPER_ALKS));
+    c->ktape_slots = c->fused2d ? L.ktape_slots : 0;
+    c->ktape = c->ktape_slots > 0 ? (void*)(w + L.off[L_KTAPE]) : nullptr;
     c->dmotion = (Motion*)(w + L.off[L_MOTION]);
     c->dbufs = (void**)(w + L.off[L_BUFS]);
     c->dinst = (Inst*)(w + L.off[L_INST]);

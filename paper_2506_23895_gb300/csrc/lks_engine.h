@@ -78,6 +78,8 @@ struct lks_ctx {
     char* pool;
     int pool_slots;
     size_t snap_bytes;
+    void* ktape = nullptr;       // transfer tape of the 2D table path (ktape_slots box records)
+    int ktape_slots = 0;
     // host state
     std::vector<double> motion;
     bool have_design = false, have_motion = false, fwd_valid = false;

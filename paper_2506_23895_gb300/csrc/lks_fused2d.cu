@@ -47,14 +47,26 @@ __device__ __forceinline__ int step_of(const Plan& p, int noff) { return __ldg(p
 // geometry from shared memory, which their global stores cannot alias, instead of reloading it
 // from global memory after every store.  Called by all threads; ends with a barrier when it
 // copies.
-__device__ __forceinline__ void stage_inst(const Plan& p, int i, int& cur, Inst& sI) {
+// kslot >= 0 points the staged record's kus at slot kslot of the instance's transfer tape.
+__device__ __forceinline__ void stage_inst(const Plan& p, int i, int& cur, Inst& sI,
+                                          int kslot = -1) {
     if (i == cur) return;
     __syncthreads();
     const int* src = reinterpret_cast<const int*>(p.tab + i);
     int* dst = reinterpret_cast<int*>(&sI);
     for (int k = threadIdx.x; k < (int)(sizeof(Inst) / 4); k += blockDim.x) dst[k] = __ldg(src + k);
     __syncthreads();
+    if (kslot >= 0) {
+        if (threadIdx.x == 0) sI.kus = sI.kus_tape + (long long)kslot * sI.g.boxN;
+        __syncthreads();
+    }
     cur = i;
+}
+
+// kappa, u_S records of a launch: the box buffer or slot kslot of the transfer tape (a taped
+// forward step writes its transfer there; the adjoint of that step reads it back).
+__device__ __forceinline__ V4<float>* kus_slot(const Inst& I, int kslot) {
+    return kslot < 0 ? I.kus : I.kus_tape + (long long)kslot * I.g.boxN;
 }
 
 // ---------------------------------------------------------------- element-wise phases
@@ -77,7 +89,7 @@ __global__ void __launch_bounds__(NT) k_t_design_pos(Plan p, int noff) {
 constexpr int kTrWin = 32;   // staged window side (design nodes)
 static_assert(kBoxTile * kBoxTile == NT, "one box tile per block of NT threads");
 
-__global__ void __launch_bounds__(NT) k_t_transfer2d(Plan p, int noff) {
+__global__ void __launch_bounds__(NT) k_t_transfer2d(Plan p, int noff, int kslot) {
     __shared__ int2 sb[kTrWin * kTrWin];
     __shared__ float4 ssc[kTrWin * kTrWin];
     __shared__ float skr[kTrWin * kTrWin];
@@ -137,7 +149,7 @@ __global__ void __launch_bounds__(NT) k_t_transfer2d(Plan p, int noff) {
         if (!node) continue;
         const long long bi = (long long)by * g.bn[0] + bx;
         if (!staged) {   // a window wider than the staging area: the global-memory path
-            transfer2d_node(d, g, m, I.ts, I.kref, I.kus, bi);
+            transfer2d_node(d, g, m, I.ts, I.kref, kus_slot(I, kslot), bi);
             continue;
         }
         const float gx0 = d.xiGf[0], gy0 = d.xiGf[1];
@@ -161,7 +173,7 @@ __global__ void __launch_bounds__(NT) k_t_transfer2d(Plan p, int noff) {
         o.x = (-s * m1x - c * m1y) * om + m.ugf[0] * m0;
         o.y = (c * m1x - s * m1y) * om + m.ugf[1] * m0;
         o.z = 0.f;
-        I.kus[bi] = o;
+        kus_slot(I, kslot)[bi] = o;
     }
 }
 
@@ -171,50 +183,6 @@ __global__ void __launch_bounds__(kObjThreads) k_t_objective(Plan p, int noff, i
         const Inst& I = p.tab[i];
         if (n < I.win_begin || n > I.win_end) continue;   // uniform over the block
         objective_block<float>(I.g, (const V4<float>*)I.bufs[src], I.jstep + n);
-    }
-}
-
-// Interior node next to the boundary for shell index t of a 2D grid: the layers x = 1,
-// x = n0-2, y = 1, y = n1-2 in that order, each node taken by the first layer holding it.
-__device__ __forceinline__ bool shell2d(const Geom& g, int t, int& x, int& y) {
-    const int n0 = g.n[0], n1 = g.n[1];
-    int layer;
-    if (t < n1) layer = 0;
-    else if (t < 2 * n1) { layer = 1; t -= n1; }
-    else if (t < 2 * n1 + n0) { layer = 2; t -= 2 * n1; }
-    else if (t < 2 * n1 + 2 * n0) { layer = 3; t -= 2 * n1 + n0; }
-    else return false;
-    const int a = layer / 2;
-    if (g.periodic[a]) return false;
-    if (a == 0) {
-        x = (layer & 1) ? n0 - 2 : 1;
-        y = t;
-    } else {
-        y = (layer & 1) ? n1 - 2 : 1;
-        x = t;
-        if (!g.periodic[0] && (x == 1 || x == n0 - 2)) return false;   // taken by an x layer
-    }
-    if (layer == 1 && x == 1) return false;   // n0 == 3: x = 1 is also the low layer
-    if (layer == 3 && y == 1) return false;
-    return !is_boundary(g, x, y, 0);
-}
-
-__global__ void __launch_bounds__(NT) k_t_bcT2d(Plan p, int noff, int lam) {
-    const int* pre = p.pre + U_SHELL * (p.count + 1);
-    const int n = step_of(p, noff);
-    for (int u = blockIdx.x; u < p.total[U_SHELL]; u += gridDim.x) {
-        const int i = find_inst(pre, p.count, u);
-        const Inst& I = p.tab[i];
-        const int t = (u - pre[i]) * kUnitThreads + threadIdx.x;
-        int x, y;
-        if (!shell2d(I.g, t, x, y)) continue;
-        ObjAdd<float> h;   // the objective source of the instance record (formed on the host)
-        h.on = n >= I.win_begin && n <= I.win_end;
-        h.r = I.src_r;
-        h.x = I.src_x;
-        h.y = I.src_y;
-        h.z = 0.f;
-        bcT_node<float>(I.g, (V4<float>*)I.bufs[lam], h, x, y, 0);
     }
 }
 
@@ -467,7 +435,7 @@ __device__ __forceinline__ void step_tile(const Inst& I, int x0, int y0, int src
 
 template <int TX, int TY>
 __global__ void __launch_bounds__(NT) k_t_step2d(Plan p, const int* __restrict__ pre, int total,
-                                                 int src, int dst) {
+                                                 int src, int dst, int kslot) {
     constexpr int HX = TX + 4, HY = TY + 4;
     extern __shared__ float4 smem[];
     float4* S = smem;                          // HY x HX state records
@@ -476,7 +444,7 @@ __global__ void __launch_bounds__(NT) k_t_step2d(Plan p, const int* __restrict__
     int cur = -1;
     for (int u = blockIdx.x; u < total; u += gridDim.x) {
         const int i = find_inst(pre, p.count, u);
-        stage_inst(p, i, cur, sI);
+        stage_inst(p, i, cur, sI, kslot);
         int x0, y0;
         tile_xy<TX, TY>(sI.g, u - pre[i], x0, y0);
         if (interior_tile<TX, TY>(sI.g, x0, y0))
@@ -510,7 +478,7 @@ __device__ __forceinline__ void cp_async_wait1() {
 // the tile kernel, bit for bit.
 template <int NTH, int YC>
 __global__ void __launch_bounds__(NTH) k_t_step2d_rows(Plan p, const int* __restrict__ pre,
-                                                        int total, int src, int dst) {
+                                                        int total, int src, int dst, int kslot) {
     // ring of state rows: 8 slots (6 in use: two rows below the f^eq row to three above), so
     // that the slot of a row is its index & 7, negative indices included
     constexpr int SW = NTH - 2, RW = NTH + 2, NR = 8;
@@ -521,7 +489,7 @@ __global__ void __launch_bounds__(NTH) k_t_step2d_rows(Plan p, const int* __rest
     const int t = threadIdx.x;
     for (int u = blockIdx.x; u < total; u += gridDim.x) {
         const int i = find_inst(pre, p.count, u);
-        stage_inst(p, i, cur, sI);
+        stage_inst(p, i, cur, sI, kslot);
         const Geom& g = sI.g;
         const int n0 = g.n[0], n1 = g.n[1], p0 = g.periodic[0], p1 = g.periodic[1];
         const int ns = tile_count(n0, SW, p0);
@@ -658,6 +626,19 @@ __device__ __forceinline__ bool in_target2(const Geom& g, const ObjSrc& o, int x
     return true;
 }
 
+// lambda at a node next to a face plus the transpose of the boundary copies it sources (out of
+// line: few nodes take it, and the tile loop keeps its registers).
+__device__ __noinline__ float4 bcT_fold(const Geom& g, const float4* lam, const ObjAdd<float>& h,
+                                        int x, int y, float4 lv) {
+    V4<float> acc;
+    acc.r = lv.x;
+    acc.x = lv.y;
+    acc.y = lv.z;
+    acc.z = lv.w;
+    bcT_gather<float>(g, (const V4<float>*)lam, h, x, y, 0, acc);
+    return make_float4(acc.r, acc.x, acc.y, acc.z);
+}
+
 // One tile of the adjoint step.  EDGE: the general path (wraps, grid edges, boundary nodes,
 // one-sided boundary rows of the transposed gradient).
 template <int TX, int TY, bool EDGE>
@@ -673,6 +654,16 @@ __device__ __forceinline__ void adj_tile(const Inst& I, int x0, int y0, const Ob
     // tiles whose halo misses the footprint box (the target) skip those per-node tests
     const bool tbox = EDGE || meets_box(g, x0 - 2, x0 + TX + 1, y0 - 2, y0 + TY + 1);
     const bool ttgt = os.on && (EDGE || meets_target(g, x0 - 2, x0 + TX + 1, y0 - 2, y0 + TY + 1));
+    // tiles whose halo holds a node next to a face: such a node first collects the transpose of
+    // the boundary copies it sources (Eqs. bc_rho, bc_u; boundary nodes are read only)
+    const bool tbc = EDGE || x0 - 2 <= 1 || x0 + TX + 1 >= n0 - 2 || y0 - 2 <= 1 ||
+                     y0 + TY + 1 >= n1 - 2;
+    ObjAdd<float> bsrc;   // the objective source of the boundary nodes inside the target
+    bsrc.on = os.on;
+    bsrc.r = os.r;
+    bsrc.x = os.x;
+    bsrc.y = os.y;
+    bsrc.z = 0.f;
     // 1. mu on the tile and a two-cell halo; e on the tile's own box nodes
     for (int k = threadIdx.x; k < HX * HY; k += NT) {
         const int ly = k / HX, lx = k - ly * HX;
@@ -684,7 +675,8 @@ __device__ __forceinline__ void adj_tile(const Inst& I, int x0, int y0, const Ob
         float4 m = make_float4(0.f, 0.f, 0.f, 0.f);
         if (!EDGE || (gx >= 0 && gx < n0 && gy >= 0 && gy < n1 && !is_boundary(g, gx, gy, 0))) {
             const long long gm = (long long)gy * n0 + gx;
-            const float4 lv = __ldg(lam + gm);
+            float4 lv = __ldg(lam + gm);
+            if (tbc && sources_boundary(g, gx, gy, 0)) lv = bcT_fold(g, lam, bsrc, gx, gy, lv);
             float lr = lv.x, lux = lv.y, luy = lv.z;
             if (ttgt && in_target2(g, os, gx, gy)) {
                 lr += os.r;
@@ -798,7 +790,7 @@ __device__ __forceinline__ void adj_tile(const Inst& I, int x0, int y0, const Ob
 template <int TX, int TY>
 __global__ void __launch_bounds__(NT) k_t_adj2d(Plan p, const int* __restrict__ pre, int total,
                                                 int noff, int lam_in, int lam_out, int sn,
-                                                int sp) {
+                                                int sp, int kslot) {
     constexpr int HX = TX + 4, HY = TY + 4;
     extern __shared__ float4 smem[];
     float4* M = smem;                          // HY x HX: mu (rho, x, y, -)
@@ -810,7 +802,7 @@ __global__ void __launch_bounds__(NT) k_t_adj2d(Plan p, const int* __restrict__ 
     for (int u = blockIdx.x; u < total; u += gridDim.x) {
         const int i = find_inst(pre, p.count, u);
         if (i != cur) {
-            stage_inst(p, i, cur, sI);
+            stage_inst(p, i, cur, sI, kslot);
             os = obj_src(sI, n);
         }
         int x0, y0;
@@ -837,11 +829,11 @@ int occ_rows() {
 }
 
 template <int C>
-cudaError_t rows_cfg(const Plan& p, int src, int dst, cudaStream_t st) {
+cudaError_t rows_cfg(const Plan& p, int src, int dst, int kslot, cudaStream_t st) {
     const int unit = U_TILE0 + C;
     if (p.total[unit] == 0) return cudaSuccess;
     k_t_step2d_rows<RowCfg<C>::NTH, RowCfg<C>::YC><<<p.grid[unit], RowCfg<C>::NTH, 0, st>>>(
-        p, p.pre + unit * (p.count + 1), p.total[unit], src, dst);
+        p, p.pre + unit * (p.count + 1), p.total[unit], src, dst, kslot);
     return cudaGetLastError();
 }
 
@@ -884,20 +876,21 @@ int cap_grid(long long units, int per_sm) {
 }
 
 template <int C>
-cudaError_t step_cfg(const Plan& p, int src, int dst, cudaStream_t st) {
+cudaError_t step_cfg(const Plan& p, int src, int dst, int kslot, cudaStream_t st) {
     const int unit = U_TILE0 + C;
     if (p.total[unit] == 0) return cudaSuccess;
     k_t_step2d<Cfg<C>::TX, Cfg<C>::TY><<<p.grid[unit], NT, Cfg<C>::step_smem, st>>>(
-        p, p.pre + unit * (p.count + 1), p.total[unit], src, dst);
+        p, p.pre + unit * (p.count + 1), p.total[unit], src, dst, kslot);
     return cudaGetLastError();
 }
 
 template <int C>
-cudaError_t adj_cfg(const Plan& p, int noff, int li, int lo, int sn, int sp, cudaStream_t st) {
+cudaError_t adj_cfg(const Plan& p, int noff, int li, int lo, int sn, int sp, int kslot,
+                    cudaStream_t st) {
     const int unit = U_TILE0 + C;
     if (p.total[unit] == 0) return cudaSuccess;
     k_t_adj2d<Cfg<C>::TX, Cfg<C>::TY><<<p.grid[U_COUNT + C], NT, Cfg<C>::adj_smem, st>>>(
-        p, p.pre + unit * (p.count + 1), p.total[unit], noff, li, lo, sn, sp);
+        p, p.pre + unit * (p.count + 1), p.total[unit], noff, li, lo, sn, sp, kslot);
     return cudaGetLastError();
 }
 
@@ -909,8 +902,6 @@ void plan_grids(Plan& p) {
     p.grid[U_BOX] = cap_grid(p.total[U_BOX], b);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_t_design_pos, NT, 0);
     p.grid[U_DCOL] = cap_grid(p.total[U_DCOL], b);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_t_bcT2d, NT, 0);
-    p.grid[U_SHELL] = cap_grid(p.total[U_SHELL], b);
     p.grid[U_INST] = std::max(1, p.count);
     const int os[kTileCfgs] = {occ_step<0>(), occ_step<1>(), occ_step<2>(), occ_step<3>(),
                                occ_step<4>(), occ_rows<5>(),  occ_rows<6>(),  occ_rows<7>(),
@@ -928,23 +919,24 @@ cudaError_t launch_t_design_pos(const Plan& p, int noff, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_t_transfer2d(const Plan& p, int noff, cudaStream_t st) {
+cudaError_t launch_t_transfer2d(const Plan& p, int noff, int kslot, cudaStream_t st) {
     if (p.total[U_BOX] == 0) return cudaSuccess;
-    k_t_transfer2d<<<p.grid[U_BOX], NT, 0, st>>>(p, noff);
+    k_t_transfer2d<<<p.grid[U_BOX], NT, 0, st>>>(p, noff, kslot);
     return cudaGetLastError();
 }
 
-cudaError_t launch_t_step2d(const Plan& p, int cfg, int src, int dst, cudaStream_t st) {
+cudaError_t launch_t_step2d(const Plan& p, int cfg, int src, int dst, int kslot,
+                            cudaStream_t st) {
     switch (cfg) {
-        case 0: return step_cfg<0>(p, src, dst, st);
-        case 1: return step_cfg<1>(p, src, dst, st);
-        case 2: return step_cfg<2>(p, src, dst, st);
-        case 3: return step_cfg<3>(p, src, dst, st);
-        case 4: return step_cfg<4>(p, src, dst, st);
-        case 5: return rows_cfg<5>(p, src, dst, st);
-        case 6: return rows_cfg<6>(p, src, dst, st);
-        case 7: return rows_cfg<7>(p, src, dst, st);
-        case 8: return rows_cfg<8>(p, src, dst, st);
+        case 0: return step_cfg<0>(p, src, dst, kslot, st);
+        case 1: return step_cfg<1>(p, src, dst, kslot, st);
+        case 2: return step_cfg<2>(p, src, dst, kslot, st);
+        case 3: return step_cfg<3>(p, src, dst, kslot, st);
+        case 4: return step_cfg<4>(p, src, dst, kslot, st);
+        case 5: return rows_cfg<5>(p, src, dst, kslot, st);
+        case 6: return rows_cfg<6>(p, src, dst, kslot, st);
+        case 7: return rows_cfg<7>(p, src, dst, kslot, st);
+        case 8: return rows_cfg<8>(p, src, dst, kslot, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -954,20 +946,14 @@ cudaError_t launch_t_objective(const Plan& p, int noff, int src, cudaStream_t st
     return cudaGetLastError();
 }
 
-cudaError_t launch_t_bcT2d(const Plan& p, int noff, int lam, cudaStream_t st) {
-    if (p.total[U_SHELL] == 0) return cudaSuccess;
-    k_t_bcT2d<<<p.grid[U_SHELL], NT, 0, st>>>(p, noff, lam);
-    return cudaGetLastError();
-}
-
 cudaError_t launch_t_adj2d(const Plan& p, int cfg, int noff, int lam_in, int lam_out, int sn,
-                           int sp, cudaStream_t st) {
+                           int sp, int kslot, cudaStream_t st) {
     switch (cfg) {
-        case 0: return adj_cfg<0>(p, noff, lam_in, lam_out, sn, sp, st);
-        case 1: return adj_cfg<1>(p, noff, lam_in, lam_out, sn, sp, st);
-        case 2: return adj_cfg<2>(p, noff, lam_in, lam_out, sn, sp, st);
-        case 3: return adj_cfg<3>(p, noff, lam_in, lam_out, sn, sp, st);
-        case 4: return adj_cfg<4>(p, noff, lam_in, lam_out, sn, sp, st);
+        case 0: return adj_cfg<0>(p, noff, lam_in, lam_out, sn, sp, kslot, st);
+        case 1: return adj_cfg<1>(p, noff, lam_in, lam_out, sn, sp, kslot, st);
+        case 2: return adj_cfg<2>(p, noff, lam_in, lam_out, sn, sp, kslot, st);
+        case 3: return adj_cfg<3>(p, noff, lam_in, lam_out, sn, sp, kslot, st);
+        case 4: return adj_cfg<4>(p, noff, lam_in, lam_out, sn, sp, kslot, st);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -178,7 +178,7 @@ lks_status transfer_at(lks_ctx* c, int n) {
     if (c->fused2d) {
         CU(launch_set_int(c->nbase, n, c->st));
         CU(launch_t_design_pos(c->plan, 0, c->st));
-        CU(launch_t_transfer2d(c->plan, 0, c->st));
+        CU(launch_t_transfer2d(c->plan, 0, -1, c->st));
         c->stats[4] += 3;
         return LKS_OK;
     }
@@ -395,14 +395,24 @@ Group self_group(lks_ctx*& c) {
     return G;
 }
 
-// Table-path launch sequences of one forward / adjoint step at offset k from *nbase.
-cudaError_t table_fwd_launches(const Group& G, int k, int src, int dst, bool with_obj,
+// Every context of the group keeps the transfers of a whole tape segment (2D table path).
+bool tape_transfers(const Group& G) {
+    if (!G.table) return false;
+    for (int i = 0; i < G.count; ++i)
+        if (!G.cs[i]->ktape || G.cs[i]->K + 1 > G.cs[i]->ktape_slots) return false;
+    return true;
+}
+
+// Table-path launch sequences of one forward / adjoint step at offset k from *nbase.  kslot >= 0:
+// the step's transfer goes to (forward) or comes from (adjoint) slot kslot of the transfer tape.
+cudaError_t table_fwd_launches(const Group& G, int k, int src, int dst, bool with_obj, int kslot,
                                lks_ctx* timed, int n, int& nl) {
     cudaError_t e;
     if ((e = launch_t_design_pos(*G.plan, k, G.st)) != cudaSuccess) return e;
-    if ((e = launch_t_transfer2d(*G.plan, k, G.st)) != cudaSuccess) return e;
+    if ((e = launch_t_transfer2d(*G.plan, k, kslot, G.st)) != cudaSuccess) return e;
     const bool tm = timed && timing_begin(timed, n, 0);
-    if ((e = launch_t_step2d(*G.plan, G.tile_fwd, src, dst, G.st)) != cudaSuccess) return e;
+    if ((e = launch_t_step2d(*G.plan, G.tile_fwd, src, dst, kslot, G.st)) != cudaSuccess)
+        return e;
     if (tm) timing_end(timed, 0);
     nl += 3;
     if (with_obj) {
@@ -412,19 +422,23 @@ cudaError_t table_fwd_launches(const Group& G, int k, int src, int dst, bool wit
     return cudaSuccess;
 }
 
+// The adjoint step gathers the transpose of the boundary copies itself; the design positions
+// of the step are formed again for the sensitivity gather.
 cudaError_t table_adj_launches(const Group& G, int k, int lam_in, int lam_out, int sn, int sp,
-                               lks_ctx* timed, int n, int& nl) {
+                               int kslot, lks_ctx* timed, int n, int& nl) {
     cudaError_t e;
     if ((e = launch_t_design_pos(*G.plan, k, G.st)) != cudaSuccess) return e;
-    if ((e = launch_t_transfer2d(*G.plan, k, G.st)) != cudaSuccess) return e;
+    if (kslot < 0) {
+        if ((e = launch_t_transfer2d(*G.plan, k, -1, G.st)) != cudaSuccess) return e;
+        ++nl;
+    }
     const bool tm = timed && timing_begin(timed, n, 1);
-    if ((e = launch_t_bcT2d(*G.plan, k, lam_in, G.st)) != cudaSuccess) return e;
-    if ((e = launch_t_adj2d(*G.plan, G.tile_adj, k, lam_in, lam_out, sn, sp, G.st)) !=
+    if ((e = launch_t_adj2d(*G.plan, G.tile_adj, k, lam_in, lam_out, sn, sp, kslot, G.st)) !=
         cudaSuccess)
         return e;
     if (tm) timing_end(timed, 1);
     if ((e = launch_t_sens(*G.plan, G.st)) != cudaSuccess) return e;
-    nl += 5;
+    nl += 3;
     return cudaSuccess;
 }
 
@@ -489,6 +503,8 @@ lks_status run_steps(Group& G, int from_level, int to_level, bool with_obj, int 
         for (int i = 0; i < G.count && with_obj; ++i)
             obj = obj || (G.cs[i]->cfg.win_begin <= to_level &&
                           G.cs[i]->cfg.win_end > from_level);
+        // a taped step leaves its transfer in the transfer tape slot of its level
+        const bool kt = tape_seg >= 0 && tape_transfers(G);
         auto fn = [&](int k, int& nl, bool direct) -> cudaError_t {
             int src, dst;
             if (tape_seg >= 0) {
@@ -499,11 +515,11 @@ lks_status run_steps(Group& G, int from_level, int to_level, bool with_obj, int 
                 src = BUF_S0 + w;
                 dst = BUF_S0 + 1 - w;
             }
-            return table_fwd_launches(G, k, src, dst, obj,
+            return table_fwd_launches(G, k, src, dst, obj, kt ? toff + k : -1,
                                       (direct && G.count == 1) ? c0 : nullptr, from_level + k, nl);
         };
         const auto key = std::make_tuple(tape_seg >= 0 ? 1 : 0, obj ? 1 : 0, len,
-                                         tape_seg >= 0 ? toff : w0, G.tile_fwd, 0);
+                                         tape_seg >= 0 ? toff : w0, G.tile_fwd, kt ? 1 : 0);
         lks_status s = table_run(G, key, from_level, len, fn);
         if (s != LKS_OK) return s;
         for (int i = 0; i < G.count; ++i) {
@@ -610,14 +626,16 @@ lks_status exec_adj(Group& G, int seg) {
         return LKS_OK;
     }
     const int par0 = c0->lam_par;
+    // the tape of this segment (levels 0..len) holds the transfer of step a + kk in slot kk
+    const bool kt = tape_transfers(G);
     auto fn = [&](int k, int& nl, bool direct) -> cudaError_t {
         const int kk = len - k + 1;                 // step n = a + kk, from b down to a + 1
         const int par = par0 ^ ((k - 1) & 1);
         return table_adj_launches(G, kk, BUF_LAM0 + par, BUF_LAM0 + 1 - par, BUF_POOL + kk,
-                                  BUF_POOL + kk - 1, (direct && G.count == 1) ? c0 : nullptr,
-                                  a + kk, nl);
+                                  BUF_POOL + kk - 1, kt ? kk : -1,
+                                  (direct && G.count == 1) ? c0 : nullptr, a + kk, nl);
     };
-    const auto key = std::make_tuple(2, 0, len, par0, 0, G.tile_adj);
+    const auto key = std::make_tuple(2, kt ? 1 : 0, len, par0, 0, G.tile_adj);
     lks_status s = table_run(G, key, a, len, fn);
     if (s != LKS_OK) return s;
     for (int i = 0; i < G.count; ++i) G.cs[i]->lam_par = par0 ^ (len & 1);
@@ -765,6 +783,7 @@ Inst make_inst(const lks_ctx* c) {
     I.kref = (const float*)c->kref;
     I.kprime = (const float*)c->kprime;
     I.kus = (V4<float>*)c->kus;
+    I.kus_tape = (V4<float>*)c->ktape;
     I.e = (float*)c->e;
     I.gacc = c->gacc;
     I.jstep = c->jstep;
@@ -792,7 +811,6 @@ void inst_units(const lks_ctx* c, int out[U_COUNT]) {
     // nodes a tile reads in shared memory)
     out[U_BOX] = body ? ((g.bn[0] + kBoxTile - 1) / kBoxTile) * ((g.bn[1] + kBoxTile - 1) / kBoxTile)
                       : 0;
-    out[U_SHELL] = (2 * (g.n[0] + g.n[1]) + kUnitThreads - 1) / kUnitThreads;
     out[U_INST] = 1;
     for (int k = 0; k < kTileCfgs; ++k)
         out[U_TILE0 + k] = tile_count(g.n[0], tile_tx(k), g.periodic[0]) *

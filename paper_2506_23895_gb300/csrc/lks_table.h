@@ -22,6 +22,7 @@ struct Inst {
     const float* kref;        // kappa_ref per design node
     const float* kprime;      // d kappa_ref / d gamma
     V4<float>* kus;           // kappa, u_S on the footprint box
+    V4<float>* kus_tape;      // kappa, u_S of each taped step (slots of boxN records) or null
     float* e;                 // dJ/dkappa density on the box
     double* gacc;             // dJ/dgamma accumulator
     double* jstep;            // objective per step
@@ -46,11 +47,11 @@ __host__ __device__ constexpr int tile_ty(int k) {
            (k == 7 ? 128 : 64)))));
 }
 
-// Work-unit kinds: design columns in blocks of kUnitThreads, footprint-box tiles, boundary-shell
-// nodes in blocks, one unit per instance (objective), tiles of each shape.
+// Work-unit kinds: design columns in blocks of kUnitThreads, footprint-box tiles, one unit per
+// instance (objective), tiles of each shape.
 constexpr int kUnitThreads = 256;
 constexpr int kBoxTile = 16;   // box tiles of the 2D transfer: kBoxTile^2 = kUnitThreads nodes
-enum { U_DCOL = 0, U_BOX, U_SHELL, U_INST, U_TILE0, U_COUNT = U_TILE0 + kTileCfgs };
+enum { U_DCOL = 0, U_BOX, U_INST, U_TILE0, U_COUNT = U_TILE0 + kTileCfgs };
 
 struct Plan {
     const Inst* tab;          // device
@@ -77,14 +78,15 @@ __host__ __device__ inline int tile_count(int n, int T, int periodic) {
 // Host: persistent grid sizes for every kernel of a plan (occupancy x SMs, capped by work).
 void plan_grids(Plan& p);
 
-// Launchers (stream st; noff = step offset from *nbase; buffer arguments are BUF_* indices).
+// Launchers (stream st; noff = step offset from *nbase; buffer arguments are BUF_* indices;
+// kslot: the kappa, u_S records a launch writes (transfer) or reads (step, adjoint): -1 for the
+// box buffer kus, else slot kslot of kus_tape).
 cudaError_t launch_t_design_pos(const Plan& p, int noff, cudaStream_t st);
-cudaError_t launch_t_transfer2d(const Plan& p, int noff, cudaStream_t st);
-cudaError_t launch_t_step2d(const Plan& p, int cfg, int src, int dst, cudaStream_t st);
+cudaError_t launch_t_transfer2d(const Plan& p, int noff, int kslot, cudaStream_t st);
+cudaError_t launch_t_step2d(const Plan& p, int cfg, int src, int dst, int kslot, cudaStream_t st);
 cudaError_t launch_t_objective(const Plan& p, int noff, int src, cudaStream_t st);
-cudaError_t launch_t_bcT2d(const Plan& p, int noff, int lam, cudaStream_t st);
 cudaError_t launch_t_adj2d(const Plan& p, int cfg, int noff, int lam_in, int lam_out, int sn,
-                           int sp, cudaStream_t st);
+                           int sp, int kslot, cudaStream_t st);
 cudaError_t launch_t_sens(const Plan& p, cudaStream_t st);
 cudaError_t launch_set_int(int* dst, int v, cudaStream_t st);
 

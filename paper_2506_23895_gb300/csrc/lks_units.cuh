@@ -276,12 +276,10 @@ __device__ __forceinline__ void obj_source(const Geom& g, int x, int y, int z, c
 // components of the boundary nodes it sources (WALL/INLET copy rho, OUTLET copies the normal
 // velocity), after their objective source.  Boundary nodes are read only; later kernels treat
 // them as zero.
+// bcT_gather adds those components to acc (the node's own value); bcT_node stores the sum.
 template <class T>
-__device__ __forceinline__ void bcT_node(const Geom& g, V4<T>* lam, const ObjAdd<T>& h, int x,
-                                         int y, int z) {
-    if (!sources_boundary(g, x, y, z)) return;
-    const long long m = node_index(g, x, y, z);
-    V4<T> acc = lam[m];
+__device__ __forceinline__ void bcT_gather(const Geom& g, const V4<T>* lam, const ObjAdd<T>& h,
+                                           int x, int y, int z, V4<T>& acc) {
     for_each_sourced_boundary(g, x, y, z, [&](int bx, int by, int bz, int f) {
         V4<T> lb = lam[node_index(g, bx, by, bz)];
         obj_source(g, bx, by, bz, h, lb);
@@ -295,6 +293,15 @@ __device__ __forceinline__ void bcT_node(const Geom& g, V4<T>* lam, const ObjAdd
             if (na == 2) acc.z += lb.z;
         }
     });
+}
+
+template <class T>
+__device__ __forceinline__ void bcT_node(const Geom& g, V4<T>* lam, const ObjAdd<T>& h, int x,
+                                         int y, int z) {
+    if (!sources_boundary(g, x, y, z)) return;
+    const long long m = node_index(g, x, y, z);
+    V4<T> acc = lam[m];
+    bcT_gather<T>(g, lam, h, x, y, z, acc);
     lam[m] = acc;
 }
 
