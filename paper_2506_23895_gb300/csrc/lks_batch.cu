@@ -89,7 +89,7 @@ lks_status batch_prepare(lks_batch* b, int n_steps) {
             }
             BCU(launch_set_int(b->nbase, 0, b->st));
             BCU(launch_t_design_pos(b->plan, 1, b->st));
-            BCU(launch_t_transfer2d(b->plan, 1, -1, b->st));
+            BCU(launch_t_transfer2d(b->plan, 1, -1, false, b->st));
             for (lks_ctx* c : b->cs) {
                 BCU(cudaMemsetAsync(c->lam[0], 0, c->snap_bytes, b->st));
                 BCU(cudaMemsetAsync(c->lam[1], 0, c->snap_bytes, b->st));

@@ -172,7 +172,7 @@ enum {
     // the second transfer buffer set (3D): same sizes as L_KUS, L_K2, L_CBASE, ...
     L_KUS2, L_K22, L_CBASE2, L_CFRAC2, L_CSC2, L_ZTI2, L_ZTW2, L_TCNT2, L_TIDX2, L_TW2, L_CM2,
     L_DZB2, L_DZF2, L_GBASE2, L_GFRAC2, L_GCNT2, L_GIDX2, L_E2,
-    L_KTAPE, L_POOL,
+    L_KTAPE, L_PB2, L_PSC2, L_POOL,
     L_COUNT
 };
 static_assert(L_COUNT <= 96, "Layout::off holds 96 regions");
@@ -268,6 +268,9 @@ Layout make_layout(const lks_config* cfg) {
         const long long kt = std::max((long long)std::ceil(std::sqrt((double)N)) + 2, 64LL);
         L.ktape_slots = t2d ? (int)std::min(P, kt) : 0;
         sz[L_KTAPE] = (size_t)L.ktape_slots * state;
+        // design positions of the steps of odd parity (even: L_CBASE, L_CSC)
+        sz[L_PB2] = t2d ? (size_t)ncol * 8 : 0;
+        sz[L_PSC2] = t2d ? (size_t)ncol * 16 : 0;
     }
     sz[L_POOL] = (size_t)P * state;
     size_t off = 0;
@@ -418,6 +421,8 @@ lks_status lks_create(const lks_config* cfg, void* workspace, size_t ws_bytes, l
                  !(cfg->flags & (LKS_FLAG_PLAIN_KERNELS | LKS_FLAG_PAPER_ALKS));
     c->ktape_slots = c->fused2d ? L.ktape_slots : 0;
     c->ktape = c->ktape_slots > 0 ? (void*)(w + L.off[L_KTAPE]) : nullptr;
+    c->pos2_b = w + L.off[L_PB2];
+    c->pos2_sc = (float4*)(w + L.off[L_PSC2]);
     c->dmotion = (Motion*)(w + L.off[L_MOTION]);
     c->dbufs = (void**)(w + L.off[L_BUFS]);
     c->dinst = (Inst*)(w + L.off[L_INST]);

@@ -80,6 +80,8 @@ struct lks_ctx {
     size_t snap_bytes;
     void* ktape = nullptr;       // transfer tape of the 2D table path (ktape_slots box records)
     int ktape_slots = 0;
+    void* pos2_b = nullptr;      // 2D table path: design positions of odd steps (int2 per column)
+    float4* pos2_sc = nullptr;   // and their sin, cos table
     // host state
     std::vector<double> motion;
     bool have_design = false, have_motion = false, fwd_valid = false;

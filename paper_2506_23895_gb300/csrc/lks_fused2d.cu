@@ -71,15 +71,23 @@ __device__ __forceinline__ V4<float>* kus_slot(const Inst& I, int kslot) {
 
 // ---------------------------------------------------------------- element-wise phases
 
-__global__ void __launch_bounds__(NT) k_t_design_pos(Plan p, int noff) {
+// Design positions of step n (unit u of the design-column units) into the set of n's parity.
+__device__ __forceinline__ void design_pos_unit(const Plan& p, int u, int n) {
     const int* pre = p.pre + U_DCOL * (p.count + 1);
+    const int i = find_inst(pre, p.count, u);
+    const Inst& I = p.tab[i];
+    const long long k = (long long)(u - pre[i]) * kUnitThreads + threadIdx.x;
+    if (k >= I.d.ncol) return;
+    int2 b;
+    float4 sc;
+    col_pos_sc(I.d, I.motion[n], k, b, sc);
+    I.pos_b[n & 1][k] = b;
+    I.pos_sc[n & 1][k] = sc;
+}
+
+__global__ void __launch_bounds__(NT) k_t_design_pos(Plan p, int noff) {
     const int n = step_of(p, noff);
-    for (int u = blockIdx.x; u < p.total[U_DCOL]; u += gridDim.x) {
-        const int i = find_inst(pre, p.count, u);
-        const Inst& I = p.tab[i];
-        const long long k = (long long)(u - pre[i]) * kUnitThreads + threadIdx.x;
-        if (k < I.d.ncol) design_col_pos_sc(I.d, I.motion[n], I.ts, k);
-    }
+    for (int u = blockIdx.x; u < p.total[U_DCOL]; u += gridDim.x) design_pos_unit(p, u, n);
 }
 
 // One 16 x 16 tile of the footprint box per work unit.  The design nodes any node of the tile can
@@ -89,14 +97,22 @@ __global__ void __launch_bounds__(NT) k_t_design_pos(Plan p, int noff) {
 constexpr int kTrWin = 32;   // staged window side (design nodes)
 static_assert(kBoxTile * kBoxTile == NT, "one box tile per block of NT threads");
 
-__global__ void __launch_bounds__(NT) k_t_transfer2d(Plan p, int noff, int kslot) {
+// With next, the units past the box tiles form the design positions of step n + 1 (the next
+// transfer's), into the other parity's set.
+__global__ void __launch_bounds__(NT) k_t_transfer2d(Plan p, int noff, int kslot, int next) {
     __shared__ int2 sb[kTrWin * kTrWin];
     __shared__ float4 ssc[kTrWin * kTrWin];
     __shared__ float skr[kTrWin * kTrWin];
     __shared__ int swin[4];
     const int* pre = p.pre + U_BOX * (p.count + 1);
     const int n = step_of(p, noff);
-    for (int u = blockIdx.x; u < p.total[U_BOX]; u += gridDim.x) {
+    const int nbox = p.total[U_BOX];
+    const int nall = nbox + (next ? p.total[U_DCOL] : 0);
+    for (int u = blockIdx.x; u < nall; u += gridDim.x) {
+        if (u >= nbox) {   // block-uniform: no barrier follows in this iteration
+            design_pos_unit(p, u - nbox, n + 1);
+            continue;
+        }
         const int i = find_inst(pre, p.count, u);
         const Inst& I = p.tab[i];
         const Design& d = I.d;
@@ -136,12 +152,12 @@ __global__ void __launch_bounds__(NT) k_t_transfer2d(Plan p, int noff, int kslot
         const int wni = swin[1] - wi0 + 1, wnj = swin[3] - wj0 + 1;
         const bool staged = wni <= kTrWin && wnj <= kTrWin;
         if (staged && wni > 0 && wnj > 0) {
-            const int2* base = reinterpret_cast<const int2*>(I.ts.col_base);
+            const int2* base = I.pos_b[n & 1];
             for (int e = threadIdx.x; e < wni * wnj; e += NT) {
                 const int jj = e / wni, ii = e - jj * wni;
                 const int k = (wj0 + jj) * d.L[0] + wi0 + ii;
                 sb[jj * kTrWin + ii] = __ldg(base + k);
-                ssc[jj * kTrWin + ii] = __ldg(I.ts.col_sc + k);
+                ssc[jj * kTrWin + ii] = __ldg(I.pos_sc[n & 1] + k);
                 skr[jj * kTrWin + ii] = __ldg(I.kref + k);
             }
         }
@@ -149,7 +165,8 @@ __global__ void __launch_bounds__(NT) k_t_transfer2d(Plan p, int noff, int kslot
         if (!node) continue;
         const long long bi = (long long)by * g.bn[0] + bx;
         if (!staged) {   // a window wider than the staging area: the global-memory path
-            transfer2d_node(d, g, m, I.ts, I.kref, kus_slot(I, kslot), bi);
+            transfer2d_node(d, g, m, I.pos_b[n & 1], I.pos_sc[n & 1], I.kref, kus_slot(I, kslot),
+                            bi);
             continue;
         }
         const float gx0 = d.xiGf[0], gy0 = d.xiGf[1];
@@ -186,13 +203,14 @@ __global__ void __launch_bounds__(kObjThreads) k_t_objective(Plan p, int noff, i
     }
 }
 
-__global__ void __launch_bounds__(NT) k_t_sens(Plan p) {
+__global__ void __launch_bounds__(NT) k_t_sens(Plan p, int noff) {
     const int* pre = p.pre + U_DCOL * (p.count + 1);
+    const int n = step_of(p, noff);
     for (int u = blockIdx.x; u < p.total[U_DCOL]; u += gridDim.x) {
         const int i = find_inst(pre, p.count, u);
         const Inst& I = p.tab[i];
         const long long k = (long long)(u - pre[i]) * kUnitThreads + threadIdx.x;
-        if (k < I.d.ncol) sens2d_node(I.d, I.g, I.ts, I.e, I.kprime, I.gacc, k);
+        if (k < I.d.ncol) sens2d_node(I.d, I.g, I.motion[n], I.e, I.kprime, I.gacc, k);
     }
 }
 
@@ -919,9 +937,9 @@ cudaError_t launch_t_design_pos(const Plan& p, int noff, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_t_transfer2d(const Plan& p, int noff, int kslot, cudaStream_t st) {
+cudaError_t launch_t_transfer2d(const Plan& p, int noff, int kslot, bool next, cudaStream_t st) {
     if (p.total[U_BOX] == 0) return cudaSuccess;
-    k_t_transfer2d<<<p.grid[U_BOX], NT, 0, st>>>(p, noff, kslot);
+    k_t_transfer2d<<<p.grid[U_BOX], NT, 0, st>>>(p, noff, kslot, next ? 1 : 0);
     return cudaGetLastError();
 }
 
@@ -958,9 +976,9 @@ cudaError_t launch_t_adj2d(const Plan& p, int cfg, int noff, int lam_in, int lam
     }
 }
 
-cudaError_t launch_t_sens(const Plan& p, cudaStream_t st) {
+cudaError_t launch_t_sens(const Plan& p, int noff, cudaStream_t st) {
     if (p.total[U_DCOL] == 0) return cudaSuccess;
-    k_t_sens<<<p.grid[U_DCOL], NT, 0, st>>>(p);
+    k_t_sens<<<p.grid[U_DCOL], NT, 0, st>>>(p, noff);
     return cudaGetLastError();
 }
 

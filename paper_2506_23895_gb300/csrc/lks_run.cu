@@ -178,7 +178,7 @@ lks_status transfer_at(lks_ctx* c, int n) {
     if (c->fused2d) {
         CU(launch_set_int(c->nbase, n, c->st));
         CU(launch_t_design_pos(c->plan, 0, c->st));
-        CU(launch_t_transfer2d(c->plan, 0, -1, c->st));
+        CU(launch_t_transfer2d(c->plan, 0, -1, false, c->st));
         c->stats[4] += 3;
         return LKS_OK;
     }
@@ -405,16 +405,21 @@ bool tape_transfers(const Group& G) {
 
 // Table-path launch sequences of one forward / adjoint step at offset k from *nbase.  kslot >= 0:
 // the step's transfer goes to (forward) or comes from (adjoint) slot kslot of the transfer tape.
+// The design positions of a run's first step come from their own launch, those of the later
+// steps from the previous step's transfer (first, next).
 cudaError_t table_fwd_launches(const Group& G, int k, int src, int dst, bool with_obj, int kslot,
-                               lks_ctx* timed, int n, int& nl) {
+                               bool first, bool next, lks_ctx* timed, int n, int& nl) {
     cudaError_t e;
-    if ((e = launch_t_design_pos(*G.plan, k, G.st)) != cudaSuccess) return e;
-    if ((e = launch_t_transfer2d(*G.plan, k, kslot, G.st)) != cudaSuccess) return e;
+    if (first) {
+        if ((e = launch_t_design_pos(*G.plan, k, G.st)) != cudaSuccess) return e;
+        ++nl;
+    }
+    if ((e = launch_t_transfer2d(*G.plan, k, kslot, next, G.st)) != cudaSuccess) return e;
     const bool tm = timed && timing_begin(timed, n, 0);
     if ((e = launch_t_step2d(*G.plan, G.tile_fwd, src, dst, kslot, G.st)) != cudaSuccess)
         return e;
     if (tm) timing_end(timed, 0);
-    nl += 3;
+    nl += 2;
     if (with_obj) {
         if ((e = launch_t_objective(*G.plan, k, dst, G.st)) != cudaSuccess) return e;
         ++nl;
@@ -422,23 +427,23 @@ cudaError_t table_fwd_launches(const Group& G, int k, int src, int dst, bool wit
     return cudaSuccess;
 }
 
-// The adjoint step gathers the transpose of the boundary copies itself; the design positions
-// of the step are formed again for the sensitivity gather.
+// The adjoint step gathers the transpose of the boundary copies itself, and the sensitivity
+// gather forms the design positions of its step.
 cudaError_t table_adj_launches(const Group& G, int k, int lam_in, int lam_out, int sn, int sp,
                                int kslot, lks_ctx* timed, int n, int& nl) {
     cudaError_t e;
-    if ((e = launch_t_design_pos(*G.plan, k, G.st)) != cudaSuccess) return e;
     if (kslot < 0) {
-        if ((e = launch_t_transfer2d(*G.plan, k, -1, G.st)) != cudaSuccess) return e;
-        ++nl;
+        if ((e = launch_t_design_pos(*G.plan, k, G.st)) != cudaSuccess) return e;
+        if ((e = launch_t_transfer2d(*G.plan, k, -1, false, G.st)) != cudaSuccess) return e;
+        nl += 2;
     }
     const bool tm = timed && timing_begin(timed, n, 1);
     if ((e = launch_t_adj2d(*G.plan, G.tile_adj, k, lam_in, lam_out, sn, sp, kslot, G.st)) !=
         cudaSuccess)
         return e;
     if (tm) timing_end(timed, 1);
-    if ((e = launch_t_sens(*G.plan, G.st)) != cudaSuccess) return e;
-    nl += 3;
+    if ((e = launch_t_sens(*G.plan, k, G.st)) != cudaSuccess) return e;
+    nl += 2;
     return cudaSuccess;
 }
 
@@ -515,7 +520,7 @@ lks_status run_steps(Group& G, int from_level, int to_level, bool with_obj, int 
                 src = BUF_S0 + w;
                 dst = BUF_S0 + 1 - w;
             }
-            return table_fwd_launches(G, k, src, dst, obj, kt ? toff + k : -1,
+            return table_fwd_launches(G, k, src, dst, obj, kt ? toff + k : -1, k == 1, k < len,
                                       (direct && G.count == 1) ? c0 : nullptr, from_level + k, nl);
         };
         const auto key = std::make_tuple(tape_seg >= 0 ? 1 : 0, obj ? 1 : 0, len,
@@ -777,7 +782,10 @@ Inst make_inst(const lks_ctx* c) {
     std::memset(&I, 0, sizeof(I));
     I.g = c->g;
     I.d = c->d;
-    I.ts = c->ts;
+    I.pos_b[0] = reinterpret_cast<int2*>(c->ts.col_base);
+    I.pos_sc[0] = c->ts.col_sc;
+    I.pos_b[1] = reinterpret_cast<int2*>(c->pos2_b);
+    I.pos_sc[1] = c->pos2_sc;
     I.motion = c->dmotion;
     I.bufs = c->dbufs;
     I.kref = (const float*)c->kref;

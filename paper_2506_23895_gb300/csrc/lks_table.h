@@ -16,7 +16,8 @@ enum { BUF_S0 = 0, BUF_S1 = 1, BUF_INIT = 2, BUF_LAM0 = 3, BUF_LAM1 = 4, BUF_POO
 struct Inst {
     Geom g;
     Design d;
-    TransferScratch ts;
+    int2* pos_b[2];           // design positions of the steps of each parity: integer base of
+    float4* pos_sc[2];        // x_ref, y_ref and sin, cos of (pi f / 2) of their fractions
     const Motion* motion;     // rows 0..max_steps with cos/sin already evaluated (device)
     void* const* bufs;        // BUF_* (device)
     const float* kref;        // kappa_ref per design node
@@ -80,14 +81,15 @@ void plan_grids(Plan& p);
 
 // Launchers (stream st; noff = step offset from *nbase; buffer arguments are BUF_* indices;
 // kslot: the kappa, u_S records a launch writes (transfer) or reads (step, adjoint): -1 for the
-// box buffer kus, else slot kslot of kus_tape).
+// box buffer kus, else slot kslot of kus_tape; next: the transfer also forms the design positions
+// of the following step).
 cudaError_t launch_t_design_pos(const Plan& p, int noff, cudaStream_t st);
-cudaError_t launch_t_transfer2d(const Plan& p, int noff, int kslot, cudaStream_t st);
+cudaError_t launch_t_transfer2d(const Plan& p, int noff, int kslot, bool next, cudaStream_t st);
 cudaError_t launch_t_step2d(const Plan& p, int cfg, int src, int dst, int kslot, cudaStream_t st);
 cudaError_t launch_t_objective(const Plan& p, int noff, int src, cudaStream_t st);
 cudaError_t launch_t_adj2d(const Plan& p, int cfg, int noff, int lam_in, int lam_out, int sn,
                            int sp, int kslot, cudaStream_t st);
-cudaError_t launch_t_sens(const Plan& p, cudaStream_t st);
+cudaError_t launch_t_sens(const Plan& p, int noff, cudaStream_t st);
 cudaError_t launch_set_int(int* dst, int v, cudaStream_t st);
 
 }  // namespace lks

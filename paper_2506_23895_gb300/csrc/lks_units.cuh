@@ -56,19 +56,17 @@ __device__ __forceinline__ int ref_coord(float ah, float al, float da, float bh,
     return gi + (int)fl;
 }
 
-__device__ __forceinline__ void design_col_pos_sc(const Design& d, const Motion& m,
-                                                  const TransferScratch& ts, long long k) {
+__device__ __forceinline__ void col_pos_sc(const Design& d, const Motion& m, long long k, int2& b,
+                                           float4& sc) {
     const int i = (int)((unsigned)k % (unsigned)d.L[0]), j = (int)((unsigned)k / (unsigned)d.L[0]);
     const float dx = (float)i - d.xiGf[0], dy = (float)j - d.xiGf[1];
     float fx, fy;   // Eq. rigid_body_position: x_ref = c dx - s dy + x_G, y_ref = s dx + c dy + y_G
-    const int bx = ref_coord(m.ch, m.cl, dx, m.sh, m.sl, dy, m.xgi[0], m.xgh[0], m.xgl[0], fx);
-    const int by = ref_coord(m.sh, m.sl, dx, -m.ch, -m.cl, dy, m.xgi[1], m.xgh[1], m.xgl[1], fy);
-    reinterpret_cast<int2*>(ts.col_base)[k] = make_int2(bx, by);
-    float4 sc;
+    b.x = ref_coord(m.ch, m.cl, dx, m.sh, m.sl, dy, m.xgi[0], m.xgh[0], m.xgl[0], fx);
+    b.y = ref_coord(m.sh, m.sl, dx, -m.ch, -m.cl, dy, m.xgi[1], m.xgh[1], m.xgl[1], fy);
     sincospif(0.5f * fx, &sc.x, &sc.y);
     sincospif(0.5f * fy, &sc.z, &sc.w);
-    ts.col_sc[k] = sc;
 }
+
 
 __device__ __forceinline__ float tap_weight(int q1, float S, float C) {
     // q1 = q + 1 in 0..3
@@ -81,7 +79,8 @@ __device__ __forceinline__ float tap_weight(int q1, float S, float C) {
 // affine in xi).  The design nodes whose taps cover x are found through the inverse rigid map
 // (a window widened against rounding) and summed in design index order.
 __device__ __forceinline__ void transfer2d_node(const Design& d, const Geom& g, const Motion& m,
-                                                const TransferScratch& ts,
+                                                const int2* __restrict__ pb,
+                                                const float4* __restrict__ psc,
                                                 const float* __restrict__ kref,
                                                 V4<float>* kus, long long bi) {
     const int x = g.blo[0] + (int)((unsigned)bi % (unsigned)g.bn[0]);
@@ -93,16 +92,15 @@ __device__ __forceinline__ void transfer2d_node(const Design& d, const Geom& g, 
     const float R = 2.f * (fabsf(c) + fabsf(s)) + 0.01f;
     const int i0 = max(0, (int)ceilf(ic - R)), i1 = min(d.L[0] - 1, (int)floorf(ic + R));
     const int j0 = max(0, (int)ceilf(jc - R)), j1 = min(d.L[1] - 1, (int)floorf(jc + R));
-    const int2* base = reinterpret_cast<const int2*>(ts.col_base);
     const float gx0 = d.xiGf[0], gy0 = d.xiGf[1];
     float kap = 0.f, m0 = 0.f, m1x = 0.f, m1y = 0.f;
     for (int j = j0; j <= j1; ++j)
         for (int i = i0; i <= i1; ++i) {
             const int k = j * d.L[0] + i;
-            const int2 b = __ldg(base + k);
+            const int2 b = __ldg(pb + k);
             const int qx = x - b.x + 1, qy = y - b.y + 1;
             if ((unsigned)qx > 3u || (unsigned)qy > 3u) continue;
-            const float4 sc = __ldg(ts.col_sc + k);
+            const float4 sc = __ldg(psc + k);
             const float W = tap_weight(qx, sc.x, sc.y) * tap_weight(qy, sc.z, sc.w);
             kap += W * __ldg(kref + k);
             m0 += W;
@@ -119,13 +117,15 @@ __device__ __forceinline__ void transfer2d_node(const Design& d, const Geom& g, 
 }
 
 // Sensitivity gather for design node k on the table path: sum over its 4 x 4 taps of
-// W e(x) with the same tap weights as transfer2d_node, times kappa', added to dJ/dgamma (FP64).
-__device__ __forceinline__ void sens2d_node(const Design& d, const Geom& g,
-                                            const TransferScratch& ts, const float* __restrict__ e,
+// W e(x) with the same tap weights as transfer2d_node (the node's position at the step formed
+// here, by the same function), times kappa', added to dJ/dgamma (FP64).
+__device__ __forceinline__ void sens2d_node(const Design& d, const Geom& g, const Motion& m,
+                                            const float* __restrict__ e,
                                             const float* __restrict__ kprime,
                                             double* __restrict__ gacc, long long k) {
-    const int2 b = reinterpret_cast<const int2*>(ts.col_base)[k];
-    const float4 sc = ts.col_sc[k];
+    int2 b;
+    float4 sc;
+    col_pos_sc(d, m, k, b, sc);
     const int ex0 = b.x - 1 - g.blo[0], ey0 = b.y - 1 - g.blo[1];
     float acc = 0.f;
 #pragma unroll
