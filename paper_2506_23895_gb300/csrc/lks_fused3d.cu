@@ -201,6 +201,44 @@ __device__ __forceinline__ void feq_node(const FusedArgs& a, const float4* __res
     }
 }
 
+// Boundary copies of a z-march forward step (Eqs. bc_rho, bc_u), once the step is written: one
+// thread per interior node next to a face -- the x layers, then the y layers without the x
+// layers' nodes, then the z layers without both -- each writing the boundary nodes it sources.
+__global__ void __launch_bounds__(256) k_bc_shell3d(Geom g, float4* __restrict__ s) {
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+    const long long ix = nx - 2, iy = ny - 2, iz = nz - 2;   // interior extents
+    const long long per[3] = {2 * iy * iz, 2 * ix * iz, 2 * ix * iy};
+    long long r = t;
+    int a = 0;
+    while (a < 3 && r >= per[a]) {
+        r -= per[a];
+        ++a;
+    }
+    if (a == 3) return;
+    const bool hi = (r & 1) != 0;
+    r >>= 1;
+    int x, y, z;
+    if (a == 0) {
+        x = hi ? nx - 2 : 1;
+        y = 1 + (int)(r % iy);
+        z = 1 + (int)(r / iy);
+        if (hi && ix == 1) return;   // a single interior row: the low layer writes
+    } else if (a == 1) {
+        y = hi ? ny - 2 : 1;
+        x = 1 + (int)(r % ix);
+        z = 1 + (int)(r / ix);
+        if ((hi && iy == 1) || x == 1 || x == nx - 2) return;
+    } else {
+        z = hi ? nz - 2 : 1;
+        x = 1 + (int)(r % ix);
+        y = 1 + (int)(r / ix);
+        if ((hi && iz == 1) || x == 1 || x == nx - 2 || y == 1 || y == ny - 2) return;
+    }
+    const long long m = ((long long)z * ny + y) * nx + x;
+    write_bc_f(g, x, y, z, s[m], s);
+}
+
 __device__ __forceinline__ int axis_mode(int gcoord, int n) {
     return gcoord == 0 ? 1 : (gcoord == n - 1 ? 2 : 0);
 }
@@ -411,8 +449,48 @@ __global__ void __launch_bounds__(NTHR, 4)
 //   * the cross-column f^eq values alternate between two shared-memory buffers, so one barrier
 //     per plane orders both their writes and their reads;
 //   * tiles of 32 x 8 columns; tiles away from the x and y faces take a path without face
-//     tests, and the rim f^eq work fills whole warps.
+//     tests; in the others only the nodes on a face redo f^eq with one-sided derivatives (one
+//     lane of a row, or a whole row), and the rim f^eq work fills whole warps.
 // The arithmetic is that of feq_node and the gather above, operation for operation.
+// Own column of the x face in a tile of TX columns from x0 when the tile holds exactly one of
+// the two x faces, else -1.
+__host__ __device__ inline int xface_col(int x0, int nx, int TX) {
+    const bool lo = x0 == 0, hi = x0 <= nx - 1 && nx - 1 < x0 + TX;
+    return lo == hi ? -1 : (lo ? 0 : nx - 1 - x0);
+}
+
+// f^eq-region coordinates (hfx, hfy) of the extra node of thread tid: the one-cell rim over whole
+// warps.  In a tile holding exactly one x face, the lanes past the last rim node take that
+// face's column, one lane per row (those nodes need one-sided x derivatives, which the rim
+// warps form anyway); otherwise they repeat earlier rim nodes (the same values stored twice).
+template <int TX, int TY, int NHALO>
+__device__ __forceinline__ void rim_node(int tid, int x0, int nx, int& hfx, int& hfy) {
+    constexpr int FW = TX + 2, FY = TY + 2;
+    constexpr int RIMW = (NHALO + 31) / 32 * 32;
+    static_assert(RIMW - NHALO >= TY, "a spare rim lane per row of the tile");
+    hfx = 0;
+    hfy = 0;
+    if (tid >= RIMW) return;
+    const int xf = xface_col(x0, nx, TX);
+    if (tid >= NHALO && tid < NHALO + TY && xf >= 0) {
+        hfx = xf + 1;
+        hfy = 1 + (tid - NHALO);
+        return;
+    }
+    const int rr = tid < NHALO ? tid : tid - (RIMW - NHALO);
+    if (rr < FW) {
+        hfx = rr;
+    } else if (rr < 2 * FW) {
+        hfx = rr - FW;
+        hfy = FY - 1;
+    } else if (rr < 2 * FW + TY) {
+        hfy = 1 + (rr - 2 * FW);
+    } else {
+        hfx = FW - 1;
+        hfy = 1 + (rr - 2 * FW - TY);
+    }
+}
+
 template <int TY_>
 struct ZCfg {
     static constexpr int TX = 32, TY = TY_;
@@ -530,10 +608,10 @@ __device__ __forceinline__ void zbody(const CUtensorMap& tmap, const FusedArgs& 
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const int gx = x0 + tx, gy = y0 + ty;
     const int hgx = x0 - 1 + hfx, hgy = y0 - 1 + hfy;
-    const bool edge = !IN && ((x0 - 1 <= 0) || (x0 + TX >= nx - 1) || (y0 - 1 <= 0) ||
-                              (y0 + TY >= ny - 1));
     const int pxm = axis_mode(gx, nx), pym = axis_mode(gy, ny);
     const int rxm = axis_mode(hgx, nx), rym = axis_mode(hgy, ny);
+    // a node on the tile's single x face outside a y-face row: a rim lane evaluates its f^eq
+    const bool xskip = !IN && pxm != 0 && pym == 0 && xface_col(x0, nx, TX) >= 0;
     const int hp = (ty + 2) * HX + (tx + 2);
     const int hr = (hfy + 1) * HX + (hfx + 1);
     const int fop = (ty + 1) * FX + (tx + 1);
@@ -541,7 +619,6 @@ __device__ __forceinline__ void zbody(const CUtensorMap& tmap, const FusedArgs& 
     constexpr int RIMW = (C::NHALO + 31) / 32 * 32;
     const bool has_rim = tid < RIMW;   // whole warps
     const bool out_col = IN || (gx >= 1 && gx <= nx - 2 && gy >= 1 && gy <= ny - 2);
-    const bool bc_col = !IN && (gx == 1 || gx == nx - 2 || gy == 1 || gy == ny - 2);
     const int bxx = gx - g.blo[0], byy = gy - g.blo[1];
     const bool box_col = g.boxN > 0 && bxx >= 0 && byy >= 0 && bxx < g.bn[0] && byy < g.bn[1];
     const long long box_plane = (long long)g.bn[0] * g.bn[1];
@@ -578,8 +655,11 @@ __device__ __forceinline__ void zbody(const CUtensorMap& tmap, const FusedArgs& 
     // the output node of plane p - 1 in the column, advanced one plane per iteration (it is
     // only dereferenced for planes inside the grid)
     float4* outp = out_col_ptr + (long long)(q0 - 3) * zstride;
-    // One plane p.  STEADY (interior tiles, planes away from the z faces and from the chunk's
-    // first output): no z-face derivative modes, no output-range and no boundary-copy tests.
+    // One plane p.  STEADY (planes away from the z faces and from the chunk's first output): no
+    // z-face derivative modes, no z output-range and no z boundary-copy tests.  Off the z faces
+    // every node takes the central-difference f^eq; in tiles at an x or y face (IN false) the
+    // face nodes then evaluate it again with their one-sided derivatives, and the output keeps
+    // its column tests and boundary copies.
     auto plane = [&](int p, auto steady) {
         constexpr bool STEADY = decltype(steady)::value;
         const bool good = mbar_wait_once(smem_addr(&bars[wslot]), wpar);
@@ -592,15 +672,37 @@ __device__ __forceinline__ void zbody(const CUtensorMap& tmap, const FusedArgs& 
         float4 rcpn = make_float4(0.f, 0.f, 0.f, 0.f);
         if (has_rim) rcpn = rp[hr];
         const float3 rup = make_float3(rcpn.y, rcpn.z, rcpn.w);
-        float f_rest, f_pz, f_mz;
+        float f_rest = 0.f, f_pz = 0.f, f_mz = 0.f;
         const int zm = STEADY ? 0 : ((p == 0) ? 1 : (p == nz - 1 ? 2 : 0));
-        if (STEADY || (!edge && zm == 0)) {
+        if (STEADY || zm == 0) {
             const float4 z0 = make_float4(0.f, 0.f, 0.f, 0.f);
-            feq_reg<HX, FS, false>(a, r0 + hp, c0, um, up, sFp, 0, 0, 0, z0, f_rest, f_pz, f_mz);
-            if (has_rim) {
-                float d0, d1, d2;
-                feq_reg<HX, FS, false>(a, r0 + hr, rc0, rum, rup, sF + forr, 0, 0, 0, z0, d0, d1,
-                                       d2);
+            if (IN) {
+                feq_reg<HX, FS, false>(a, r0 + hp, c0, um, up, sFp, 0, 0, 0, z0, f_rest, f_pz,
+                                       f_mz);
+                if (has_rim) {
+                    float d0, d1, d2;
+                    feq_reg<HX, FS, false>(a, r0 + hr, rc0, rum, rup, sF + forr, 0, 0, 0, z0, d0,
+                                           d1, d2);
+                }
+            } else {
+                // one-sided x / y derivatives where the node is on a face: a y-face row as a
+                // whole warp; the rim warps for the rim and the column of the tile's x face,
+                // whose lanes in the other rows leave their node to them (xskip)
+                if (pym != 0) {
+                    feq_reg<HX, FS, true>(a, r0 + hp, c0, um, up, sFp, pxm, pym, 0, z0, f_rest,
+                                          f_pz, f_mz);
+                } else if (!xskip) {
+                    feq_reg<HX, FS, false>(a, r0 + hp, c0, um, up, sFp, 0, 0, 0, z0, f_rest,
+                                           f_pz, f_mz);
+                    if (pxm != 0)   // a tile holding both x faces
+                        feq_reg<HX, FS, true>(a, r0 + hp, c0, um, up, sFp, pxm, 0, 0, z0, f_rest,
+                                              f_pz, f_mz);
+                }
+                if (has_rim) {
+                    float d0, d1, d2;
+                    feq_reg<HX, FS, true>(a, r0 + hr, rc0, rum, rup, sF + forr, rxm, rym, 0, z0,
+                                          d0, d1, d2);
+                }
             }
         } else {
             const int z2 = (zm == 1) ? 2 : nz - 3;
@@ -649,7 +751,7 @@ __device__ __forceinline__ void zbody(const CUtensorMap& tmap, const FusedArgs& 
             const float syp = cpp_m + cmp_m, sym = cpm_m + cmm_m;
             const float all = sxp + sxm + f_mz;
             const int qz = p - 1;
-            if (STEADY || (out_col && qz >= zlo && qz <= zhi)) {
+            if (STEADY ? out_col : (out_col && qz >= zlo && qz <= zhi)) {
                 const float r = acc0[0] + all;
                 const float ux = acc0[1] + (sxp - sxm) + bfx;
                 const float uy = acc0[2] + (syp - sym) + bfy;
@@ -668,9 +770,7 @@ __device__ __forceinline__ void zbody(const CUtensorMap& tmap, const FusedArgs& 
                     o.z = uy;
                     o.w = uz;
                 }
-                *outp = o;
-                if (!STEADY && (bc_col || qz == 1 || qz == nz - 2))
-                    write_bc_f(g, gx, gy, qz, o, a.out);
+                *outp = o;   // the boundary copies follow in k_bc_shell3d
             }
         }
         acc0[0] = acc1[0] + (f_rest + fpx + fmx + fpy + fmy);
@@ -688,7 +788,7 @@ __device__ __forceinline__ void zbody(const CUtensorMap& tmap, const FusedArgs& 
         }
     };
     // steady planes: output plane p - 1 in [max(q0, 2), nz - 3] and f^eq plane p off the faces
-    const int ps0 = IN ? max(q0 + 1, 3) : q1 + 1, ps1 = IN ? min(q1, nz - 2) : q1;
+    const int ps0 = max(q0 + 1, 3), ps1 = min(q1, nz - 2);
     int p = q0 - 1;
     for (; ok && p <= q1 && p < ps0; ++p) plane(p, std::false_type{});
 #pragma unroll 1
@@ -709,7 +809,7 @@ template <int TY_>
 __global__ void __launch_bounds__(ZCfg<TY_>::NTHR, ZCfg<TY_>::MINB)
     k_zstep3d(const __grid_constant__ CUtensorMap tmap, const FusedArgs a) {
     using C = ZCfg<TY_>;
-    constexpr int TX = C::TX, TY = C::TY, FW = C::FW, FY = C::FY;
+    constexpr int TX = C::TX, TY = C::TY;
     constexpr int NSLOT = C::NSLOT;
     extern __shared__ __align__(128) unsigned char smem[];
     float4* raw = reinterpret_cast<float4*>(smem);
@@ -724,22 +824,8 @@ __global__ void __launch_bounds__(ZCfg<TY_>::NTHR, ZCfg<TY_>::MINB)
     const int nplanes = q1 - q0 + 4;   // raw planes q0-2 .. q1+1 (load index k = plane - q0 + 2)
     // rim nodes over whole warps: lanes past the last rim node repeat earlier ones (the same
     // values are stored twice), so no warp splits on the rim work
-    constexpr int RIMW = (C::NHALO + 31) / 32 * 32;
-    const int rr = tid < C::NHALO ? tid : tid - (RIMW - C::NHALO);
-    int hfx = 0, hfy = 0;   // threads past the rim warps keep (0, 0): they read, never store
-    if (tid < RIMW) {
-        if (rr < FW) {
-            hfx = rr;
-        } else if (rr < 2 * FW) {
-            hfx = rr - FW;
-            hfy = FY - 1;
-        } else if (rr < 2 * FW + TY) {
-            hfy = 1 + (rr - 2 * FW);
-        } else {
-            hfx = FW - 1;
-            hfy = 1 + (rr - 2 * FW - TY);
-        }
-    }
+    int hfx, hfy;   // threads past the rim warps keep (0, 0): they read, never store
+    rim_node<TX, TY, C::NHALO>(tid, x0, nx, hfx, hfy);
     if ((smem_addr(smem) & 127u) != 0u) {
         if (tid == 0) atomicOr(a.err, 16);
         return;
@@ -1156,7 +1242,7 @@ __global__ void __launch_bounds__(PCfg::NTHR, PCfg::MINB)
     static_assert(C::TX == Z::TX && C::TY == Z::TY && C::SLOT == Z::SLOT && C::HX == Z::HX &&
                       C::HY == Z::HY && Z::SMEM <= C::SMEM,
                   "edge tiles reuse the register z-march in the same shared memory");
-    constexpr int TX = C::TX, TY = C::TY, FW = C::FW, FY = C::FY;
+    constexpr int TX = C::TX, TY = C::TY;
     extern __shared__ __align__(128) unsigned char smem[];
     float4* raw = reinterpret_cast<float4*>(smem);
     const Geom& g = a.f.g;
@@ -1165,22 +1251,8 @@ __global__ void __launch_bounds__(PCfg::NTHR, PCfg::MINB)
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const int q0 = blockIdx.z * a.f.zchunk;
     const int q1 = min(nz, q0 + a.f.zchunk);
-    constexpr int RIMW = (C::NHALO + 31) / 32 * 32;
-    const int rr = tid < C::NHALO ? tid : tid - (RIMW - C::NHALO);
-    int hfx = 0, hfy = 0;
-    if (tid < RIMW) {
-        if (rr < FW) {
-            hfx = rr;
-        } else if (rr < 2 * FW) {
-            hfx = rr - FW;
-            hfy = FY - 1;
-        } else if (rr < 2 * FW + TY) {
-            hfy = 1 + (rr - 2 * FW);
-        } else {
-            hfx = FW - 1;
-            hfy = 1 + (rr - 2 * FW - TY);
-        }
-    }
+    int hfx, hfy;
+    rim_node<TX, TY, C::NHALO>(tid, x0, nx, hfx, hfy);
     if ((smem_addr(smem) & 127u) != 0u) {
         if (tid == 0) atomicOr(a.f.err, 16);
         return;
@@ -1350,13 +1422,21 @@ cudaError_t launch_fused_step3d(const Geom& g, const V4<float>* src, const V4<fl
     a.w2 = Wts<float, 3>::w2;
     for (int k = 0; k < 3; ++k) a.bf[k] = (float)g.body[k];
     CUtensorMap map;
-    if (v == 2) {
-        if (!encode_state_map(&map, src, g, PCfg::HX, PCfg::HY)) return cudaErrorInvalidValue;
-        return launch_zpair(g, map, a, st);
-    }
-    if (v == 1) {
-        if (!encode_state_map(&map, src, g, ZCfg<8>::HX, ZCfg<8>::HY)) return cudaErrorInvalidValue;
-        return launch_zstep<8>(g, map, a, st);
+    if (v == 1 || v == 2) {
+        cudaError_t e;
+        if (v == 2) {
+            if (!encode_state_map(&map, src, g, PCfg::HX, PCfg::HY)) return cudaErrorInvalidValue;
+            e = launch_zpair(g, map, a, st);
+        } else {
+            if (!encode_state_map(&map, src, g, ZCfg<8>::HX, ZCfg<8>::HY))
+                return cudaErrorInvalidValue;
+            e = launch_zstep<8>(g, map, a, st);
+        }
+        if (e != cudaSuccess) return e;
+        const long long ix = g.n[0] - 2, iy = g.n[1] - 2, iz = g.n[2] - 2;
+        const long long shell = 2 * (iy * iz + ix * iz + ix * iy);
+        k_bc_shell3d<<<(unsigned)((shell + 255) / 256), 256, 0, st>>>(g, a.out);
+        return cudaGetLastError();
     }
     if (!encode_state_map(&map, src, g, HX, HY)) return cudaErrorInvalidValue;
     static std::atomic<unsigned> attr{0};   // devices whose shared-memory limit is raised
