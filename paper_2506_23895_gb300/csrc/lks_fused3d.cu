@@ -201,21 +201,42 @@ __device__ __forceinline__ void feq_node(const FusedArgs& a, const float4* __res
     }
 }
 
+// Single-precision face values for the boundary copies: per face the prescribed (ux, uy, uz,
+// rho - rho0), rounded once on the host, and whether the face keeps the source's rho (wall,
+// inlet: u prescribed) or prescribes rho and copies the normal velocity (outlet).
+struct ShellFaces {
+    float4 v[6];
+    int keep_rho[6];
+};
+
+// The value bc_value gives a boundary node of face f from its source's value o (x: rho - rho0).
+__device__ __forceinline__ float4 face_value(const ShellFaces& F, int f, const float4& o) {
+    const float4 p = F.v[f];
+    if (F.keep_rho[f]) return make_float4(o.x, p.x, p.y, p.z);
+    const int na = f >> 1;
+    return make_float4(p.w, na == 0 ? o.y : p.x, na == 1 ? o.z : p.y, na == 2 ? o.w : p.z);
+}
+
 // Boundary copies of a z-march forward step (Eqs. bc_rho, bc_u), once the step is written: one
 // thread per interior node next to a face -- the x layers, then the y layers without the x
-// layers' nodes, then the z layers without both -- each writing the boundary nodes it sources.
-__global__ void __launch_bounds__(256) k_bc_shell3d(Geom g, float4* __restrict__ s) {
+// layers' nodes, then the z layers without both -- each writing the boundary nodes it sources
+// (one node of one face for most; edges and corners through write_bc_f).
+__global__ void __launch_bounds__(256)
+    k_bc_shell3d(Geom g, const __grid_constant__ ShellFaces F, float4* __restrict__ s) {
     const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
     const long long ix = nx - 2, iy = ny - 2, iz = nz - 2;   // interior extents
-    const long long per[3] = {2 * iy * iz, 2 * ix * iz, 2 * ix * iy};
     long long r = t;
-    int a = 0;
-    while (a < 3 && r >= per[a]) {
-        r -= per[a];
-        ++a;
+    int a;
+    if (r < 2 * iy * iz) {
+        a = 0;
+    } else if ((r -= 2 * iy * iz) < 2 * ix * iz) {
+        a = 1;
+    } else if ((r -= 2 * ix * iz) < 2 * ix * iy) {
+        a = 2;
+    } else {
+        return;
     }
-    if (a == 3) return;
     const bool hi = (r & 1) != 0;
     r >>= 1;
     int x, y, z;
@@ -236,7 +257,25 @@ __global__ void __launch_bounds__(256) k_bc_shell3d(Geom g, float4* __restrict__
         if ((hi && iz == 1) || x == 1 || x == nx - 2 || y == 1 || y == ny - 2) return;
     }
     const long long m = ((long long)z * ny + y) * nx + x;
-    write_bc_f(g, x, y, z, s[m], s);
+    const float4 o = s[m];
+    const int nfx = (x == 1) + (x == nx - 2), nfy = (y == 1) + (y == ny - 2);
+    const int nfz = (z == 1) + (z == nz - 2);
+    if (nfx + nfy + nfz == 1) {
+        int f, bx = x, by = y, bz = z;
+        if (nfx) {
+            f = x == 1 ? 0 : 1;
+            bx = x == 1 ? 0 : nx - 1;
+        } else if (nfy) {
+            f = y == 1 ? 2 : 3;
+            by = y == 1 ? 0 : ny - 1;
+        } else {
+            f = z == 1 ? 4 : 5;
+            bz = z == 1 ? 0 : nz - 1;
+        }
+        s[((long long)bz * ny + by) * nx + bx] = face_value(F, f, o);
+        return;
+    }
+    write_bc_f(g, x, y, z, o, s);
 }
 
 __device__ __forceinline__ int axis_mode(int gcoord, int n) {
@@ -1433,9 +1472,15 @@ cudaError_t launch_fused_step3d(const Geom& g, const V4<float>* src, const V4<fl
             e = launch_zstep<8>(g, map, a, st);
         }
         if (e != cudaSuccess) return e;
+        ShellFaces F;
+        for (int f = 0; f < 6; ++f) {
+            F.v[f] = make_float4((float)g.bcv[f][0], (float)g.bcv[f][1], (float)g.bcv[f][2],
+                                 (float)(g.bcv[f][3] - g.rho0));
+            F.keep_rho[f] = g.bc[f] == BC_WALL || g.bc[f] == BC_INLET;
+        }
         const long long ix = g.n[0] - 2, iy = g.n[1] - 2, iz = g.n[2] - 2;
         const long long shell = 2 * (iy * iz + ix * iz + ix * iy);
-        k_bc_shell3d<<<(unsigned)((shell + 255) / 256), 256, 0, st>>>(g, a.out);
+        k_bc_shell3d<<<(unsigned)((shell + 255) / 256), 256, 0, st>>>(g, F, a.out);
         return cudaGetLastError();
     }
     if (!encode_state_map(&map, src, g, HX, HY)) return cudaErrorInvalidValue;

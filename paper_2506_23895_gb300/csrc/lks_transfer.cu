@@ -196,6 +196,63 @@ __global__ void __launch_bounds__(kThreads)
     }
 }
 
+// The same lists, moments and plane sums with one thread per box column, for transfers with few
+// design planes (2D): there a box column is a single node, the columns are many and the warp
+// per column would leave its lanes idle over the plane sums.
+template <class T>
+__global__ void __launch_bounds__(kThreads)
+    k_tap_lists_col(Design d, Geom g, Motion m, TransferScratch ts, const T* __restrict__ kref_t,
+                    T* __restrict__ k2) {
+    const long long ncols = (long long)g.bn[0] * g.bn[1];
+    const long long col = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (col >= ncols) return;
+    const int x = g.blo[0] + (int)(col % g.bn[0]);
+    const int y = g.blo[1] + (int)(col / g.bn[0]);
+    const float px = (float)x - m.xgf[0], py = (float)y - m.xgf[1];
+    const float ic = fmaf(m.cf, px, fmaf(m.sf, py, d.xiGf[0]));
+    const float jc = fmaf(-m.sf, px, fmaf(m.cf, py, d.xiGf[1]));
+    const float R = 2.f * (fabsf(m.cf) + fabsf(m.sf)) + 0.01f;
+    const int i0 = max(0, (int)ceilf(ic - R)), i1 = min(d.L[0] - 1, (int)floorf(ic + R));
+    const int j0 = max(0, (int)ceilf(jc - R)), j1 = min(d.L[1] - 1, (int)floorf(jc + R));
+    const T* frac = (const T*)ts.col_frac;
+    int* tidx = ts.tap_idx + col * kMaxTaps;
+    T* tw = (T*)ts.tap_w + col * kMaxTaps;
+    int cnt = 0;
+    T m0 = (T)0, m1x = (T)0, m1y = (T)0;
+    for (int j = j0; j <= j1; ++j)
+        for (int i = i0; i <= i1; ++i) {
+            const int k = j * d.L[0] + i;
+            const T rx = (T)(x - ts.col_base[2 * k]) - frac[2 * k];
+            const T ry = (T)(y - ts.col_base[2 * k + 1]) - frac[2 * k + 1];
+            if (!(fabs(rx) < (T)2 && fabs(ry) < (T)2)) continue;   // exact in T
+            const T W = peskin(rx) * peskin(ry);
+            if (W == (T)0) continue;
+            if (cnt == kMaxTaps) {
+                atomicOr(ts.err, 1);
+                i = i1;
+                j = j1;
+                break;
+            }
+            tidx[cnt] = k;
+            tw[cnt] = W;
+            ++cnt;
+            m0 += W;
+            m1x += W * (T)(i - d.xiG[0]);
+            m1y += W * (T)(j - d.xiG[1]);
+        }
+    ts.tap_cnt[col] = cnt;
+    T* cm = (T*)ts.col_m + 3 * col;
+    cm[0] = m0;
+    cm[1] = m1x;
+    cm[2] = m1y;
+    const int lz = d.L[2];
+    for (int z = 0; z < lz; ++z) {
+        T a = (T)0;
+        for (int e = 0; e < cnt; ++e) a += tw[e] * kref_t[(long long)tidx[e] * lz + z];
+        k2[col * lz + z] = a;
+    }
+}
+
 // The fill: kappa = sum over the z taps of w_z K2 and u_S = m_z (omega R'(theta) m1 + u_G m0)
 // on every node of the footprint box (u_ref is affine in xi, Eq. rigid_body_velocity).  A block
 // covers 32 box columns x 8 box planes; the K2 values those planes need (a window of at most
@@ -414,8 +471,12 @@ void launch_transfer(const Design& d, const Geom& g, const Motion& m, TransferSc
                      const T* kref_t, T* k2, V4<T>* kus, cudaStream_t st) {
     if (d.nd == 0 || g.boxN == 0) return;
     const long long ncols = (long long)g.bn[0] * g.bn[1];
-    k_tap_lists<T><<<(unsigned)((ncols + kTapWarps - 1) / kTapWarps), kThreads, 0, st>>>(
-        d, g, m, ts, kref_t, k2);
+    if (d.L[2] >= 8)
+        k_tap_lists<T><<<(unsigned)((ncols + kTapWarps - 1) / kTapWarps), kThreads, 0, st>>>(
+            d, g, m, ts, kref_t, k2);
+    else
+        k_tap_lists_col<T><<<(unsigned)((ncols + kThreads - 1) / kThreads), kThreads, 0, st>>>(
+            d, g, m, ts, kref_t, k2);
     const dim3 fgrd((unsigned)((ncols + kFillCols - 1) / kFillCols),
                     (unsigned)((g.bn[2] + kFillPlanes - 1) / kFillPlanes));
     k_fill<T><<<fgrd, kFillCols * kFillPlanes, 0, st>>>(d, g, m, ts, k2, kus);
