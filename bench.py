@@ -66,6 +66,9 @@ def parse():
                     help="instead of the benchmark: the 512^2 channel workload at its full "
                          "horizon, dJ/dgamma of the GPU FP64 path against central differences "
                          "(eps = 1e-4) at CELLS seeded design cells, one JSON line")
+    ap.add_argument("--step-variant", type=int, choices=[0, 1, 2], default=None,
+                    help="fused 3D forward-step variant of the 256^3 leg (default: the "
+                         "library's, 1)")
     ap.add_argument("--workload", choices=["cfg4", "batch2d"], default="cfg4",
                     help="cfg4: the 256^3 3D line (default); batch2d: the batched 2D workload")
     return ap.parse_args()
@@ -438,6 +441,8 @@ def run_ours(args):
     nodes = p.nodes
     stream = torch.cuda.current_stream()
     solver = lks.Solver(p, lks.FP32, stream=stream)
+    if args.step_variant is not None:
+        solver.step_variant(args.step_variant)
     solver.set_motion(w.motion)
     gamma_dev = torch.from_numpy(w.gamma).to(dev)
     g_dev = torch.empty(w.gamma.shape, dtype=torch.float64, device=dev)
@@ -628,7 +633,17 @@ def run_ours(args):
             "tolerance": {"J_rel": 1e-5, "dJdgamma_rel_l2": 1e-4}}
     tr = committed_ncu("ncu_transfer", TRANSFER_SOURCES)
     if rank == 0 and tr:
-        out["transfer"] = {k: tr[k] for k in ("kernels", "per_step", "note") if k in tr}
+        # each transfer kernel against the two ceilings that could bind it: DRAM bytes over the
+        # measured copy bandwidth, and executed warp instructions over the SMs' issue rate
+        # (152 SMs x 4 schedulers x 2070 MHz); both well below 1 means latency-bound
+        issue_rate = 152 * 4 * 2.07e9
+        kern = {}
+        for name, k in tr.get("kernels", {}).items():
+            t = k["us"] * 1e-6
+            kern[name] = dict(k, dram_frac=k["dram_mb"] * 1e6 / t / (peak * 1e9),
+                              issue_frac=k["warp_inst"] / t / issue_rate)
+        out["transfer"] = {"kernels": kern, "per_step": tr.get("per_step"),
+                           "note": tr.get("note"), "source": "profiles/ncu_transfer.json"}
     if rank == 0 and not args.no_batch:
         out["batch2d"] = batch2d_leg(args, lks, W, stream)
     if rank == 0 and not args.no_configs:

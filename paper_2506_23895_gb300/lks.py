@@ -346,7 +346,7 @@ class Solver:
         return {1: "fused3d", 2: "fused2d"}.get(self.lib.lks_uses_fused(self.ctx), "plain")
 
     def step_variant(self, request: int = -2) -> int:
-        """Fused 3D step variant: request 0..1 fixes one (1 by default), -1 times them on the
+        """Fused 3D step variant: request 0..2 fixes one (1 by default), -1 times them on the
         first step, -2 only reads; returns the variant in use (-1 before the first fused step)."""
         v = ctypes.c_int(-1)
         self._check(self.lib.lks_step_variant(self.ctx, request, ctypes.byref(v)))
