@@ -374,6 +374,38 @@ __device__ __forceinline__ bool meets_target(const Geom& g, int xa, int xb, int 
     return xb >= g.obox[0] && xa <= g.obox[1] && yb >= g.obox[2] && ya <= g.obox[3];
 }
 
+// Boundary copies sourced by interior node (x, y) of value o (Eqs. bc_rho, bc_u): a node next to
+// one face writes that face's boundary node with the face's single-precision values (the values
+// bc_value gives); a node next to two faces (a corner's source) takes the general rule.
+__device__ __forceinline__ void write_bc2(const Inst& I, int x, int y, const V4<float>& o,
+                                          V4<float>* out) {
+    const Geom& g = I.g;
+    const int n0 = g.n[0], n1 = g.n[1];
+    const bool xl = !g.periodic[0] && x == 1, xh = !g.periodic[0] && x == n0 - 2;
+    const bool yl = !g.periodic[1] && y == 1, yh = !g.periodic[1] && y == n1 - 2;
+    const int nf = (int)xl + (int)xh + (int)yl + (int)yh;
+    if (nf == 0) return;
+    if (nf > 1) {
+        write_bc_from(g, x, y, 0, o, out);
+        return;
+    }
+    const int f = xl ? 0 : (xh ? 1 : (yl ? 2 : 3));
+    const int bx = xl ? 0 : (xh ? n0 - 1 : x), by = yl ? 0 : (yh ? n1 - 1 : y);
+    const float4 p = I.bcf[f];
+    V4<float> b;
+    if (I.bckeep[f]) {
+        b.r = o.r;
+        b.x = p.x;
+        b.y = p.y;
+    } else {
+        b.r = p.w;
+        b.x = f < 2 ? o.x : p.x;
+        b.y = f < 2 ? p.y : o.y;
+    }
+    b.z = 0.f;
+    out[(long long)by * n0 + bx] = b;
+}
+
 // kappa, u_S at node (x, y) of the footprint box, else zero.
 __device__ __forceinline__ float4 kus_at(const Inst& I, int x, int y) {
     long long bi;
@@ -446,7 +478,7 @@ __device__ __forceinline__ void step_tile(const Inst& I, int x0, int y0, int src
                                        tbox ? kus_at(I, x, y) : make_float4(0.f, 0.f, 0.f, 0.f),
                                        kst, bfx, bfy);
         out[m] = o;
-        if (EDGE) write_bc_from(g, x, y, 0, o, out);
+        if (EDGE) write_bc2(I, x, y, o, out);
     }
     __syncthreads();
 }
@@ -600,7 +632,7 @@ __global__ void __launch_bounds__(NTH) k_t_step2d_rows(Plan p, const int* __rest
                         tbox ? kus_at(sI, xc, y) : make_float4(0.f, 0.f, 0.f, 0.f), kst, bfx,
                         bfy);
                     out[m] = o;
-                    write_bc_from(g, xc, y, 0, o, out);
+                    write_bc2(sI, xc, y, o, out);
                 }
                 b2 = a2;
                 b5 = a5;

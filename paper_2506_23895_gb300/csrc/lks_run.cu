@@ -807,6 +807,11 @@ Inst make_inst(const lks_ctx* c) {
     I.src_r = g.okind == 0 ? (float)(-h / (3.0 * g.ocount)) : 0.f;
     I.src_x = g.okind == 0 ? 0.f : (float)(-h * g.odir[0] / g.ocount);
     I.src_y = g.okind == 0 ? 0.f : (float)(-h * g.odir[1] / g.ocount);
+    for (int f = 0; f < 4; ++f) {
+        I.bcf[f] = make_float4((float)g.bcv[f][0], (float)g.bcv[f][1], 0.f,
+                               (float)(g.bcv[f][3] - g.rho0));
+        I.bckeep[f] = g.bc[f] == BC_WALL || g.bc[f] == BC_INLET;
+    }
     return I;
 }
 

@@ -31,6 +31,9 @@ struct Inst {
     float Af, bf[2];          // A and the body force in single precision
     double hwin;              // 1 / (window length): the window weight h_n inside the window
     float src_r, src_x, src_y;   // h_n d j / d (rho, ux, uy) at a target node, inside the window
+    float4 bcf[4];            // per face: prescribed (ux, uy, 0, rho - rho0) in single precision
+    int bckeep[4];            // per face: 1 keeps the source's rho (wall, inlet), 0 prescribes
+                              // it and copies the normal velocity (outlet)
 };
 
 // Configurations of the fused kernels, chosen per run by the autotuner.  Step: five tile
