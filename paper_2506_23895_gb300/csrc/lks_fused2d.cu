@@ -689,6 +689,32 @@ __device__ __noinline__ float4 bcT_fold(const Geom& g, const float4* lam, const 
     return make_float4(acc.r, acc.x, acc.y, acc.z);
 }
 
+// The same for a node next to a single face (most of them): its one boundary node inline, with
+// the arithmetic of bcT_gather; nodes next to two faces take bcT_fold.
+__device__ __forceinline__ float4 bcT_fold2(const Inst& I, const float4* lam,
+                                            const ObjAdd<float>& h, int x, int y, float4 lv) {
+    const Geom& g = I.g;
+    const int n0 = g.n[0], n1 = g.n[1];
+    const bool xl = !g.periodic[0] && x == 1, xh = !g.periodic[0] && x == n0 - 2;
+    const bool yl = !g.periodic[1] && y == 1, yh = !g.periodic[1] && y == n1 - 2;
+    if ((int)xl + (int)xh + (int)yl + (int)yh != 1) return bcT_fold(g, lam, h, x, y, lv);
+    const int f = xl ? 0 : (xh ? 1 : (yl ? 2 : 3));
+    const int bx = xl ? 0 : (xh ? n0 - 1 : x), by = yl ? 0 : (yh ? n1 - 1 : y);
+    V4<float> lb;
+    {
+        const float4 t = lam[(long long)by * n0 + bx];
+        lb.r = t.x;
+        lb.x = t.y;
+        lb.y = t.z;
+        lb.z = t.w;
+    }
+    obj_source(g, bx, by, 0, h, lb);
+    if (I.bckeep[f]) lv.x += lb.r;
+    else if (f < 2) lv.y += lb.x;
+    else lv.z += lb.y;
+    return lv;
+}
+
 // One tile of the adjoint step.  EDGE: the general path (wraps, grid edges, boundary nodes,
 // one-sided boundary rows of the transposed gradient).
 template <int TX, int TY, bool EDGE>
@@ -726,7 +752,7 @@ __device__ __forceinline__ void adj_tile(const Inst& I, int x0, int y0, const Ob
         if (!EDGE || (gx >= 0 && gx < n0 && gy >= 0 && gy < n1 && !is_boundary(g, gx, gy, 0))) {
             const long long gm = (long long)gy * n0 + gx;
             float4 lv = __ldg(lam + gm);
-            if (tbc && sources_boundary(g, gx, gy, 0)) lv = bcT_fold(g, lam, bsrc, gx, gy, lv);
+            if (tbc && sources_boundary(g, gx, gy, 0)) lv = bcT_fold2(I, lam, bsrc, gx, gy, lv);
             float lr = lv.x, lux = lv.y, luy = lv.z;
             if (ttgt && in_target2(g, os, gx, gy)) {
                 lr += os.r;
