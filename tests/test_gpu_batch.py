@@ -70,6 +70,22 @@ def test_fused2d_matches_plain_and_oracle(L, name):
     assert rel_l2(gf, go) < 1e-4
 
 
+def test_transfer_tape_matches_transfers_formed_again(L):
+    """The adjoint of a taped step reads the step's kappa and u_S from the transfer tape when the
+    tape segment fits it (up to max(ceil(sqrt N) + 2, 64) steps), else it forms the transfer
+    again: both give the same values, so J, the state and dJ/dgamma are bitwise equal."""
+    w = W.small_channel2d(nx=40, ny=30, LD=12, n_steps=150, omega=0.01, seed=31)
+    # full history: one tape segment of 150 steps, longer than the transfer tape
+    J0, st0, g0, s0 = single(L, w)
+    assert s0["tape_steps"] == 150 and s0["recomputed_steps"] == 0
+    # 30 snapshot slots: tape segments of 13 steps, recomputed, each within the transfer tape
+    J1, st1, g1, s1 = single(L, w, slots=30)
+    assert s1["recomputed_steps"] > 0 and s1["tape_steps"] < 64
+    assert J0 == J1
+    assert np.array_equal(st0, st1)
+    assert np.array_equal(g0, g1)
+
+
 def test_fused2d_periodic_box(L):
     n, Ld, steps = (40, 34, 1), (9, 9, 1), 30
     p = W.periodic_box(2, n, A=0.35, L=Ld, n_steps=steps)
