@@ -295,40 +295,13 @@ __device__ __forceinline__ void bcT_gather(const Geom& g, const V4<T>* lam, cons
     });
 }
 
-// A node next to a single face sources one boundary node: that case inline, with the same
-// arithmetic as the loop over the neighbourhood (which the others take).
 template <class T>
 __device__ __forceinline__ void bcT_node(const Geom& g, V4<T>* lam, const ObjAdd<T>& h, int x,
                                          int y, int z) {
     if (!sources_boundary(g, x, y, z)) return;
     const long long m = node_index(g, x, y, z);
     V4<T> acc = lam[m];
-    const int c[3] = {x, y, z};
-    int nf = 0, fa = 0, fs = 0;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        if (a >= g.dim || g.periodic[a]) continue;
-        const int lo = c[a] == 1, hi = c[a] == g.n[a] - 2;
-        if (lo | hi) {
-            nf += lo + hi;
-            fa = a;
-            fs = hi;
-        }
-    }
-    if (nf == 1) {
-        const int bx = fa == 0 ? (fs ? g.n[0] - 1 : 0) : x;
-        const int by = fa == 1 ? (fs ? g.n[1] - 1 : 0) : y;
-        const int bz = fa == 2 ? (fs ? g.n[2] - 1 : 0) : z;
-        V4<T> lb = lam[node_index(g, bx, by, bz)];
-        obj_source(g, bx, by, bz, h, lb);
-        const int t = g.bc[2 * fa + fs];
-        if (t == BC_WALL || t == BC_INLET) acc.r += lb.r;
-        else if (fa == 0) acc.x += lb.x;
-        else if (fa == 1) acc.y += lb.y;
-        else acc.z += lb.z;
-    } else {
-        bcT_gather<T>(g, lam, h, x, y, z, acc);
-    }
+    bcT_gather<T>(g, lam, h, x, y, z, acc);
     lam[m] = acc;
 }
 
