@@ -197,8 +197,8 @@ __global__ void __launch_bounds__(kThreads)
 }
 
 // The same lists, moments and plane sums with one thread per box column, for transfers with few
-// design planes (2D): there a box column is a single node, the columns are many and the warp
-// per column would leave its lanes idle over the plane sums.
+// design planes over many columns (large 2D boxes): there a box column is a single node, and a
+// warp per column would leave its lanes idle over the plane sums.
 template <class T>
 __global__ void __launch_bounds__(kThreads)
     k_tap_lists_col(Design d, Geom g, Motion m, TransferScratch ts, const T* __restrict__ kref_t,
@@ -471,7 +471,9 @@ void launch_transfer(const Design& d, const Geom& g, const Motion& m, TransferSc
                      const T* kref_t, T* k2, V4<T>* kus, cudaStream_t st) {
     if (d.nd == 0 || g.boxN == 0) return;
     const long long ncols = (long long)g.bn[0] * g.bn[1];
-    if (d.L[2] >= 8)
+    // a warp per column while the warps stay few or the planes many; one thread per column for
+    // the large single-plane boxes of 2D transfers
+    if (d.L[2] >= 8 || ncols <= 16384)
         k_tap_lists<T><<<(unsigned)((ncols + kTapWarps - 1) / kTapWarps), kThreads, 0, st>>>(
             d, g, m, ts, kref_t, k2);
     else
