@@ -499,21 +499,25 @@ __host__ __device__ inline int xface_col(int x0, int nx, int TX) {
 }
 
 // f^eq-region coordinates (hfx, hfy) of the extra node of thread tid: the one-cell rim over whole
-// warps.  In a tile holding exactly one x face, the lanes past the last rim node take that
-// face's column, one lane per row (those nodes need one-sided x derivatives, which the rim
-// warps form anyway); otherwise they repeat earlier rim nodes (the same values stored twice).
+// warps.  In a tile holding exactly one x face, every node of that face's column goes to the
+// last rim warp -- its rows (one spare lane per row) and its two rim-row nodes (two more spare
+// lanes), whose own lanes in the rim rows then repeat their left neighbour -- so that only that
+// warp needs the one-sided x derivatives; otherwise the spare lanes repeat earlier rim nodes.
+// Repeated nodes store the same values twice.
 template <int TX, int TY, int NHALO>
 __device__ __forceinline__ void rim_node(int tid, int x0, int nx, int& hfx, int& hfy) {
     constexpr int FW = TX + 2, FY = TY + 2;
     constexpr int RIMW = (NHALO + 31) / 32 * 32;
-    static_assert(RIMW - NHALO >= TY, "a spare rim lane per row of the tile");
+    static_assert(RIMW - NHALO >= TY + 2, "spare rim lanes for the face column");
+    static_assert(NHALO >= RIMW - 32, "the face column in the last rim warp");
     hfx = 0;
     hfy = 0;
     if (tid >= RIMW) return;
     const int xf = xface_col(x0, nx, TX);
-    if (tid >= NHALO && tid < NHALO + TY && xf >= 0) {
+    if (xf >= 0 && tid >= NHALO && tid < NHALO + TY + 2) {
+        const int r = tid - NHALO;
         hfx = xf + 1;
-        hfy = 1 + (tid - NHALO);
+        hfy = r < TY ? 1 + r : (r == TY ? 0 : FY - 1);
         return;
     }
     const int rr = tid < NHALO ? tid : tid - (RIMW - NHALO);
@@ -528,6 +532,7 @@ __device__ __forceinline__ void rim_node(int tid, int x0, int nx, int& hfx, int&
         hfx = FW - 1;
         hfy = 1 + (rr - 2 * FW - TY);
     }
+    if (xf >= 0 && tid < NHALO && (hfy == 0 || hfy == FY - 1) && hfx == xf + 1) hfx = xf;
 }
 
 template <int TY_>
@@ -657,6 +662,8 @@ __device__ __forceinline__ void zbody(const CUtensorMap& tmap, const FusedArgs& 
     const int forr = hfy * FX + hfx;
     constexpr int RIMW = (C::NHALO + 31) / 32 * 32;
     const bool has_rim = tid < RIMW;   // whole warps
+    // rim warps holding a face node take the one-sided forms (a uniform choice per warp)
+    const bool rim_edge = !IN && __any_sync(0xffffffffu, has_rim && (rxm | rym) != 0);
     const bool out_col = IN || (gx >= 1 && gx <= nx - 2 && gy >= 1 && gy <= ny - 2);
     const int bxx = gx - g.blo[0], byy = gy - g.blo[1];
     const bool box_col = g.boxN > 0 && bxx >= 0 && byy >= 0 && bxx < g.bn[0] && byy < g.bn[1];
@@ -739,8 +746,12 @@ __device__ __forceinline__ void zbody(const CUtensorMap& tmap, const FusedArgs& 
                 }
                 if (has_rim) {
                     float d0, d1, d2;
-                    feq_reg<HX, FS, true>(a, r0 + hr, rc0, rum, rup, sF + forr, rxm, rym, 0, z0,
-                                          d0, d1, d2);
+                    if (rim_edge)
+                        feq_reg<HX, FS, true>(a, r0 + hr, rc0, rum, rup, sF + forr, rxm, rym, 0,
+                                              z0, d0, d1, d2);
+                    else
+                        feq_reg<HX, FS, false>(a, r0 + hr, rc0, rum, rup, sF + forr, 0, 0, 0, z0,
+                                               d0, d1, d2);
                 }
             }
         } else {
