@@ -1,19 +1,20 @@
 // D2Q9 FP32 kernels over instance tables (lks_table.h): every launch covers all instances of a
 // plan with a persistent grid that walks the concatenated work units.
 //
-//   k_t_design_pos  x_ref, y_ref of every design column (design_col_pos);
-//   k_t_transfer2d  kappa and u_S on every footprint-box node (transfer2d_node, Sec. 2.3);
+//   k_t_design_pos  x_ref, y_ref of every design column (col_pos_sc), for a run's first step;
+//   k_t_transfer2d  kappa and u_S on every footprint-box node (transfer2d_node, Sec. 2.3), into
+//                   the box buffer or the transfer tape, and the next step's design positions;
 //   k_t_step2d      fused LKS step (Alg. 1; Sec. 2.2 f^eq with the viscosity term, Eqs. rho,
 //                   u, u_ex_2, bc_rho, bc_u) on TX x TY tiles: the state tile with a two-cell
 //                   halo goes to shared memory, f^eq of the tile and a one-cell rim is
 //                   evaluated once per node and direction, then gathered;
 //   k_t_objective   one block per instance inside the objective window (Sec. 2.5);
-//   k_t_bcT2d       transpose of the boundary copies (bcT_node);
 //   k_t_adj2d       fused exact adjoint step (structure of Alg. 2, Eqs. arho, au, as): lambda
-//                   to mu (Brinkman transpose and the kappa sensitivity density e), moments
+//                   plus the transpose of the boundary copies, to mu (Brinkman transpose and
+//                   the kappa sensitivity density e), moments
 //                   of F~ on the tile and a one-cell rim, adjoint equilibrium and the full
 //                   transposed velocity gradient including the one-sided boundary rows;
-//   k_t_sens        dJ/dgamma gather per design column (sens_run, Sec. 2.4).
+//   k_t_sens        dJ/dgamma gather per design node (sens2d_node, Sec. 2.4).
 #include <cuda_runtime.h>
 
 #include "lks_table.h"
