@@ -80,6 +80,10 @@ CASES = {
                                           trans_amp=1.5, seed=31),
     "ragged3d": lambda: W.small_duct3d(nx=37, ny=29, nz=33, LD=9, n_steps=20, omega=0.01,
                                        trans_amp=1.0, seed=32),
+    # nx - 1 and ny - 1 one past a tile (32 x 8): a face in the rim column of a tile and in
+    # the rim row of another, next to tiles holding a single face
+    "rimface3d": lambda: W.small_duct3d(nx=33, ny=17, nz=13, LD=7, n_steps=14, omega=0.02,
+                                        trans_amp=0.8, seed=35),
 }
 
 
@@ -211,7 +215,7 @@ MID3D = lambda: W.small_duct3d(nx=70, ny=45, nz=52, LD=14, n_steps=30, omega=0.0
 
 
 @pytest.mark.parametrize("name", ["small3d_J2", "small3d_J1", "ragged3d", "mid3d",
-                                  "corners3d"])
+                                  "corners3d", "rimface3d"])
 def test_fused_fp32_step_matches_plain_fp32_and_oracle(L, name):
     w = MID3D() if name == "mid3d" else CASES[name]()
     Jf, sf, gf, _ = run_gpu(L, w, L.FP32, expect_fused=True)
@@ -224,7 +228,7 @@ def test_fused_fp32_step_matches_plain_fp32_and_oracle(L, name):
     assert rel_l2(gf, go) < 1e-4
 
 
-@pytest.mark.parametrize("name", ["small3d_J1", "ragged3d", "mid3d", "corners3d"])
+@pytest.mark.parametrize("name", ["small3d_J1", "ragged3d", "mid3d", "corners3d", "rimface3d"])
 def test_fused_step_variants_agree(L, name):
     """Every variant of the fused 3D forward step (fixed through lks_step_variant) gives the
     same run as variant 0 up to rounding, within the FP32 tolerances of the oracle; the default
