@@ -93,18 +93,28 @@ __global__ void __launch_bounds__(NT) k_t_design_pos(Plan p, int noff) {
 
 // One 16 x 16 tile of the footprint box per work unit.  The design nodes any node of the tile can
 // reach (the tile's inverse rigid image widened by the kernel radius: at most 30 x 30 nodes) are
-// staged in shared memory with contiguous reads; every node then runs the candidate loop of
-// transfer2d_node on the staged copy, in the same order and with the same arithmetic.
+// staged in shared memory with contiguous reads and binned by their integer base into a table of
+// cells; every node then visits the 4 x 4 cells whose taps cover it, so that it touches only the
+// design nodes in its support (about 16, against some 36 window candidates).  A tile whose table
+// overflows runs the candidate loop of transfer2d_node on the staged copy instead.
 constexpr int kTrWin = 32;   // staged window side (design nodes)
 static_assert(kBoxTile * kBoxTile == NT, "one box tile per block of NT threads");
+// Cells of the tile's design-node table: the integer bases b that can reach a node of the tile
+// (b in [x - 2, x + 1] per axis), kTrCells per axis; a unit-spaced rotated lattice puts at most
+// two design nodes in one unit cell, kTrCap leaves room (a fuller cell sends the tile back to the
+// candidate loop).
+constexpr int kTrCells = kBoxTile + 3, kTrCap = 4;
 
 // With next, the units past the box tiles form the design positions of step n + 1 (the next
 // transfer's), into the other parity's set.
-__global__ void __launch_bounds__(NT) k_t_transfer2d(Plan p, int noff, int kslot, int next) {
+__global__ void __launch_bounds__(NT, 5) k_t_transfer2d(Plan p, int noff, int kslot, int next) {
     __shared__ int2 sb[kTrWin * kTrWin];
     __shared__ float4 ssc[kTrWin * kTrWin];
     __shared__ float skr[kTrWin * kTrWin];
     __shared__ int swin[4];
+    __shared__ int scnt[kTrCells * kTrCells];
+    __shared__ unsigned short sent[kTrCells * kTrCells * kTrCap];
+    __shared__ int sfull;
     const int* pre = p.pre + U_BOX * (p.count + 1);
     const int n = step_of(p, noff);
     const int nbox = p.total[U_BOX];
@@ -140,7 +150,9 @@ __global__ void __launch_bounds__(NT) k_t_transfer2d(Plan p, int noff, int kslot
             swin[1] = -(1 << 30);
             swin[2] = 1 << 30;
             swin[3] = -(1 << 30);
+            sfull = 0;
         }
+        for (int e = threadIdx.x; e < kTrCells * kTrCells; e += NT) scnt[e] = 0;
         __syncthreads();
         if (node && i0 <= i1 && j0 <= j1) {
             atomicMin(&swin[0], i0);
@@ -152,14 +164,39 @@ __global__ void __launch_bounds__(NT) k_t_transfer2d(Plan p, int noff, int kslot
         const int wi0 = swin[0], wj0 = swin[2];
         const int wni = swin[1] - wi0 + 1, wnj = swin[3] - wj0 + 1;
         const bool staged = wni <= kTrWin && wnj <= kTrWin;
+        // the tile's first analysis node less 2: the lowest base whose taps reach the tile
+        const int cx0 = g.blo[0] + bx0 - 2, cy0 = g.blo[1] + by0 - 2;
         if (staged && wni > 0 && wnj > 0) {
             const int2* base = I.pos_b[n & 1];
             for (int e = threadIdx.x; e < wni * wnj; e += NT) {
                 const int jj = e / wni, ii = e - jj * wni;
                 const int k = (wj0 + jj) * d.L[0] + wi0 + ii;
-                sb[jj * kTrWin + ii] = __ldg(base + k);
+                const int2 bk = __ldg(base + k);
+                sb[jj * kTrWin + ii] = bk;
                 ssc[jj * kTrWin + ii] = __ldg(I.pos_sc[n & 1] + k);
                 skr[jj * kTrWin + ii] = __ldg(I.kref + k);
+                const int cx = bk.x - cx0, cy = bk.y - cy0;
+                if ((unsigned)cx < (unsigned)kTrCells && (unsigned)cy < (unsigned)kTrCells) {
+                    const int cell = cy * kTrCells + cx;
+                    const int slot = atomicAdd(&scnt[cell], 1);
+                    if (slot < kTrCap) sent[cell * kTrCap + slot] = (unsigned short)(jj * kTrWin + ii);
+                    else sfull = 1;
+                }
+            }
+        }
+        __syncthreads();
+        // each cell's design nodes in design index order (the staging order of the slots is not
+        // fixed)
+        if (staged && !sfull) {
+            for (int cell = threadIdx.x; cell < kTrCells * kTrCells; cell += NT) {
+                const int cnt = scnt[cell];
+                unsigned short* ent = sent + cell * kTrCap;
+                for (int a1 = 1; a1 < cnt; ++a1)
+                    for (int a2 = a1; a2 > 0 && ent[a2 - 1] > ent[a2]; --a2) {
+                        const unsigned short tmp = ent[a2];
+                        ent[a2] = ent[a2 - 1];
+                        ent[a2 - 1] = tmp;
+                    }
             }
         }
         __syncthreads();
@@ -172,19 +209,41 @@ __global__ void __launch_bounds__(NT) k_t_transfer2d(Plan p, int noff, int kslot
         }
         const float gx0 = d.xiGf[0], gy0 = d.xiGf[1];
         float kap = 0.f, m0 = 0.f, m1x = 0.f, m1y = 0.f;
-        for (int j = j0; j <= j1; ++j)
-            for (int ii = i0; ii <= i1; ++ii) {
-                const int sk = (j - wj0) * kTrWin + (ii - wi0);
-                const int2 b = sb[sk];
-                const int qx = x - b.x + 1, qy = y - b.y + 1;
-                if ((unsigned)qx > 3u || (unsigned)qy > 3u) continue;
-                const float4 sc = ssc[sk];
-                const float W = tap_weight(qx, sc.x, sc.y) * tap_weight(qy, sc.z, sc.w);
-                kap += W * skr[sk];
-                m0 += W;
-                m1x += W * ((float)ii - gx0);
-                m1y += W * ((float)j - gy0);
-            }
+        if (!sfull) {
+            // the design nodes whose base b reaches (x, y): b = (x, y) + 1 - (qx, qy), qx, qy in
+            // 0..3, visited by tap (qy, qx) and then in design index order within a cell
+            const int ccx = x - cx0 + 1, ccy = y - cy0 + 1;
+#pragma unroll
+            for (int qy = 0; qy < 4; ++qy)
+#pragma unroll
+                for (int qx = 0; qx < 4; ++qx) {
+                    const int cell = (ccy - qy) * kTrCells + (ccx - qx);
+                    const int cnt = scnt[cell];
+                    for (int a1 = 0; a1 < cnt; ++a1) {
+                        const int sk = sent[cell * kTrCap + a1];
+                        const float4 sc = ssc[sk];
+                        const float W = tap_weight(qx, sc.x, sc.y) * tap_weight(qy, sc.z, sc.w);
+                        kap += W * skr[sk];
+                        m0 += W;
+                        m1x += W * ((float)(wi0 + (sk & (kTrWin - 1))) - gx0);
+                        m1y += W * ((float)(wj0 + (sk / kTrWin)) - gy0);
+                    }
+                }
+        } else {
+            for (int j = j0; j <= j1; ++j)
+                for (int ii = i0; ii <= i1; ++ii) {
+                    const int sk = (j - wj0) * kTrWin + (ii - wi0);
+                    const int2 b = sb[sk];
+                    const int qx = x - b.x + 1, qy = y - b.y + 1;
+                    if ((unsigned)qx > 3u || (unsigned)qy > 3u) continue;
+                    const float4 sc = ssc[sk];
+                    const float W = tap_weight(qx, sc.x, sc.y) * tap_weight(qy, sc.z, sc.w);
+                    kap += W * skr[sk];
+                    m0 += W;
+                    m1x += W * ((float)ii - gx0);
+                    m1y += W * ((float)j - gy0);
+                }
+        }
         const float om = m.omf;
         V4<float> o;
         o.r = kap;
