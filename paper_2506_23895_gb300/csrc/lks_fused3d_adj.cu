@@ -8,8 +8,9 @@
 //      (lambda_rho + d j/d rho, (lambda_u + d j/d u) / (1 + kappa)) -- the transpose of the
 //      Brinkman update (Eq. u_ex_2) -- and, on the tile's nodes inside the footprint box,
 //      e = mu_u . (u_S - u^n), the sensitivity density dJ/dkappa;
-//   2. gathers F~_i(y) = mu_rho(y + c_i) + c_i . mu_u(y + c_i) on the tile and a one-cell rim
-//      into R~ = sum w F~, U~ = sum w c F~, S~ = sum w c c F~ (corner sums by a butterfly);
+//   2. gathers F~_i(y) = mu_rho(y + c_i) + c_i . mu_u(y + c_i) on the tile
+//      into R~ = sum w F~, U~ = sum w c F~, S~ = sum w c c F~ (corner sums by a butterfly), and
+//      on a one-cell rim (corners excepted) the three S~ components its tile neighbour needs;
 //   3. writes lambda^{n-1} = (R~, 3 U~ + 9 S~ u^{n-1} - 3 R~ u^{n-1} + D^T(2 A S~)) for the
 //      tile, with the transposed gradient in its central form; boundary rows' one-sided parts
 //      are added afterwards by k_adj_bcorr from the 2 A S~ values this kernel stores for
@@ -34,7 +35,11 @@ constexpr int FX = TX + 2, FY = TY + 2;     // moment region with a one-cell hal
 constexpr int PF = FX + 1;                  // row pitch of the S~ planes (odd)
 constexpr int NSLOT = 5;
 constexpr int NTHR = TX * TY;
-constexpr int NRIM1 = FX * FY - TX * TY;    // 84 rim nodes of the moment region
+// rim nodes of the moment region whose S~ the transposed gradient reads: the two y-rim rows
+// (warps 0 and 1, one row each) and the two x-rim columns (lanes 0..15 of warp 2); the four
+// corners of the region are never read
+constexpr int NRIM1 = 2 * TX + 2 * TY;
+static_assert(TX == 32 && 2 * TY <= 32, "rim rows map to whole warps");
 constexpr int NRIM2 = HX * HY - TX * TY;    // 176 halo nodes to convert
 constexpr int NS = 5;                       // S~ components shared in-plane: xx xy xz yy yz
 constexpr unsigned PLANE_BYTES = PX * HY * 16;   // bytes one TMA box delivers
@@ -118,15 +123,14 @@ struct Mom {
     float R, Ux, Uy, Uz, Sxx, Sxy, Sxz, Syy, Syz, Szz;
 };
 
-// Moments of F~ at one node from mu in planes p-1 (cm), p (c0), p+1 (cp); pointers at the node.
-__device__ __forceinline__ Mom moments(const AdjArgs& a, const float4* __restrict__ c0,
-                                       const float4* __restrict__ cm,
-                                       const float4* __restrict__ cp) {
-    const float4 s = c0[0], xp = c0[1], xm = c0[-1], yp = c0[PX], ym = c0[-PX];
-    const float4 zp = cp[0], zm = cm[0];
-    const float gpx = xp.x + xp.y, gmx = xm.x - xm.y;
-    const float gpy = yp.x + yp.z, gmy = ym.x - ym.z;
-    const float gpz = zp.x + zp.w, gmz = zm.x - zm.w;
+// Sums of F~ over the eight corner neighbours (sx, sy, sz) of a node, in planes p-1 (cm) and
+// p+1 (cp): G = sum F~, and the sums weighted by sx, sy, sz, sx sy, sx sz, sy sz.
+struct Corners {
+    float G, xG, yG, zG, xyG, xzG, yzG;
+};
+
+__device__ __forceinline__ Corners corners(const float4* __restrict__ cm,
+                                           const float4* __restrict__ cp) {
     // corners (sx, sy, sz): F~ = mu_rho + sx mu_x + sy mu_y + sz mu_z at y + (sx, sy, sz)
     float a_[2][2], b_[2][2];   // [sy>0?0:1][sz>0?0:1]: sums/differences over sx
 #pragma unroll
@@ -150,8 +154,29 @@ __device__ __forceinline__ Mom moments(const AdjArgs& a, const float4* __restric
     const float Adp = a_[0][0] - a_[1][0], Adm = a_[0][1] - a_[1][1];
     const float Bp = b_[0][0] + b_[1][0], Bm = b_[0][1] + b_[1][1];
     const float Bdp = b_[0][0] - b_[1][0], Bdm = b_[0][1] - b_[1][1];
-    const float sG = Ap + Am, szG = Ap - Am, syG = Adp + Adm, syzG = Adp - Adm;
-    const float sxG = Bp + Bm, sxzG = Bp - Bm, sxyG = Bdp + Bdm;
+    Corners c;
+    c.G = Ap + Am;
+    c.zG = Ap - Am;
+    c.yG = Adp + Adm;
+    c.yzG = Adp - Adm;
+    c.xG = Bp + Bm;
+    c.xzG = Bp - Bm;
+    c.xyG = Bdp + Bdm;
+    return c;
+}
+
+// Moments of F~ at one node from mu in planes p-1 (cm), p (c0), p+1 (cp); pointers at the node.
+__device__ __forceinline__ Mom moments(const float4* __restrict__ c0,
+                                       const float4* __restrict__ cm,
+                                       const float4* __restrict__ cp) {
+    const float4 s = c0[0], xp = c0[1], xm = c0[-1], yp = c0[PX], ym = c0[-PX];
+    const float4 zp = cp[0], zm = cm[0];
+    const float gpx = xp.x + xp.y, gmx = xm.x - xm.y;
+    const float gpy = yp.x + yp.z, gmy = ym.x - ym.z;
+    const float gpz = zp.x + zp.w, gmz = zm.x - zm.w;
+    const Corners k = corners(cm, cp);
+    const float sG = k.G, szG = k.zG, syG = k.yG, syzG = k.yzG;
+    const float sxG = k.xG, sxzG = k.xzG, sxyG = k.xyG;
     using Wf = Wts<float, 3>;
     Mom m;
     const float ax = gpx + gmx, ay = gpy + gmy, az = gpz + gmz;
@@ -167,6 +192,32 @@ __device__ __forceinline__ Mom moments(const AdjArgs& a, const float4* __restric
     m.Sxz = Wf::s_2 * sxzG;
     m.Syz = Wf::s_2 * syzG;
     return m;
+}
+
+// The in-plane S~ components (9 S~) that the transposed gradient takes from a rim node: x-rim
+// nodes (XRIM) give xx, xy, xz from the +-x faces and the corners, y-rim nodes give xy, yy, yz
+// from the +-y faces and the corners; the same expressions as moments().
+template <bool XRIM>
+__device__ __forceinline__ void rim_moments(const float4* __restrict__ c0,
+                                            const float4* __restrict__ cm,
+                                            const float4* __restrict__ cp, float& s0, float& s1,
+                                            float& s2) {
+    using Wf = Wts<float, 3>;
+    const Corners k = corners(cm, cp);
+    const float s2G = Wf::s_2 * k.G;
+    if (XRIM) {
+        const float4 xp = c0[1], xm = c0[-1];
+        const float gpx = xp.x + xp.y, gmx = xm.x - xm.y;
+        s0 = Wf::s_1 * (gpx + gmx) + s2G;
+        s1 = Wf::s_2 * k.xyG;
+        s2 = Wf::s_2 * k.xzG;
+    } else {
+        const float4 yp = c0[PX], ym = c0[-PX];
+        const float gpy = yp.x + yp.z, gmy = ym.x - ym.z;
+        s0 = Wf::s_2 * k.xyG;
+        s1 = Wf::s_1 * (gpy + gmy) + s2G;
+        s2 = Wf::s_2 * k.yzG;
+    }
 }
 
 // ONEBAR = false: per plane a barrier after the TMA wait and one after the conversion.
@@ -209,20 +260,18 @@ __global__ void __launch_bounds__(NTHR, 4)
     }
     // rim node of the moment region (tid < NRIM1), in moment-region coordinates
     int rfx = 0, rfy = 0;
-    if (tid < NRIM1) {
-        if (tid < FX) {
-            rfx = tid;
-            rfy = 0;
-        } else if (tid < 2 * FX) {
-            rfx = tid - FX;
-            rfy = FY - 1;
-        } else if (tid < 2 * FX + TY) {
-            rfx = 0;
-            rfy = 1 + (tid - 2 * FX);
-        } else {
-            rfx = FX - 1;
-            rfy = 1 + (tid - 2 * FX - TY);
-        }
+    if (tid < TX) {
+        rfx = 1 + tid;
+        rfy = 0;
+    } else if (tid < 2 * TX) {
+        rfx = 1 + tid - TX;
+        rfy = FY - 1;
+    } else if (tid < 2 * TX + TY) {
+        rfx = 0;
+        rfy = 1 + (tid - 2 * TX);
+    } else if (tid < NRIM1) {
+        rfx = FX - 1;
+        rfy = 1 + (tid - 2 * TX - TY);
     }
     if (tid == 0) {
         for (int s = 0; s < NSLOT; ++s) mbar_init(smem_addr(&bars[s]));
@@ -257,19 +306,24 @@ __global__ void __launch_bounds__(NTHR, 4)
                      const float4& u, bool write_out) {
         const int q = p - 1;
         float* sw = sS + (size_t)(p & 1) * NS * FS;
-        const Mom m = moments(a, r0 + hp, rm + hp, rp + hp);
+        const Mom m = moments(r0 + hp, rm + hp, rp + hp);
         sw[0 * FS + fo] = m.Sxx;
         sw[1 * FS + fo] = m.Sxy;
         sw[2 * FS + fo] = m.Sxz;
         sw[3 * FS + fo] = m.Syy;
         sw[4 * FS + fo] = m.Syz;
-        if (tid < NRIM1) {
-            const Mom mr = moments(a, r0 + hr, rm + hr, rp + hr);
-            sw[0 * FS + fr] = mr.Sxx;
-            sw[1 * FS + fr] = mr.Sxy;
-            sw[2 * FS + fr] = mr.Sxz;
-            sw[3 * FS + fr] = mr.Syy;
-            sw[4 * FS + fr] = mr.Syz;
+        if (tid < 2 * TX) {
+            float s0, s1, s2;
+            rim_moments<false>(r0 + hr, rm + hr, rp + hr, s0, s1, s2);
+            sw[1 * FS + fr] = s0;
+            sw[3 * FS + fr] = s1;
+            sw[4 * FS + fr] = s2;
+        } else if (tid < NRIM1) {
+            float s0, s1, s2;
+            rim_moments<true>(r0 + hr, rm + hr, rp + hr, s0, s1, s2);
+            sw[0 * FS + fr] = s0;
+            sw[1 * FS + fr] = s1;
+            sw[2 * FS + fr] = s2;
         }
         // 3. lambda^{n-1} of plane q = p - 1 (its in-plane S~ was stored last iteration)
         if (write_out) {
