@@ -123,33 +123,26 @@ struct Mom {
     float R, Ux, Uy, Uz, Sxx, Sxy, Sxz, Syy, Syz, Szz;
 };
 
-// Sums of F~ over the eight corner neighbours (sx, sy, sz) of a node, in planes p-1 (cm) and
-// p+1 (cp): G = sum F~, and the sums weighted by sx, sy, sz, sx sy, sx sz, sy sz.
+// Corner neighbours (sx, sy, sz) of a node: F~ = mu_rho + sx mu_x + sy mu_y + sz mu_z there.
+// For one sy and one sz, from the records np (sx = +1) and nm (sx = -1) of the corner plane:
+// a = F~(+1) + F~(-1), b = F~(+1) - F~(-1).
+__device__ __forceinline__ void corner_pair(const float4 np, const float4 nm, float sy, float sz,
+                                            float& a, float& b) {
+    const float base_p = np.x + sy * np.z + sz * np.w;
+    const float base_m = nm.x + sy * nm.z + sz * nm.w;
+    const float gp = base_p + np.y;   // sx = +1
+    const float gm = base_m - nm.y;   // sx = -1
+    a = gp + gm;
+    b = gp - gm;
+}
+
+// Sums of F~ over the eight corner neighbours, from a_, b_ indexed [sy > 0 ? 0 : 1][sz > 0 ?
+// 0 : 1]: G = sum F~, and the sums weighted by sx, sy, sz, sx sy, sx sz, sy sz.
 struct Corners {
     float G, xG, yG, zG, xyG, xzG, yzG;
 };
 
-__device__ __forceinline__ Corners corners(const float4* __restrict__ cm,
-                                           const float4* __restrict__ cp) {
-    // corners (sx, sy, sz): F~ = mu_rho + sx mu_x + sy mu_y + sz mu_z at y + (sx, sy, sz)
-    float a_[2][2], b_[2][2];   // [sy>0?0:1][sz>0?0:1]: sums/differences over sx
-#pragma unroll
-    for (int jz = 0; jz < 2; ++jz) {
-        const float4* pl = jz == 0 ? cp : cm;
-        const float sz = jz == 0 ? 1.f : -1.f;
-#pragma unroll
-        for (int jy = 0; jy < 2; ++jy) {
-            const int oy = jy == 0 ? PX : -PX;
-            const float sy = jy == 0 ? 1.f : -1.f;
-            const float4 np = pl[oy + 1], nm = pl[oy - 1];
-            const float base_p = np.x + sy * np.z + sz * np.w;
-            const float base_m = nm.x + sy * nm.z + sz * nm.w;
-            const float gp = base_p + np.y;   // sx = +1
-            const float gm = base_m - nm.y;   // sx = -1
-            a_[jy][jz] = gp + gm;
-            b_[jy][jz] = gp - gm;
-        }
-    }
+__device__ __forceinline__ Corners corner_sums(const float (&a_)[2][2], const float (&b_)[2][2]) {
     const float Ap = a_[0][0] + a_[1][0], Am = a_[0][1] + a_[1][1];
     const float Adp = a_[0][0] - a_[1][0], Adm = a_[0][1] - a_[1][1];
     const float Bp = b_[0][0] + b_[1][0], Bm = b_[0][1] + b_[1][1];
@@ -165,6 +158,54 @@ __device__ __forceinline__ Corners corners(const float4* __restrict__ cm,
     return c;
 }
 
+// The corner sums of a node from mu in planes p-1 (cm) and p+1 (cp); pointers at the node.
+__device__ __forceinline__ Corners corners(const float4* __restrict__ cm,
+                                           const float4* __restrict__ cp) {
+    float a_[2][2], b_[2][2];
+#pragma unroll
+    for (int jz = 0; jz < 2; ++jz) {
+        const float4* pl = jz == 0 ? cp : cm;
+#pragma unroll
+        for (int jy = 0; jy < 2; ++jy) {
+            const int oy = jy == 0 ? PX : -PX;
+            corner_pair(pl[oy + 1], pl[oy - 1], jy == 0 ? 1.f : -1.f, jz == 0 ? 1.f : -1.f,
+                        a_[jy][jz], b_[jy][jz]);
+        }
+    }
+    return corner_sums(a_, b_);
+}
+
+// The sz = -1 corner terms of plane pl seen from the node one plane above: c = (a[sy = +1],
+// a[sy = -1], b[sy = +1], b[sy = -1]).
+__device__ __forceinline__ void corner_below(const float4* __restrict__ pl, float (&c)[4]) {
+#pragma unroll
+    for (int jy = 0; jy < 2; ++jy) {
+        const int oy = jy == 0 ? PX : -PX;
+        corner_pair(pl[oy + 1], pl[oy - 1], jy == 0 ? 1.f : -1.f, -1.f, c[jy], c[2 + jy]);
+    }
+}
+
+// Moments from the in-plane face sums g(p|m)(x|y), the z-face sums gpz, gmz, mu_rho of the node
+// (s_rho) and the corner sums.
+__device__ __forceinline__ Mom assemble(float s_rho, float gpx, float gmx, float gpy, float gmy,
+                                        float gpz, float gmz, const Corners& k) {
+    using Wf = Wts<float, 3>;
+    Mom m;
+    const float ax = gpx + gmx, ay = gpy + gmy, az = gpz + gmz;
+    const float s2G = Wf::s_2 * k.G;
+    m.R = Wf::w0 * s_rho + Wf::w1 * (ax + ay + az) + Wf::w2 * k.G;
+    m.Ux = Wf::w3_1 * (gpx - gmx) + Wf::w3_2 * k.xG;
+    m.Uy = Wf::w3_1 * (gpy - gmy) + Wf::w3_2 * k.yG;
+    m.Uz = Wf::w3_1 * (gpz - gmz) + Wf::w3_2 * k.zG;
+    m.Sxx = Wf::s_1 * ax + s2G;
+    m.Syy = Wf::s_1 * ay + s2G;
+    m.Szz = Wf::s_1 * az + s2G;
+    m.Sxy = Wf::s_2 * k.xyG;
+    m.Sxz = Wf::s_2 * k.xzG;
+    m.Syz = Wf::s_2 * k.yzG;
+    return m;
+}
+
 // Moments of F~ at one node from mu in planes p-1 (cm), p (c0), p+1 (cp); pointers at the node.
 __device__ __forceinline__ Mom moments(const float4* __restrict__ c0,
                                        const float4* __restrict__ cm,
@@ -175,23 +216,36 @@ __device__ __forceinline__ Mom moments(const float4* __restrict__ c0,
     const float gpy = yp.x + yp.z, gmy = ym.x - ym.z;
     const float gpz = zp.x + zp.w, gmz = zm.x - zm.w;
     const Corners k = corners(cm, cp);
-    const float sG = k.G, szG = k.zG, syG = k.yG, syzG = k.yzG;
-    const float sxG = k.xG, sxzG = k.xzG, sxyG = k.xyG;
-    using Wf = Wts<float, 3>;
-    Mom m;
-    const float ax = gpx + gmx, ay = gpy + gmy, az = gpz + gmz;
-    const float s2G = Wf::s_2 * sG;
-    m.R = Wf::w0 * s.x + Wf::w1 * (ax + ay + az) + Wf::w2 * sG;
-    m.Ux = Wf::w3_1 * (gpx - gmx) + Wf::w3_2 * sxG;
-    m.Uy = Wf::w3_1 * (gpy - gmy) + Wf::w3_2 * syG;
-    m.Uz = Wf::w3_1 * (gpz - gmz) + Wf::w3_2 * szG;
-    m.Sxx = Wf::s_1 * ax + s2G;
-    m.Syy = Wf::s_1 * ay + s2G;
-    m.Szz = Wf::s_1 * az + s2G;
-    m.Sxy = Wf::s_2 * sxyG;
-    m.Sxz = Wf::s_2 * sxzG;
-    m.Syz = Wf::s_2 * syzG;
-    return m;
+    return assemble(s.x, gpx, gmx, gpy, gmy, gpz, gmz, k);
+}
+
+// moments() for a thread that marches one column in z and keeps in registers what the next
+// planes reuse: the node's own mu in planes p-1, p, p+1 (own_m, own_0, own_p: mu_rho and mu_z)
+// and the sz = -1 corner terms of plane p-1 (below, formed two planes earlier from the same
+// records); it reads only the four in-plane faces and the four corners of plane p+1 (c0, cp:
+// pointers at the node) and returns plane p+1's sz = -1 terms for node p+2 in next_below.
+__device__ __forceinline__ Mom moments_marched(const float4* __restrict__ c0,
+                                               const float4* __restrict__ cp, float2 own_m,
+                                               float own_0, float2 own_p,
+                                               const float (&below)[4],
+                                               float (&next_below)[4]) {
+    const float4 xp = c0[1], xm = c0[-1], yp = c0[PX], ym = c0[-PX];
+    const float gpx = xp.x + xp.y, gmx = xm.x - xm.y;
+    const float gpy = yp.x + yp.z, gmy = ym.x - ym.z;
+    const float gpz = own_p.x + own_p.y, gmz = own_m.x - own_m.y;
+    float a_[2][2], b_[2][2];
+#pragma unroll
+    for (int jy = 0; jy < 2; ++jy) {
+        const int oy = jy == 0 ? PX : -PX;
+        const float sy = jy == 0 ? 1.f : -1.f;
+        const float4 np = cp[oy + 1], nm = cp[oy - 1];
+        corner_pair(np, nm, sy, 1.f, a_[jy][0], b_[jy][0]);
+        corner_pair(np, nm, sy, -1.f, next_below[jy], next_below[2 + jy]);
+        a_[jy][1] = below[jy];
+        b_[jy][1] = below[2 + jy];
+    }
+    const Corners k = corner_sums(a_, b_);
+    return assemble(own_0, gpx, gmx, gpy, gmy, gpz, gmz, k);
 }
 
 // The in-plane S~ components (9 S~) that the transposed gradient takes from a rim node: x-rim
@@ -222,9 +276,16 @@ __device__ __forceinline__ void rim_moments(const float4* __restrict__ c0,
 
 // ONEBAR = false: per plane a barrier after the TMA wait and one after the conversion.
 // ONEBAR = true: every thread waits on the plane it converts and the conversion runs one plane
-// further ahead, so a single barrier per plane orders everything.
+// further ahead, so a single barrier per plane orders everything; each thread keeps its own
+// column's mu and the corner terms of the plane below in registers (moments_marched), which
+// takes three blocks per SM (80 registers) instead of four.
 template <bool ONEBAR>
-__global__ void __launch_bounds__(NTHR, 4)
+constexpr int adj_minb() {
+    return ONEBAR ? 3 : 4;
+}
+
+template <bool ONEBAR>
+__global__ void __launch_bounds__(NTHR, adj_minb<ONEBAR>())
     k_fused_adj3d(const __grid_constant__ CUtensorMap tmap, const AdjArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     float4* raw = reinterpret_cast<float4*>(smem + OFF_RAW);
@@ -299,6 +360,10 @@ __global__ void __launch_bounds__(NTHR, 4)
 
     Mom prev = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     float szm_x = 0.f, szm_y = 0.f, szm_z = 0.f;   // S~_{.z} of plane p-2
+    // ONEBAR: the own node's (mu_rho, mu_z) in planes p-1, p, p+1 and the sz = -1 corner terms
+    // of plane p-1 (below) and of plane p (below_next)
+    float2 own_m = make_float2(0.f, 0.f), own_0 = own_m, own_p = own_m;
+    float below[4] = {0.f, 0.f, 0.f, 0.f}, below_next[4] = {0.f, 0.f, 0.f, 0.f};
     bool ok = true;
     // moments of plane p from the converted planes p-1 (rm), p (r0), p+1 (rp) on the tile and
     // its rim, then lambda^{n-1} of plane p-1 (u: u^{n-1} there)
@@ -306,7 +371,20 @@ __global__ void __launch_bounds__(NTHR, 4)
                      const float4& u, bool write_out) {
         const int q = p - 1;
         float* sw = sS + (size_t)(p & 1) * NS * FS;
-        const Mom m = moments(r0 + hp, rm + hp, rp + hp);
+        Mom m;
+        if constexpr (ONEBAR) {
+            // the terms of plane p-1 come from plane p-3's pass, but not for the first two planes
+            if (p < q0 + 1) corner_below(rm + hp, below);
+            float nb[4];
+            m = moments_marched(r0 + hp, rp + hp, own_m, own_0.x, own_p, below, nb);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                below[k] = below_next[k];
+                below_next[k] = nb[k];
+            }
+        } else {
+            m = moments(r0 + hp, rm + hp, rp + hp);
+        }
         sw[0 * FS + fo] = m.Sxx;
         sw[1 * FS + fo] = m.Sxy;
         sw[2 * FS + fo] = m.Sxz;
@@ -427,11 +505,14 @@ __global__ void __launch_bounds__(NTHR, 4)
             const bool write_out = q >= q0 && own_in;
             float4 u = make_float4(0.f, 0.f, 0.f, 0.f);
             if (write_out) u = a.sp[q * zstride + col];
+            float4 nv = make_float4(0.f, 0.f, 0.f, 0.f);   // own mu of plane p + 2
             if (kc < nplanes) {
                 good = mbar_wait_once(smem_addr(&bars[kc % NSLOT]), (kc / NSLOT) & 1);
                 float4* pl = raw + (size_t)(kc % NSLOT) * SLOT;
                 const int gz = p + 2;
-                to_mu(a, pl[hp], cf_own, gx, gy, gz, own_in, has_obj);
+                nv = pl[hp];
+                to_mu(a, nv, cf_own, gx, gy, gz, own_in, has_obj);
+                pl[hp] = nv;
                 if (tid < NRIM2)
                     to_mu(a, pl[hc], cf_halo, x0 - 2 + cx, y0 - 2 + cy, gz, false, has_obj);
             }
@@ -439,6 +520,9 @@ __global__ void __launch_bounds__(NTHR, 4)
                 plane(p, raw + (size_t)((kc - 3) % NSLOT) * SLOT,
                       raw + (size_t)((kc - 2) % NSLOT) * SLOT,
                       raw + (size_t)((kc - 1) % NSLOT) * SLOT, u, write_out);
+            own_m = own_0;
+            own_0 = own_p;
+            own_p = make_float2(nv.x, nv.w);
             if (__syncthreads_or(!good)) {
                 ok = false;
                 break;
@@ -569,7 +653,8 @@ cudaError_t launch_fused_adj3d(const Geom& g, const V4<float>* lam_in, V4<float>
     }
     a.has_obj = (a.obj_r != 0.f || a.obj_u[0] != 0.f || a.obj_u[1] != 0.f || a.obj_u[2] != 0.f);
     const int tiles_x = (g.n[0] + TX - 1) / TX, tiles_y = (g.n[1] + TY - 1) / TY;
-    a.zchunk = fused_zchunk_waves(g, (long long)tiles_x * tiles_y, 4);
+    a.zchunk = fused_zchunk_waves(g, (long long)tiles_x * tiles_y,
+                                  variant == 1 ? adj_minb<true>() : adj_minb<false>());
     const int chunks = (g.n[2] + a.zchunk - 1) / a.zchunk;
     if (variant == 1)
         k_fused_adj3d<true><<<dim3(tiles_x, tiles_y, chunks), NTHR, SMEM_BYTES, st>>>(map, a);
